@@ -1,0 +1,757 @@
+/*
+ * FP64 CPU oracle of the explicit momentum right-hand side (test infrastructure).
+ *
+ * This file is the plain, slow, obviously-correct definition that the CUDA
+ * path is checked against.  Only the tests, the smoke check and the CPU-
+ * baseline leg of the benchmark may load it; the product path never does.
+ * It shares no source with the CUDA library.
+ *
+ * What it computes (Borrell et al., "Heterogeneous CPU/GPU co-execution of
+ * CFD simulations on the POWER9 architecture", section 2.1):
+ *   momentum equation (Eq. momentum), rho = 1, mu = nu:
+ *     du/dt + [2 u.eps(u) + (div u) u - 1/2 grad|u|^2] - div(2 nu eps(u)) + grad p + div tau = 0,
+ *     eps(u) = 1/2 (grad u + grad u^T), tau = -2 nu_t eps(u) (Vreman closure, section 2.1).
+ *   Galerkin FE in space (section 2.1), element-by-element assembly with the
+ *   three steps gather / computation / scatter (section 2.3.3):
+ *     R_a,i = - sum_e sum_g W_g [ N_a (c_i + d_i p) + 2 (nu + nu_t) eps_ij d_j N_a ],
+ *     W_g = w_g det J,  c = G u + (tr G) u  (the bracket evaluated pointwise
+ *     on the FE interpolant: 2 eps u - 1/2 grad|u|^2 = G u with G_ij = du_i/dx_j).
+ *   Lumped mass: row sums of the element mass matrix of the section 2.3.3
+ *     listing, M_a = sum_e sum_g W_g N_a.
+ *   Time integration: a three-stage Runge-Kutta momentum update (Algorithm 1);
+ *     the stage coefficients are the SSP-RK3 (Shu-Osher) ones, pressure frozen.
+ *
+ * Readings where the paper is silent (each one is listed in the design notes):
+ *   - quadrature per element type (the paper only says a category is a type
+ *     plus an integration rule): TET04 4-point degree-2 rule; PEN06 3-point
+ *     triangle x 2-point Gauss; HEX08 2x2x2 Gauss; PYR05 8-point collapsed
+ *     (Duffy) rule with 2-point Gauss-Jacobi(2,0) in the axial direction;
+ *   - Vreman filter width Delta = V_e^(1/3), V_e = sum_g W_g;
+ *   - Vreman nu_t = 0 when alpha:alpha == 0 or B_beta <= 0;
+ *   - pressure term in gradient form, viscous term in 2 eps form, natural
+ *     boundary terms dropped.
+ *
+ * Layouts (numpy-friendly): xyz, u, rhs are [n_nodes][3] row-major; conn is
+ * [n_elem][n_en] with the VTK local node order; p, mass are [n_nodes].
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_TET04 0
+#define ORC_PYR05 1
+#define ORC_PEN06 2
+#define ORC_HEX08 3
+
+#define ORC_TERM_CONV 1u
+#define ORC_TERM_VISC 2u
+#define ORC_TERM_SGS 4u
+#define ORC_TERM_PRES 8u
+
+#define ORC_CLOSURE_NONE 0
+#define ORC_CLOSURE_VREMAN 1
+#define ORC_CLOSURE_MLP 2
+
+#define MAXN 8
+#define MAXG 8
+
+typedef struct {
+    int64_t n_nodes;
+    const double *xyz;        /* [n_nodes][3] */
+    int64_t n_elem[4];
+    const int32_t *conn[4];   /* [n_elem][n_en] */
+} orc_mesh;
+
+/* MLP closure: 6 -> 64 -> 64 -> 64 -> 1, SiLU hidden, softplus output. */
+#define MLP_IN 6
+#define MLP_H 64
+typedef struct {
+    const double *w1, *b1;    /* [64][6], [64] */
+    const double *w2, *b2;    /* [64][64], [64] */
+    const double *w3, *b3;    /* [64][64], [64] */
+    const double *w4, *b4;    /* [64], [1] */
+    const double *feat_mean;  /* [6] */
+    const double *feat_std;   /* [6] */
+    double out_scale;         /* nu_t = out_scale * softplus(z) */
+} orc_mlp;
+
+typedef struct {
+    double nu;
+    double c_vreman;
+    int closure;
+    uint32_t mask;
+    const orc_mlp *mlp;
+} orc_params;
+
+int orc_nnode(int etype) {
+    static const int n[4] = {4, 5, 6, 8};
+    return (etype >= 0 && etype < 4) ? n[etype] : 0;
+}
+
+int orc_ngauss(int etype) {
+    static const int n[4] = {4, 8, 6, 8};
+    return (etype >= 0 && etype < 4) ? n[etype] : 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Quadrature rules on the reference elements.
+ *   TET04: {r,s,t >= 0, r+s+t <= 1}, volume 1/6.
+ *   PYR05: base [-1,1]^2 at zeta = 0, apex zeta = 1, volume 4/3.
+ *   PEN06: triangle {r,s >= 0, r+s <= 1} x zeta in [-1,1], volume 1.
+ *   HEX08: [-1,1]^3, volume 8.                                            */
+int orc_quadrature(int etype, double *pts, double *w) {
+    const double g = 1.0 / sqrt(3.0);
+    int n = 0;
+    if (etype == ORC_TET04) {
+        /* degree-2 rule: barycentric coordinates (b, a, a, a) and permutations */
+        const double a = (5.0 - sqrt(5.0)) / 20.0;
+        const double b = (5.0 + 3.0 * sqrt(5.0)) / 20.0;
+        const double P[4][3] = {{a, a, a}, {b, a, a}, {a, b, a}, {a, a, b}};
+        for (n = 0; n < 4; ++n) {
+            pts[3 * n + 0] = P[n][0];
+            pts[3 * n + 1] = P[n][1];
+            pts[3 * n + 2] = P[n][2];
+            w[n] = 1.0 / 24.0;
+        }
+        return 4;
+    }
+    if (etype == ORC_PEN06) {
+        const double T[3][2] = {{1.0 / 6.0, 1.0 / 6.0}, {2.0 / 3.0, 1.0 / 6.0}, {1.0 / 6.0, 2.0 / 3.0}};
+        const double Z[2] = {-g, g};
+        for (int iz = 0; iz < 2; ++iz)
+            for (int it = 0; it < 3; ++it) {
+                pts[3 * n + 0] = T[it][0];
+                pts[3 * n + 1] = T[it][1];
+                pts[3 * n + 2] = Z[iz];
+                w[n] = 1.0 / 6.0;
+                ++n;
+            }
+        return 6;
+    }
+    if (etype == ORC_HEX08) {
+        for (int k = 0; k < 2; ++k)
+            for (int j = 0; j < 2; ++j)
+                for (int i = 0; i < 2; ++i) {
+                    pts[3 * n + 0] = i ? g : -g;
+                    pts[3 * n + 1] = j ? g : -g;
+                    pts[3 * n + 2] = k ? g : -g;
+                    w[n] = 1.0;
+                    ++n;
+                }
+        return 8;
+    }
+    if (etype == ORC_PYR05) {
+        /* collapsed map (a, b, t) -> ((1-t) a, (1-t) b, t), Jacobian (1-t)^2;
+         * a, b: 2-point Gauss-Legendre on [-1,1]; t: 2-point Gauss rule for
+         * the weight (1-t)^2 on [0,1] (roots of the degree-2 orthogonal
+         * polynomial t^2 - 2t/3 + 1/15; weights from the first two moments). */
+        const double s = sqrt(2.0 / 45.0);
+        const double t1 = 1.0 / 3.0 - s, t2 = 1.0 / 3.0 + s;
+        const double w2 = (1.0 / 12.0 - t1 / 3.0) / (t2 - t1);
+        const double w1 = 1.0 / 3.0 - w2;
+        const double T[2] = {t1, t2}, WT[2] = {w1, w2};
+        for (int k = 0; k < 2; ++k)
+            for (int j = 0; j < 2; ++j)
+                for (int i = 0; i < 2; ++i) {
+                    const double t = T[k];
+                    pts[3 * n + 0] = (1.0 - t) * (i ? g : -g);
+                    pts[3 * n + 1] = (1.0 - t) * (j ? g : -g);
+                    pts[3 * n + 2] = t;
+                    w[n] = WT[k];
+                    ++n;
+                }
+        return 8;
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Shape functions N[a] and reference derivatives dN[a][j] = dN_a / dxi_j. */
+int orc_shape(int etype, const double *xi, double *N, double *dN) {
+    const double r = xi[0], s = xi[1], t = xi[2];
+    if (etype == ORC_TET04) {
+        N[0] = 1.0 - r - s - t; N[1] = r; N[2] = s; N[3] = t;
+        const double d[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+        for (int a = 0; a < 4; ++a)
+            for (int j = 0; j < 3; ++j) dN[3 * a + j] = d[a][j];
+        return 4;
+    }
+    if (etype == ORC_PEN06) {
+        const double L[3] = {1.0 - r - s, r, s};
+        const double Lr[3] = {-1.0, 1.0, 0.0};
+        const double Ls[3] = {-1.0, 0.0, 1.0};
+        const double zm = 0.5 * (1.0 - t), zp = 0.5 * (1.0 + t);
+        for (int i = 0; i < 3; ++i) {
+            N[i] = L[i] * zm;
+            N[i + 3] = L[i] * zp;
+            dN[3 * i + 0] = Lr[i] * zm;
+            dN[3 * i + 1] = Ls[i] * zm;
+            dN[3 * i + 2] = -0.5 * L[i];
+            dN[3 * (i + 3) + 0] = Lr[i] * zp;
+            dN[3 * (i + 3) + 1] = Ls[i] * zp;
+            dN[3 * (i + 3) + 2] = 0.5 * L[i];
+        }
+        return 6;
+    }
+    if (etype == ORC_HEX08) {
+        const double S[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
+                                {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+        for (int a = 0; a < 8; ++a) {
+            const double fx = 1.0 + S[a][0] * r, fy = 1.0 + S[a][1] * s, fz = 1.0 + S[a][2] * t;
+            N[a] = 0.125 * fx * fy * fz;
+            dN[3 * a + 0] = 0.125 * S[a][0] * fy * fz;
+            dN[3 * a + 1] = 0.125 * fx * S[a][1] * fz;
+            dN[3 * a + 2] = 0.125 * fx * fy * S[a][2];
+        }
+        return 8;
+    }
+    if (etype == ORC_PYR05) {
+        /* rational pyramid functions, base corners (xi_i, eta_i), apex N_5 = zeta:
+         * N_i = 1/4 [ (1 + xi_i xi)(1 + eta_i eta) - zeta + xi_i eta_i xi eta zeta / (1 - zeta) ] */
+        const double B[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
+        const double q = 1.0 / (1.0 - t);
+        for (int i = 0; i < 4; ++i) {
+            const double xi_i = B[i][0], et_i = B[i][1];
+            const double c = xi_i * et_i;
+            N[i] = 0.25 * ((1.0 + xi_i * r) * (1.0 + et_i * s) - t + c * r * s * t * q);
+            dN[3 * i + 0] = 0.25 * (xi_i * (1.0 + et_i * s) + c * s * t * q);
+            dN[3 * i + 1] = 0.25 * (et_i * (1.0 + xi_i * r) + c * r * t * q);
+            dN[3 * i + 2] = 0.25 * (-1.0 + c * r * s * q * q);
+        }
+        N[4] = t;
+        dN[12] = 0.0; dN[13] = 0.0; dN[14] = 1.0;
+        return 5;
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+static double det3(const double J[3][3]) {
+    return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1])
+         - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0])
+         + J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+static void inv3(const double J[3][3], double det, double Ji[3][3]) {
+    const double d = 1.0 / det;
+    Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) * d;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * d;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * d;
+    Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) * d;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * d;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * d;
+    Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) * d;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * d;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * d;
+}
+
+/* Geometry of one element at every Gauss point:
+ *   J_ij = sum_a X_a,i dN_a/dxi_j,  W_g = w_g det J,
+ *   dN_a/dx_i = sum_j dN_a/dxi_j (J^-1)_ji.
+ * Returns 0, or -1 if some det J <= 0 (inverted / degenerate element). */
+int orc_element_geometry(int etype, const double *X /*[nen][3]*/, double *N /*[ng][nen]*/,
+                         double *dNdx /*[ng][nen][3]*/, double *W /*[ng]*/, double *detJ /*[ng]*/) {
+    double pts[3 * MAXG], w[MAXG], Nl[MAXN], dN[3 * MAXN];
+    const int ng = orc_quadrature(etype, pts, w);
+    const int nen = orc_nnode(etype);
+    if (ng == 0) return -2;
+    for (int g = 0; g < ng; ++g) {
+        orc_shape(etype, pts + 3 * g, Nl, dN);
+        double J[3][3] = {{0}};
+        for (int a = 0; a < nen; ++a)
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) J[i][j] += X[3 * a + i] * dN[3 * a + j];
+        const double d = det3(J);
+        if (detJ) detJ[g] = d;
+        if (!(d > 0.0)) return -1;
+        double Ji[3][3];
+        inv3(J, d, Ji);
+        if (W) W[g] = w[g] * d;
+        for (int a = 0; a < nen; ++a) {
+            if (N) N[g * nen + a] = Nl[a];
+            if (dNdx)
+                for (int i = 0; i < 3; ++i) {
+                    double v = 0.0;
+                    for (int j = 0; j < 3; ++j) v += dN[3 * a + j] * Ji[j][i];
+                    dNdx[(g * nen + a) * 3 + i] = v;
+                }
+        }
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Vreman (2004) eddy viscosity at one point, with G_ij = du_i/dx_j:
+ *   alpha_ij = du_j/dx_i = G_ji,
+ *   beta_ij  = Delta^2 sum_m alpha_mi alpha_mj,
+ *   B_beta   = b11 b22 - b12^2 + b11 b33 - b13^2 + b22 b33 - b23^2,
+ *   nu_t     = c sqrt(B_beta / (alpha_ij alpha_ij)),  0 if alpha:alpha == 0 or B_beta <= 0. */
+double orc_vreman(const double *G /*[3][3]*/, double delta, double c) {
+    double al[3][3], be[3][3], aa = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            al[i][j] = G[3 * j + i];
+            aa += al[i][j] * al[i][j];
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int m = 0; m < 3; ++m) s += al[m][i] * al[m][j];
+            be[i][j] = delta * delta * s;
+        }
+    const double B = be[0][0] * be[1][1] - be[0][1] * be[0][1] + be[0][0] * be[2][2] - be[0][2] * be[0][2]
+                   + be[1][1] * be[2][2] - be[1][2] * be[1][2];
+    if (aa == 0.0 || B <= 0.0) return 0.0;
+    return c * sqrt(B / aa);
+}
+
+/* ---------------------------------------------------------------------- */
+/* MLP closure.  Features from S = (G + G^T)/2 and O = (G - G^T)/2:
+ *   I1 = tr S^2, I2 = tr O^2, I3 = tr S^3, I4 = tr S O^2, I5 = tr S^2 O^2,
+ *   x_k = sign(I_k) |I_k|^(1/d_k), d = (2, 2, 3, 3, 4)   (units of a rate),
+ *   x_6 = log Delta;  inputs (x - mean) / std.                          */
+static void mat3mul(const double A[3][3], const double B[3][3], double C[3][3]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += A[i][k] * B[k][j];
+            C[i][j] = s;
+        }
+}
+
+static double tr3(const double A[3][3]) { return A[0][0] + A[1][1] + A[2][2]; }
+
+static double signed_root(double v, double d) {
+    if (v == 0.0) return 0.0;
+    return (v > 0.0 ? 1.0 : -1.0) * pow(fabs(v), 1.0 / d);
+}
+
+void orc_mlp_features(const double *G, double delta, double *x /*[6]*/) {
+    double S[3][3], O[3][3], S2[3][3], O2[3][3], S3[3][3], SO2[3][3], S2O2[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            S[i][j] = 0.5 * (G[3 * i + j] + G[3 * j + i]);
+            O[i][j] = 0.5 * (G[3 * i + j] - G[3 * j + i]);
+        }
+    mat3mul(S, S, S2);
+    mat3mul(O, O, O2);
+    mat3mul(S2, S, S3);
+    mat3mul(S, O2, SO2);
+    mat3mul(S2, O2, S2O2);
+    x[0] = signed_root(tr3(S2), 2.0);
+    x[1] = signed_root(tr3(O2), 2.0);
+    x[2] = signed_root(tr3(S3), 3.0);
+    x[3] = signed_root(tr3(SO2), 3.0);
+    x[4] = signed_root(tr3(S2O2), 4.0);
+    x[5] = log(delta);
+}
+
+static double silu(double z) { return z / (1.0 + exp(-z)); }
+static double softplus(double z) { return z > 30.0 ? z : log1p(exp(z)); }
+
+/* Forward pass for a batch of raw (un-normalised) features; y = nu_t. */
+void orc_mlp_forward(const orc_mlp *m, const double *x /*[B][6]*/, int64_t B, double *y /*[B]*/) {
+    for (int64_t b = 0; b < B; ++b) {
+        double in[MLP_IN], h1[MLP_H], h2[MLP_H], h3[MLP_H];
+        for (int k = 0; k < MLP_IN; ++k) in[k] = (x[b * MLP_IN + k] - m->feat_mean[k]) / m->feat_std[k];
+        for (int o = 0; o < MLP_H; ++o) {
+            double s = m->b1[o];
+            for (int k = 0; k < MLP_IN; ++k) s += m->w1[o * MLP_IN + k] * in[k];
+            h1[o] = silu(s);
+        }
+        for (int o = 0; o < MLP_H; ++o) {
+            double s = m->b2[o];
+            for (int k = 0; k < MLP_H; ++k) s += m->w2[o * MLP_H + k] * h1[k];
+            h2[o] = silu(s);
+        }
+        for (int o = 0; o < MLP_H; ++o) {
+            double s = m->b3[o];
+            for (int k = 0; k < MLP_H; ++k) s += m->w3[o * MLP_H + k] * h2[k];
+            h3[o] = silu(s);
+        }
+        double z = m->b4[0];
+        for (int k = 0; k < MLP_H; ++k) z += m->w4[k] * h3[k];
+        y[b] = m->out_scale * softplus(z);
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Element residual of one element (the "computation" step), FP64.
+ *   X [nen][3] coordinates, U [nen][3] velocity, P [nen] pressure (gathered).
+ *   r [nen][3] element residual (overwritten).  nut [ng] optional output.
+ * Returns 0, or -1 for det J <= 0.                                          */
+static int element_rhs(int etype, const double *X, const double *U, const double *P, const orc_params *prm,
+                       double *r, double *nut, double *vol) {
+    double N[MAXG * MAXN], dNdx[MAXG * MAXN * 3], W[MAXG];
+    const int ng = orc_ngauss(etype), nen = orc_nnode(etype);
+    if (orc_element_geometry(etype, X, N, dNdx, W, NULL) != 0) return -1;
+    double V = 0.0;
+    for (int g = 0; g < ng; ++g) V += W[g];
+    if (vol) *vol = V;
+    const double delta = cbrt(V);
+    memset(r, 0, sizeof(double) * 3 * nen);
+    for (int g = 0; g < ng; ++g) {
+        const double *Ng = N + g * nen;
+        const double *dg = dNdx + g * nen * 3;
+        double ug[3] = {0, 0, 0}, G[9] = {0}, gp[3] = {0, 0, 0};
+        for (int a = 0; a < nen; ++a) {
+            for (int i = 0; i < 3; ++i) {
+                ug[i] += Ng[a] * U[3 * a + i];
+                gp[i] += dg[3 * a + i] * P[a];
+                for (int j = 0; j < 3; ++j) G[3 * i + j] += U[3 * a + i] * dg[3 * a + j];
+            }
+        }
+        const double trG = G[0] + G[4] + G[8];
+        double eps[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) eps[i][j] = 0.5 * (G[3 * i + j] + G[3 * j + i]);
+        double nut_g = 0.0;
+        if ((prm->mask & ORC_TERM_SGS) || nut) {
+            if (prm->closure == ORC_CLOSURE_VREMAN) {
+                nut_g = orc_vreman(G, delta, prm->c_vreman);
+            } else if (prm->closure == ORC_CLOSURE_MLP && prm->mlp) {
+                double f[MLP_IN];
+                orc_mlp_features(G, delta, f);
+                orc_mlp_forward(prm->mlp, f, 1, &nut_g);
+            }
+        }
+        if (nut) nut[g] = nut_g;
+        double cvec[3] = {0, 0, 0};
+        if (prm->mask & ORC_TERM_CONV)
+            for (int i = 0; i < 3; ++i) {
+                double s = trG * ug[i];
+                for (int j = 0; j < 3; ++j) s += G[3 * i + j] * ug[j];
+                cvec[i] = s;
+            }
+        double f0[3];
+        for (int i = 0; i < 3; ++i) f0[i] = cvec[i] + ((prm->mask & ORC_TERM_PRES) ? gp[i] : 0.0);
+        double visc = 0.0;
+        if (prm->mask & ORC_TERM_VISC) visc += prm->nu;
+        if (prm->mask & ORC_TERM_SGS) visc += nut_g;
+        for (int a = 0; a < nen; ++a)
+            for (int i = 0; i < 3; ++i) {
+                double s = Ng[a] * f0[i];
+                for (int j = 0; j < 3; ++j) s += 2.0 * visc * eps[i][j] * dg[3 * a + j];
+                r[3 * a + i] -= W[g] * s;
+            }
+    }
+    return 0;
+}
+
+static void gather(const orc_mesh *m, int etype, int64_t e, const double *u, const double *p, double *X, double *U,
+                   double *P) {
+    const int nen = orc_nnode(etype);
+    const int32_t *c = m->conn[etype] + e * nen;
+    for (int a = 0; a < nen; ++a) {
+        const int64_t n = c[a];
+        for (int i = 0; i < 3; ++i) {
+            X[3 * a + i] = m->xyz[3 * n + i];
+            U[3 * a + i] = u[3 * n + i];
+        }
+        P[a] = p[n];
+    }
+}
+
+static int64_t g_bad_elem = -1;
+static int g_bad_type = -1;
+
+int64_t orc_bad_element(int *etype) {
+    if (etype) *etype = g_bad_type;
+    return g_bad_elem;
+}
+
+/* Validates connectivity indices; returns 0 or -3. */
+static int check_conn(const orc_mesh *m) {
+    for (int t = 0; t < 4; ++t) {
+        const int nen = orc_nnode(t);
+        for (int64_t k = 0; k < m->n_elem[t] * nen; ++k)
+            if (m->conn[t][k] < 0 || m->conn[t][k] >= m->n_nodes) {
+                g_bad_type = t;
+                g_bad_elem = k / nen;
+                return -3;
+            }
+    }
+    return 0;
+}
+
+/* Serial assembly in natural element order (types in order TET, PYR, PEN, HEX).
+ *   rhs [n_nodes][3] is overwritten.  nut[t] optional [n_elem][ng] per type;
+ *   vol[t] optional [n_elem] element volumes.  Returns 0, -1 (det J <= 0),
+ *   -3 (index out of range).                                              */
+int orc_assemble_rhs(const orc_mesh *m, const double *u, const double *p, const orc_params *prm, double *rhs,
+                     double **nut, double **vol) {
+    if (check_conn(m)) return -3;
+    memset(rhs, 0, sizeof(double) * 3 * m->n_nodes);
+    double X[3 * MAXN], U[3 * MAXN], P[MAXN], r[3 * MAXN];
+    for (int t = 0; t < 4; ++t) {
+        const int nen = orc_nnode(t), ng = orc_ngauss(t);
+        for (int64_t e = 0; e < m->n_elem[t]; ++e) {
+            gather(m, t, e, u, p, X, U, P);
+            double *nut_e = (nut && nut[t]) ? nut[t] + e * ng : NULL;
+            double *vol_e = (vol && vol[t]) ? vol[t] + e : NULL;
+            if (element_rhs(t, X, U, P, prm, r, nut_e, vol_e) != 0) {
+                g_bad_type = t;
+                g_bad_elem = e;
+                return -1;
+            }
+            const int32_t *c = m->conn[t] + e * nen;
+            for (int a = 0; a < nen; ++a)
+                for (int i = 0; i < 3; ++i) rhs[3 * (int64_t)c[a] + i] += r[3 * a + i];
+        }
+    }
+    return 0;
+}
+
+/* The same assembly with OpenMP threads over elements, per-thread private
+ * RHS arrays and a final reduction (timed CPU baseline). */
+int orc_assemble_rhs_omp(const orc_mesh *m, const double *u, const double *p, const orc_params *prm, double *rhs,
+                         int nthreads) {
+    if (check_conn(m)) return -3;
+    const int64_t n3 = 3 * m->n_nodes;
+    int status = 0;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#else
+    nthreads = 1;
+#endif
+    double *priv = (double *)calloc((size_t)nthreads * (size_t)n3, sizeof(double));
+    if (!priv) return -4;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads)
+#endif
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *mine = priv + (size_t)tid * (size_t)n3;
+        double X[3 * MAXN], U[3 * MAXN], P[MAXN], r[3 * MAXN];
+        for (int t = 0; t < 4; ++t) {
+            const int nen = orc_nnode(t);
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+            for (int64_t e = 0; e < m->n_elem[t]; ++e) {
+                gather(m, t, e, u, p, X, U, P);
+                if (element_rhs(t, X, U, P, prm, r, NULL, NULL) != 0) {
+                    status = -1;
+                    continue;
+                }
+                const int32_t *c = m->conn[t] + e * nen;
+                for (int a = 0; a < nen; ++a)
+                    for (int i = 0; i < 3; ++i) mine[3 * (int64_t)c[a] + i] += r[3 * a + i];
+            }
+        }
+    }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+#endif
+    for (int64_t k = 0; k < n3; ++k) {
+        double s = 0.0;
+        for (int th = 0; th < nthreads; ++th) s += priv[(size_t)th * (size_t)n3 + k];
+        rhs[k] = s;
+    }
+    free(priv);
+    return status;
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Lumped mass M_a = sum_e sum_g W_g N_a(g): the row sum of the element mass
+ * matrix Ae_ab = sum_g J w N_a N_b of the section 2.3.3 listing. */
+int orc_lumped_mass(const orc_mesh *m, double *mass) {
+    if (check_conn(m)) return -3;
+    memset(mass, 0, sizeof(double) * m->n_nodes);
+    double X[3 * MAXN], N[MAXG * MAXN], W[MAXG];
+    for (int t = 0; t < 4; ++t) {
+        const int nen = orc_nnode(t), ng = orc_ngauss(t);
+        for (int64_t e = 0; e < m->n_elem[t]; ++e) {
+            const int32_t *c = m->conn[t] + e * nen;
+            for (int a = 0; a < nen; ++a)
+                for (int i = 0; i < 3; ++i) X[3 * a + i] = m->xyz[3 * (int64_t)c[a] + i];
+            if (orc_element_geometry(t, X, N, NULL, W, NULL) != 0) {
+                g_bad_type = t;
+                g_bad_elem = e;
+                return -1;
+            }
+            for (int a = 0; a < nen; ++a) {
+                double s = 0.0;
+                for (int b = 0; b < nen; ++b)
+                    for (int g = 0; g < ng; ++g) s += W[g] * N[g * nen + a] * N[g * nen + b];
+                mass[c[a]] += s;
+            }
+        }
+    }
+    return 0;
+}
+
+/* Consistent element mass matrix Ae_ab (listing of section 2.3.3), one element. */
+int orc_element_mass(int etype, const double *X, double *Ae /*[nen][nen]*/) {
+    double N[MAXG * MAXN], W[MAXG];
+    const int nen = orc_nnode(etype), ng = orc_ngauss(etype);
+    if (orc_element_geometry(etype, X, N, NULL, W, NULL) != 0) return -1;
+    for (int a = 0; a < nen; ++a)
+        for (int b = 0; b < nen; ++b) {
+            double s = 0.0;
+            for (int g = 0; g < ng; ++g) s += W[g] * N[g * nen + a] * N[g * nen + b];
+            Ae[a * nen + b] = s;
+        }
+    return 0;
+}
+
+/* Periodic fold of a nodal array with ncomp components per node:
+ * every slave's value is added to its master, then copied back. */
+void orc_periodic_fold(int64_t n, const int32_t *master, double *v, int ncomp) {
+    for (int64_t i = 0; i < n; ++i)
+        if (master[i] != i)
+            for (int c = 0; c < ncomp; ++c) v[(int64_t)master[i] * ncomp + c] += v[i * ncomp + c];
+    for (int64_t i = 0; i < n; ++i)
+        if (master[i] != i)
+            for (int c = 0; c < ncomp; ++c) v[i * ncomp + c] = v[(int64_t)master[i] * ncomp + c];
+}
+
+/* One stage of the three-stage SSP Runge-Kutta momentum update (Shu-Osher):
+ *   u^(k+1) = a_k u^n + b_k (u^(k) + dt M^-1 R(u^(k), p^n)),
+ *   (a, b) = (0, 1), (3/4, 1/4), (1/3, 2/3);
+ * R is folded over periodic pairs, M is the folded lumped mass, and nodes
+ * with dirichlet != 0 keep u^n.  uk_out may alias uk.                      */
+int orc_rk_stage(const orc_mesh *m, const int32_t *master, const uint8_t *dirichlet, const double *mass_folded,
+                 const double *un, const double *uk, const double *p, const orc_params *prm, int stage, double dt,
+                 double *uk_out) {
+    static const double A[3] = {0.0, 0.75, 1.0 / 3.0};
+    static const double Bc[3] = {1.0, 0.25, 2.0 / 3.0};
+    if (stage < 0 || stage > 2) return -2;
+    const int64_t n = m->n_nodes;
+    double *R = (double *)malloc(sizeof(double) * 3 * n);
+    if (!R) return -4;
+    int st = orc_assemble_rhs(m, uk, p, prm, R, NULL, NULL);
+    if (st) {
+        free(R);
+        return st;
+    }
+    if (master) orc_periodic_fold(n, master, R, 3);
+    for (int64_t i = 0; i < n; ++i)
+        for (int c = 0; c < 3; ++c) {
+            const int64_t k = 3 * i + c;
+            if (dirichlet && dirichlet[i])
+                uk_out[k] = un[k];
+            else
+                uk_out[k] = A[stage] * un[k] + Bc[stage] * (uk[k] + dt * R[k] / mass_folded[i]);
+        }
+    free(R);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* MLP training pieces (FP64): loss and gradient by reverse-mode chain rule,
+ * and one Adam step.  Parameter vector layout (8,833 values):
+ *   w1[64][6] b1[64] w2[64][64] b2[64] w3[64][64] b3[64] w4[64] b4[1].
+ * Inputs x are already normalised; target y and prediction are in units of
+ * out_scale (pred = softplus(z)).  loss = mean_b (pred_b - y_b)^2.         */
+#define MLP_NPARAM (MLP_H * MLP_IN + MLP_H + 2 * (MLP_H * MLP_H + MLP_H) + MLP_H + 1)
+
+int orc_mlp_nparam(void) { return MLP_NPARAM; }
+
+static double sigm(double z) { return 1.0 / (1.0 + exp(-z)); }
+
+double orc_mlp_loss_grad(const double *theta, const double *x /*[B][6]*/, const double *y, int64_t B,
+                         double *grad /*[NPARAM] or NULL*/) {
+    const double *w1 = theta, *b1 = w1 + MLP_H * MLP_IN;
+    const double *w2 = b1 + MLP_H, *b2 = w2 + MLP_H * MLP_H;
+    const double *w3 = b2 + MLP_H, *b3 = w3 + MLP_H * MLP_H;
+    const double *w4 = b3 + MLP_H, *b4 = w4 + MLP_H;
+    double *gw1 = grad, *gb1 = grad ? gw1 + MLP_H * MLP_IN : NULL;
+    double *gw2 = grad ? gb1 + MLP_H : NULL, *gb2 = grad ? gw2 + MLP_H * MLP_H : NULL;
+    double *gw3 = grad ? gb2 + MLP_H : NULL, *gb3 = grad ? gw3 + MLP_H * MLP_H : NULL;
+    double *gw4 = grad ? gb3 + MLP_H : NULL, *gb4 = grad ? gw4 + MLP_H : NULL;
+    if (grad) memset(grad, 0, sizeof(double) * MLP_NPARAM);
+    double loss = 0.0;
+    for (int64_t b = 0; b < B; ++b) {
+        const double *in = x + b * MLP_IN;
+        double z1[MLP_H], h1[MLP_H], z2[MLP_H], h2[MLP_H], z3[MLP_H], h3[MLP_H];
+        for (int o = 0; o < MLP_H; ++o) {
+            double s = b1[o];
+            for (int k = 0; k < MLP_IN; ++k) s += w1[o * MLP_IN + k] * in[k];
+            z1[o] = s; h1[o] = silu(s);
+        }
+        for (int o = 0; o < MLP_H; ++o) {
+            double s = b2[o];
+            for (int k = 0; k < MLP_H; ++k) s += w2[o * MLP_H + k] * h1[k];
+            z2[o] = s; h2[o] = silu(s);
+        }
+        for (int o = 0; o < MLP_H; ++o) {
+            double s = b3[o];
+            for (int k = 0; k < MLP_H; ++k) s += w3[o * MLP_H + k] * h2[k];
+            z3[o] = s; h3[o] = silu(s);
+        }
+        double z4 = b4[0];
+        for (int k = 0; k < MLP_H; ++k) z4 += w4[k] * h3[k];
+        const double pred = softplus(z4);
+        const double diff = pred - y[b];
+        loss += diff * diff;
+        if (!grad) continue;
+        /* d loss_b / d z4 = 2 diff / B * softplus'(z4) */
+        const double dz4 = 2.0 * diff / (double)B * sigm(z4);
+        double dh3[MLP_H], dz3[MLP_H], dh2[MLP_H], dz2[MLP_H], dh1[MLP_H], dz1[MLP_H];
+        gb4[0] += dz4;
+        for (int k = 0; k < MLP_H; ++k) {
+            gw4[k] += dz4 * h3[k];
+            dh3[k] = dz4 * w4[k];
+        }
+        /* silu'(z) = s(z) (1 + z (1 - s(z))) */
+        for (int o = 0; o < MLP_H; ++o) {
+            const double s = sigm(z3[o]);
+            dz3[o] = dh3[o] * s * (1.0 + z3[o] * (1.0 - s));
+        }
+        for (int k = 0; k < MLP_H; ++k) dh2[k] = 0.0;
+        for (int o = 0; o < MLP_H; ++o) {
+            gb3[o] += dz3[o];
+            for (int k = 0; k < MLP_H; ++k) {
+                gw3[o * MLP_H + k] += dz3[o] * h2[k];
+                dh2[k] += dz3[o] * w3[o * MLP_H + k];
+            }
+        }
+        for (int o = 0; o < MLP_H; ++o) {
+            const double s = sigm(z2[o]);
+            dz2[o] = dh2[o] * s * (1.0 + z2[o] * (1.0 - s));
+        }
+        for (int k = 0; k < MLP_H; ++k) dh1[k] = 0.0;
+        for (int o = 0; o < MLP_H; ++o) {
+            gb2[o] += dz2[o];
+            for (int k = 0; k < MLP_H; ++k) {
+                gw2[o * MLP_H + k] += dz2[o] * h1[k];
+                dh1[k] += dz2[o] * w2[o * MLP_H + k];
+            }
+        }
+        for (int o = 0; o < MLP_H; ++o) {
+            const double s = sigm(z1[o]);
+            dz1[o] = dh1[o] * s * (1.0 + z1[o] * (1.0 - s));
+        }
+        for (int o = 0; o < MLP_H; ++o) {
+            gb1[o] += dz1[o];
+            for (int k = 0; k < MLP_IN; ++k) gw1[o * MLP_IN + k] += dz1[o] * in[k];
+        }
+    }
+    return loss / (double)B;
+}
+
+/* One Adam step (Kingma & Ba 2015) with bias correction; step counter t >= 1. */
+void orc_adam_step(double *theta, const double *grad, double *m1, double *m2, int64_t n, double lr, double beta1,
+                   double beta2, double eps, int64_t t) {
+    const double c1 = 1.0 - pow(beta1, (double)t), c2 = 1.0 - pow(beta2, (double)t);
+    for (int64_t k = 0; k < n; ++k) {
+        m1[k] = beta1 * m1[k] + (1.0 - beta1) * grad[k];
+        m2[k] = beta2 * m2[k] + (1.0 - beta2) * grad[k] * grad[k];
+        theta[k] -= lr * (m1[k] / c1) / (sqrt(m2[k] / c2) + eps);
+    }
+}
