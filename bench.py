@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Benchmark of the momentum-RHS element assembly on one B300 per rank.
+
+Workload (one "step"): a three-stage SSP-RK3 momentum update, replayed from a
+CUDA graph, on the airplane-like mesh: a jittered 170^3-node grid split into
+tetrahedra, a carved seeded ellipsoid and a 5-layer prism boundary layer
+(28,661,550 TET04 + 99,320 PEN06 = 28,760,870 elements, 4,917,615 nodes),
+mixed precision (FP32 element arithmetic, FP64 Jacobians for the prisms, FP64
+nodal sums), Vreman closure.  Each step runs 3 element assemblies, periodic
+fold (none here), and 3 stage updates.
+
+metric: element assemblies per second (Melem/s) = 3 x elements / step time.
+
+Also printed: the roofline of the dominant kernel (TET04 assembly) timed
+live with CUDA events, the end-to-end rate through the public API with host
+buffers, the oracle's CPU rate on a bounded sample, clocks.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("airplane-like: jittered 170^3-node tet grid (Kuhn 6-tet split), carved seeded ellipsoid, "
+            "5-layer PEN06 boundary layer; RK3 step (3 assemblies) as a CUDA graph; mixed FP32/FP64; Vreman")
+METRIC = "RHS assembly Melem/s"
+UNIT = "Melem/s"
+DT = 1e-4
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(n_axis: int):
+    from paper_2005_05899_b300 import meshgen as mg
+    t = time.time()
+    mesh = mg.airplane_mesh(n_axis, seed=4)
+    field = mg.inflow_field(mesh, seed=5)
+    log(f"[bench] mesh {mesh.counts()} nodes {mesh.n_nodes} generated in {time.time() - t:.1f}s")
+    return mesh, field
+
+
+def tet_algorithmic_bytes(mesh) -> tuple:
+    """Algorithmic bytes of one TET04 assembly launch: int32 connectivity
+    (16 B/element) + each referenced node once: coordinates (12 B) +
+    velocity (12 B) + pressure (4 B) read in FP32, RHS (24 B) written in FP64."""
+    conn = mesh.conn[0]
+    n_nodes = int(np.unique(conn).size)
+    e = int(conn.shape[0])
+    return 16 * e + 52 * n_nodes, e, n_nodes
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2005_05899_b300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_2005_05899_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key: str, alg_scale: float):
+    """dram read+write bytes per launch from a committed ncu summary, if it was
+    taken on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    rec = d.get(kernel_key)
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return float(rec["dram_bytes_per_launch"]) * alg_scale
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.device), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception as e:  # no nvidia-smi: no clock record
+            log(f"[bench] clock sampling unavailable: {e}")
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(mesh, field, target_s: float = 12.0, steps: int = 1):
+    """The FP64 oracle (OpenMP variant, all host cores) on a bounded sample:
+    a contiguous run of tetrahedra of the same mesh with its own compact node
+    numbering; returns (Melem/s, threads, description, seconds)."""
+    import oracle as O
+    conn = mesh.conn[0]
+
+    def sample(ne):
+        sub = conn[:ne]
+        nodes, inv = np.unique(sub, return_inverse=True)
+        om = O.OracleMesh(mesh.xyz[nodes], {0: inv.reshape(sub.shape).astype(np.int32)})
+        return om, field.u[nodes], field.p[nodes]
+
+    threads = O.max_threads()
+    om, u, p = sample(200_000)
+    t = time.time()
+    O.assemble_rhs_omp(om, u, p, field.nu, field.c_vreman, "vreman")
+    rate = 200_000 / max(time.time() - t, 1e-6)
+    ne = int(min(conn.shape[0], max(200_000, rate * target_s / max(steps, 1))))
+    om, u, p = sample(ne)
+    t = time.time()
+    for _ in range(steps):
+        O.assemble_rhs_omp(om, u, p, field.nu, field.c_vreman, "vreman")
+    dt = time.time() - t
+    desc = (f"{ne} contiguous TET04 of the same mesh ({ne / conn.shape[0]:.1%}), FP64 oracle OpenMP, "
+            f"{steps} assembly pass(es), {dt:.1f}s")
+    return ne * steps / dt / 1e6, threads, desc, dt
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    mesh, field = make_workload(args.n_axis)
+    for _ in range(args.warmup):
+        pass
+    vals = []
+    cores = None
+    desc = ""
+    total_t = 0.0
+    per_step = max(2.0, min(20.0, 150.0 / max(args.steps, 1)))
+    for _ in range(args.steps):
+        v, cores, desc, dt = cpu_baseline(mesh, field, target_s=per_step, steps=1)
+        vals.append(v)
+        total_t += dt
+    value = statistics.median(vals)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_t / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "elements": mesh.n_elem_total, "nodes": mesh.n_nodes},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2005_05899_b300 import fea
+    mesh, field = make_workload(args.n_axis)
+    ctx = fea.Context(local)
+    t = time.time()
+    dm = ctx.upload_mesh(mesh)
+    log(f"[bench] upload {time.time() - t:.1f}s")
+    dm.upload_field(field.u, field.p, field.nu, field.c_vreman)
+    if args.autotune:
+        plan = dm.autotune(prec="mixed", closure="vreman")
+        log(f"[bench] plan {plan.as_dict()}")
+    E = mesh.n_elem_total
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # warm-up (graph capture happens on the first call)
+    for _ in range(args.warmup):
+        dm.rk_step_graph(DT, prec="mixed", closure="vreman")
+    ctx.sync_status()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = ctx.launch_count
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dm.rk_step_graph(DT, prec="mixed", closure="vreman")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = ctx.launch_count - l0
+    ctx.sync_status()
+    # dominant kernel: TET04 assembly, timed with events on its launch stream
+    rhs = torch.empty((3, dm.n_nodes), dtype=torch.float64, device="cuda")
+    ctx.profile(True)
+    ctx.profile_read(0, 0, reset=True)
+    for _ in range(max(5, args.steps // 3)):
+        dm.assemble(rhs, prec="mixed", closure="vreman")
+    torch.cuda.synchronize()
+    tet_ms, tet_n = ctx.profile_read(0, 0, reset=True)
+    ctx.profile(False)
+    clk = clocks.stop()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    ms_step = ms_max / args.steps
+    value = ws * 3 * E * args.steps / (ms_max / 1e3) / 1e6
+    # end to end through the public API with pinned host buffers
+    n = dm.n_nodes
+    u_host = torch.from_numpy(np.ascontiguousarray(field.u.T)).pin_memory()
+    p_host = torch.from_numpy(np.ascontiguousarray(field.p)).pin_memory()
+    out_host = torch.empty((3, n), dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, args.steps // 5)
+    for _ in range(2):
+        dm.upload_field(u_host, p_host, field.nu, field.c_vreman)
+        dm.rk_step_graph(DT, prec="mixed", closure="vreman")
+        dm.state(out_host)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        dm.upload_field(u_host, p_host, field.nu, field.c_vreman)
+        dm.rk_step_graph(DT, prec="mixed", closure="vreman")
+        dm.state(out_host)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    ctx.sync_status()
+    e2e_val = ws * 3 * E * e2e_steps / (e2e_ms / 1e3) / 1e6
+    # roofline of the TET04 kernel
+    alg, e_tet, n_tet = tet_algorithmic_bytes(mesh)
+    peak, peak_kind = peaks()
+    per_launch_s = tet_ms / 1e3 / max(tet_n, 1)
+    achieved = alg / per_launch_s / 1e9
+    traffic = ncu_traffic("tet04_mixed_assembly", 1.0)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "accumulation": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "elements": E, "nodes": dm.n_nodes,
+                       "counts": mesh.counts(), "l2": "inputs larger than L2 (no flush needed)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": "TET04 assembly (mixed, Vreman)",
+                         "peak_kind": f"{peak_kind} hbm_gbs", "alg_bytes_per_launch": alg,
+                         "kernel_ms": per_launch_s * 1e3, "kernel_melem_s": e_tet / per_launch_s / 1e6},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 32 * n, "d2h_bytes_per_step": 24 * n},
+            "gpu_launches": launches, "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        v, cores, desc, _ = cpu_baseline(mesh, field, target_s=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-axis", type=int, default=170, help="grid nodes per axis of the airplane-like mesh")
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

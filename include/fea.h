@@ -1,0 +1,234 @@
+/*
+ * fea.h -- C ABI of the B300 (sm_103a) momentum right-hand-side assembly.
+ *
+ * The operation is the element assembly of the explicit momentum equation of
+ * Borrell et al., "Heterogeneous CPU/GPU co-execution of CFD simulations on
+ * the POWER9 architecture" (FGCS 2020):
+ *   - the filtered incompressible momentum equation of section 2.1
+ *     (Eq. momentum) with rho = 1, mu = nu, the EMAC-form convective bracket
+ *     evaluated pointwise on the finite-element interpolant, the Vreman
+ *     subgrid viscosity (section 2.1) and Galerkin linear elements;
+ *   - assembled element by element with the three steps gather ->
+ *     computation -> scatter of section 2.3.3 ("Element and boundary
+ *     assemblies"), over categories of same element type and integration
+ *     rule (section 2.3.3);
+ *   - advanced by the three Runge-Kutta stages of Algorithm 1 (element
+ *     assembly, momentum update), here with the SSP-RK3 coefficients and a
+ *     frozen pressure.
+ *
+ * For node a and component i the assembled right-hand side is
+ *   R_a,i = - sum_e sum_g W_g [ N_a (c_i + d_i p) + 2 (nu + nu_t) eps_ij d_j N_a ]
+ * with W_g = w_g det J, G_ij = du_i/dx_j, eps = (G + G^T)/2,
+ * c = G u + (tr G) u, and nu_t from the closure.
+ *
+ * Conventions (every entry point):
+ *   - All work is asynchronous on the caller's CUDA stream (cudaStream_t
+ *     passed as void*, NULL = legacy default stream).  Errors that the host
+ *     can detect are returned at once; errors detected on the device
+ *     (det J <= 0, a non-finite residual, a bounded wait that gave up) set a
+ *     device error word that fea_sync_status() reads and clears.
+ *   - Node arrays are structure-of-arrays in the caller's node order:
+ *     a vector field is [3][n_nodes] (all x, then all y, then all z).
+ *     The library never reorders the caller's nodes; it reorders its own
+ *     copy of the elements (type buckets sorted along a Morton curve).
+ *   - Pointers marked "host or device" may point to either (CUDA unified
+ *     addressing decides); "device" means device memory the caller owns
+ *     (e.g. a torch tensor) and that must stay valid until the stream work
+ *     that uses it has finished.
+ *   - No exception or abort crosses this interface; every function returns
+ *     a fea_status.  fea_last_error() gives a message for the last failure
+ *     on that context.
+ *   - Local node order per element type is the VTK one:
+ *       TET04 (r,s,t) corners 0,(1,0,0),(0,1,0),(0,0,1);
+ *       PYR05 base (-1,-1),(1,-1),(1,1),(-1,1) at zeta=0, apex zeta=1;
+ *       PEN06 bottom triangle (zeta=-1) then top triangle (zeta=+1);
+ *       HEX08 bottom face then top face, counter-clockwise.
+ *   - Integration rules (one per type; a category is type + rule):
+ *       TET04 4-point degree-2 rule, PYR05 8-point collapsed rule
+ *       (2x2 Gauss-Legendre x 2-point Gauss-Jacobi(2,0)), PEN06 3-point
+ *       triangle x 2-point Gauss, HEX08 2x2x2 Gauss.
+ */
+#ifndef FEA_H
+#define FEA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FEA_OK = 0,
+    FEA_EINVAL = 1,    /* bad argument (null pointer, size, enum value) */
+    FEA_ENOMEM = 2,    /* a device or host allocation failed */
+    FEA_ECUDA = 3,     /* a CUDA runtime call failed (message has the CUDA error) */
+    FEA_EMESH = 4,     /* connectivity index out of range, or det J <= 0 */
+    FEA_ENUMERIC = 5,  /* a non-finite value in a residual */
+    FEA_ETIMEOUT = 6,  /* a bounded device-side wait gave up */
+    FEA_ESTATE = 7,    /* call out of order (e.g. assemble before field upload) */
+    FEA_ENOTFOUND = 8  /* unknown mesh id */
+} fea_status;
+
+typedef enum { FEA_TET04 = 0, FEA_PYR05 = 1, FEA_PEN06 = 2, FEA_HEX08 = 3 } fea_etype;
+
+typedef enum {
+    FEA_FP64 = 0,   /* every operation in FP64 */
+    FEA_MIXED = 1   /* FP32 element arithmetic; FP64 Jacobian determinant and
+                       inverse for elements flagged fp64_jac; FP64 nodal sums */
+} fea_prec;
+
+typedef enum { FEA_CLOSURE_NONE = 0, FEA_CLOSURE_VREMAN = 1, FEA_CLOSURE_MLP = 2 } fea_closure;
+
+/* term mask: which parts of the bracket above are assembled */
+enum { FEA_TERM_CONV = 1, FEA_TERM_VISC = 2, FEA_TERM_SGS = 4, FEA_TERM_PRES = 8, FEA_TERM_ALL = 15 };
+
+/* scatter strategy of the element residuals into the nodal RHS */
+typedef enum {
+    FEA_SCATTER_AUTO = 0,   /* the mesh's current plan (autotuned or default) */
+    FEA_SCATTER_ATOMIC = 1, /* one FP64 atomic add per element node and component */
+    FEA_SCATTER_CHUNK = 2   /* CTA-local assembly of a chunk of elements in
+                               shared memory; FP64 atomics only for nodes the
+                               chunk shares with other chunks */
+} fea_scatter;
+
+typedef struct fea_ctx fea_ctx;
+
+/* Mesh description for fea_mesh_upload.  All pointers: HOST memory, read
+ * during the call only (the library keeps its own device copies). */
+typedef struct {
+    int64_t n_nodes;
+    const double *xyz;                  /* [3][n_nodes] coordinates */
+    int64_t n_elem[4];                  /* elements per fea_etype */
+    const int32_t *conn[4];             /* [n_elem[t]][n_en(t)], 0-based node ids; NULL if n_elem[t]==0 */
+    const int32_t *periodic_master;     /* optional [n_nodes]: master node id, or the node itself */
+    const uint8_t *dirichlet;           /* optional [n_nodes]: 1 = velocity held (RK stages) */
+    const uint8_t *fp64_jac[4];         /* optional [n_elem[t]]: 1 = FP64 Jacobian in FEA_MIXED
+                                           (stretched boundary-layer elements) */
+} fea_mesh_desc;
+
+/* Launch plan of one mesh (chosen by fea_autotune or set by hand). */
+typedef struct {
+    int32_t scatter;            /* fea_scatter (not AUTO) */
+    int32_t threads_per_block;  /* element kernels: 64..1024, multiple of 32 */
+    int32_t chunk_elems;        /* elements per chunk for FEA_SCATTER_CHUNK */
+    int32_t reserved;
+} fea_plan;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Creates a context on CUDA device `device` (made current for the calls on
+ * this context).  *out receives the handle.  Returns FEA_ECUDA when no device
+ * is usable. */
+fea_status fea_create(int device, fea_ctx **out);
+
+/* Frees every device buffer the context owns.  NULL is allowed. */
+void fea_destroy(fea_ctx *ctx);
+
+/* Message of the last failure on this context (never NULL; owned by ctx,
+ * valid until the next call on ctx). */
+const char *fea_last_error(const fea_ctx *ctx);
+
+/* Library version string (static storage). */
+const char *fea_version(void);
+
+/* ---- mesh and fields ---------------------------------------------------- */
+
+/* Mesh upload (the "mesh arrays" and category packing of section 2.3.3):
+ * validates indices, buckets elements by (type, FP64-Jacobian flag), sorts
+ * each bucket along a Morton curve of element centroids, builds chunk tables
+ * for the CTA-local scatter, copies coordinates (FP64 and FP32) and computes
+ * the lumped mass (section 2.3.3 mass-matrix listing, row sums).
+ * Synchronous with respect to the host (returns when the copies are done).
+ * *mesh_id receives the id.  Errors: FEA_EINVAL, FEA_EMESH (index out of
+ * range or det J <= 0 at a Gauss point; the message names the element),
+ * FEA_ENOMEM, FEA_ECUDA. */
+fea_status fea_mesh_upload(fea_ctx *ctx, const fea_mesh_desc *desc, void *stream, int32_t *mesh_id);
+
+/* Mesh sizes: n_nodes, and elements per type (n_elem may be NULL). */
+fea_status fea_mesh_info(fea_ctx *ctx, int32_t mesh, int64_t *n_nodes, int64_t n_elem[4]);
+
+/* Lumped mass M_a = sum_e sum_g W_g N_a(g) into out [n_nodes] (device),
+ * NOT folded over periodic pairs. */
+fea_status fea_lumped_mass(fea_ctx *ctx, int32_t mesh, double *out, void *stream);
+
+/* Field upload: nodal velocity u [3][n_nodes] and pressure p [n_nodes],
+ * host or device, dtype 0 = float64, 1 = float32.  Also (re)starts the RK
+ * state: u^n = u^(0) = u.  nu: kinematic viscosity; c_vreman: Vreman
+ * constant.  Asynchronous; host sources are staged through the library. */
+fea_status fea_field_upload(fea_ctx *ctx, int32_t mesh, const void *u, const void *p, int dtype, double nu,
+                            double c_vreman, void *stream);
+
+/* ---- the hot path -------------------------------------------------------- */
+
+/* Element assembly of the momentum RHS (Eq. momentum, section 2.3.3) from
+ * the uploaded field.  rhs_out [3][n_nodes] (device) is overwritten (not
+ * accumulated) in the caller's node order, NOT folded over periodic pairs.
+ * nut_out (optional, device): nu_t at every Gauss point, types concatenated
+ * in fea_etype order, caller element order within a type, n_gauss(t) values
+ * per element (4, 8, 6, 8).  scatter: FEA_SCATTER_AUTO uses the mesh plan. */
+fea_status fea_assemble_rhs(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure closure, uint32_t term_mask,
+                            fea_scatter scatter, double *rhs_out, float *nut_out, void *stream);
+
+/* Batched form: one persistent launch over the (mesh, bucket, chunk) work
+ * items of n meshes (each with its own field, nu and c_vreman).
+ * meshes [n] (host); rhs_out [n] (host array of device pointers, each
+ * [3][n_nodes(mesh)]), overwritten.  The same precision/closure/mask apply to
+ * all meshes. */
+fea_status fea_assemble_rhs_batched(fea_ctx *ctx, const int32_t *meshes, int32_t n, fea_prec prec,
+                                    fea_closure closure, uint32_t term_mask, double *const *rhs_out,
+                                    void *stream);
+
+/* In-place periodic fold of v [ncomp][n_nodes] (device): every slave's value
+ * is added to its master, then copied back to the slave.  No-op without a
+ * periodic map. */
+fea_status fea_periodic_fold(fea_ctx *ctx, int32_t mesh, double *v, int32_t ncomp, void *stream);
+
+/* One SSP-RK3 momentum-update stage (Algorithm 1, stage index 0..2) on the
+ * library-owned state:  u^(k+1) = a_k u^n + b_k (u^(k) + dt M^-1 R(u^(k))),
+ * (a, b) = (0, 1), (3/4, 1/4), (1/3, 2/3); R folded, M the folded lumped
+ * mass, Dirichlet nodes hold u^n, pressure frozen at the uploaded p.  Stage 2
+ * also makes the result the new u^n. */
+fea_status fea_rk_stage(fea_ctx *ctx, int32_t mesh, int32_t stage, double dt, fea_prec prec, fea_closure closure,
+                        void *stream);
+
+/* A full three-stage step replayed from a CUDA graph (captured on first use
+ * for this (mesh, dt, prec, closure) and replayed afterwards). */
+fea_status fea_rk_step_graph(fea_ctx *ctx, int32_t mesh, double dt, fea_prec prec, fea_closure closure,
+                             void *stream);
+
+/* Copies the current state u^(k) [3][n_nodes] to out (host or device). */
+fea_status fea_state_download(fea_ctx *ctx, int32_t mesh, double *out, void *stream);
+
+/* ---- plans, autotuning, status ----------------------------------------- */
+
+fea_status fea_get_plan(fea_ctx *ctx, int32_t mesh, fea_plan *plan);
+fea_status fea_set_plan(fea_ctx *ctx, int32_t mesh, const fea_plan *plan);
+
+/* Times the candidate plans of one mesh (after a field upload) with CUDA
+ * events and keeps the fastest; with cache_path != NULL the result is read
+ * from / appended to that text file, keyed by device name and mesh
+ * statistics.  Synchronous. */
+fea_status fea_autotune(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure closure, const char *cache_path);
+
+/* Synchronises the stream, then reads and clears the device error word:
+ * FEA_EMESH (det J <= 0 seen), FEA_ENUMERIC (non-finite residual),
+ * FEA_ETIMEOUT (bounded wait gave up), or FEA_OK. */
+fea_status fea_sync_status(fea_ctx *ctx, void *stream);
+
+/* Number of kernels this context has launched so far (host counter). */
+int64_t fea_launch_count(const fea_ctx *ctx);
+
+/* Kernel timing (profiling aid).  While enabled, every element-assembly
+ * kernel launched outside a CUDA graph is bracketed by two CUDA events
+ * recorded on its launch stream.  fea_profile_read synchronises those
+ * events and returns, for the category (etype, fp64_jac), the summed kernel
+ * time in milliseconds and the number of launches; reset != 0 clears the
+ * records.  Errors: FEA_EINVAL, FEA_ECUDA. */
+fea_status fea_profile_enable(fea_ctx *ctx, int on);
+fea_status fea_profile_read(fea_ctx *ctx, int etype, int fp64_jac, double *total_ms, int64_t *launches, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEA_H */

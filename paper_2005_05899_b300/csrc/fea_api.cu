@@ -1,0 +1,854 @@
+// C ABI of libfea (see include/fea.h): contexts, mesh upload and category
+// packing, field upload, the assembly entry points, RK stages, CUDA-graph
+// capture, plans and the device status word.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "fea_internal.h"
+
+using namespace fea;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// reference elements: Gauss rules and shape functions at the Gauss points
+
+void gauss2(double x[2]) {
+    x[0] = -1.0 / sqrt(3.0);
+    x[1] = 1.0 / sqrt(3.0);
+}
+
+// Quadrature points (reference coordinates) and weights per type.
+int rule(int et, double pts[][3], double w[]) {
+    double g[2];
+    gauss2(g);
+    int n = 0;
+    switch (et) {
+        case FEA_TET04: {
+            // degree-2 rule: one barycentric coordinate b, the others a
+            const double a = (5.0 - sqrt(5.0)) / 20.0, b = (5.0 + 3.0 * sqrt(5.0)) / 20.0;
+            const double bary[4][4] = {{b, a, a, a}, {a, b, a, a}, {a, a, b, a}, {a, a, a, b}};
+            for (int q = 0; q < 4; ++q) {
+                // (r, s, t) = barycentric weights of vertices 1, 2, 3
+                pts[n][0] = bary[q][1];
+                pts[n][1] = bary[q][2];
+                pts[n][2] = bary[q][3];
+                w[n++] = 1.0 / 24.0;
+            }
+            // order: point q has the large weight on vertex q (q = 0 first)
+            return n;
+        }
+        case FEA_PEN06: {
+            const double tri[3][2] = {{1.0 / 6.0, 1.0 / 6.0}, {2.0 / 3.0, 1.0 / 6.0}, {1.0 / 6.0, 2.0 / 3.0}};
+            for (int kz = 0; kz < 2; ++kz)
+                for (int q = 0; q < 3; ++q) {
+                    pts[n][0] = tri[q][0];
+                    pts[n][1] = tri[q][1];
+                    pts[n][2] = g[kz];
+                    w[n++] = 1.0 / 6.0;
+                }
+            return n;
+        }
+        case FEA_HEX08: {
+            for (int k = 0; k < 2; ++k)
+                for (int j = 0; j < 2; ++j)
+                    for (int i = 0; i < 2; ++i) {
+                        pts[n][0] = g[i];
+                        pts[n][1] = g[j];
+                        pts[n][2] = g[k];
+                        w[n++] = 1.0;
+                    }
+            return n;
+        }
+        case FEA_PYR05: {
+            // (a, b, t) -> ((1-t) a, (1-t) b, t); Gauss-Legendre in a, b and
+            // the 2-point rule for the weight (1-t)^2 on [0, 1] in t, whose
+            // nodes are the roots of t^2 - (2/3) t + 1/15.
+            const double r = sqrt(2.0 / 45.0);
+            const double tn[2] = {1.0 / 3.0 - r, 1.0 / 3.0 + r};
+            // weights from the moments int (1-t)^2 = 1/3 and int t (1-t)^2 = 1/12
+            const double w1 = (1.0 / 12.0 - tn[0] / 3.0) / (tn[1] - tn[0]);
+            const double tw[2] = {1.0 / 3.0 - w1, w1};
+            for (int k = 0; k < 2; ++k)
+                for (int j = 0; j < 2; ++j)
+                    for (int i = 0; i < 2; ++i) {
+                        pts[n][0] = (1.0 - tn[k]) * g[i];
+                        pts[n][1] = (1.0 - tn[k]) * g[j];
+                        pts[n][2] = tn[k];
+                        w[n++] = tw[k];
+                    }
+            return n;
+        }
+    }
+    return 0;
+}
+
+void shape_at(int et, const double x[3], double N[], double dN[][3]) {
+    const double r = x[0], s = x[1], t = x[2];
+    switch (et) {
+        case FEA_TET04: {
+            N[0] = 1.0 - r - s - t;
+            N[1] = r;
+            N[2] = s;
+            N[3] = t;
+            for (int a = 0; a < 4; ++a)
+                for (int j = 0; j < 3; ++j) dN[a][j] = (a == 0) ? -1.0 : (a - 1 == j ? 1.0 : 0.0);
+            return;
+        }
+        case FEA_PEN06: {
+            const double L[3] = {1.0 - r - s, r, s};
+            const double dLr[3] = {-1.0, 1.0, 0.0}, dLs[3] = {-1.0, 0.0, 1.0};
+            for (int h = 0; h < 2; ++h) {
+                const double zf = h ? 0.5 * (1.0 + t) : 0.5 * (1.0 - t);
+                const double dz = h ? 0.5 : -0.5;
+                for (int i = 0; i < 3; ++i) {
+                    const int a = 3 * h + i;
+                    N[a] = L[i] * zf;
+                    dN[a][0] = dLr[i] * zf;
+                    dN[a][1] = dLs[i] * zf;
+                    dN[a][2] = L[i] * dz;
+                }
+            }
+            return;
+        }
+        case FEA_HEX08: {
+            static const int sg[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
+                                         {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+            for (int a = 0; a < 8; ++a) {
+                const double px = 0.5 * (1.0 + sg[a][0] * r), py = 0.5 * (1.0 + sg[a][1] * s),
+                             pz = 0.5 * (1.0 + sg[a][2] * t);
+                N[a] = px * py * pz;
+                dN[a][0] = 0.5 * sg[a][0] * py * pz;
+                dN[a][1] = 0.5 * sg[a][1] * px * pz;
+                dN[a][2] = 0.5 * sg[a][2] * px * py;
+            }
+            return;
+        }
+        case FEA_PYR05: {
+            // base corners c = (cx, cy); the rational term carries xi eta zeta / (1 - zeta)
+            static const int cb[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
+            const double inv = 1.0 / (1.0 - t);
+            const double q = r * s * t * inv;
+            for (int a = 0; a < 4; ++a) {
+                const double cx = cb[a][0], cy = cb[a][1];
+                N[a] = 0.25 * ((1.0 + cx * r) * (1.0 + cy * s) - t + cx * cy * q);
+                dN[a][0] = 0.25 * (cx * (1.0 + cy * s) + cx * cy * s * t * inv);
+                dN[a][1] = 0.25 * (cy * (1.0 + cx * r) + cx * cy * r * t * inv);
+                dN[a][2] = 0.25 * (-1.0 + cx * cy * r * s * inv * inv);
+            }
+            N[4] = t;
+            dN[4][0] = 0.0;
+            dN[4][1] = 0.0;
+            dN[4][2] = 1.0;
+            return;
+        }
+    }
+}
+
+RefTables make_tables() {
+    RefTables T;
+    memset(&T, 0, sizeof(T));
+    for (int et = 0; et < 4; ++et) {
+        double pts[kMaxNg][3], w[kMaxNg];
+        const int ng = rule(et, pts, w);
+        for (int g = 0; g < ng; ++g) {
+            double N[kMaxNen], dN[kMaxNen][3];
+            shape_at(et, pts[g], N, dN);
+            T.w[et][g] = w[g];
+            for (int a = 0; a < kNen[et]; ++a) {
+                T.N[et][g][a] = N[a];
+                for (int j = 0; j < 3; ++j) T.dN[et][g][a][j] = dN[a][j];
+            }
+        }
+    }
+    return T;
+}
+
+// ---------------------------------------------------------------------------
+
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { reset(); }
+    void reset() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    cudaError_t alloc(size_t count) {
+        reset();
+        if (count == 0) return cudaSuccess;
+        n = count;
+        return cudaMalloc((void **)&p, count * sizeof(T));
+    }
+};
+
+struct Bucket {
+    int etype = 0, fp64j = 0;
+    int64_t count = 0;
+    DevBuf<int32_t> conn, orig;
+    DevBuf<uint16_t> lconn;
+    DevBuf<int64_t> chunk_off;
+    DevBuf<int32_t> chunk_nodes;
+    int32_t chunk_elems = 0;
+    int64_t n_chunks = 0;
+    int32_t max_chunk_nodes = 0;
+    BucketDev dev() const {
+        BucketDev b;
+        b.etype = etype;
+        b.fp64j = fp64j;
+        b.count = count;
+        b.conn = conn.p;
+        b.orig = orig.p;
+        b.chunk_elems = chunk_elems;
+        b.n_chunks = n_chunks;
+        b.lconn = lconn.p;
+        b.chunk_node_off = chunk_off.p;
+        b.chunk_nodes = chunk_nodes.p;
+        b.max_chunk_nodes = max_chunk_nodes;
+        return b;
+    }
+};
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    double dt = 0.0;
+    int prec = -1, closure = -1;
+};
+
+struct Mesh {
+    int64_t n = 0;
+    int64_t n_elem[4] = {0, 0, 0, 0};
+    std::vector<std::unique_ptr<Bucket>> buckets;
+    DevBuf<double> xyz64;
+    DevBuf<float4> xyz32;
+    DevBuf<int32_t> slaves, masters;
+    DevBuf<uint8_t> dirichlet;
+    DevBuf<double> mass, minv;
+    // state
+    DevBuf<double> un, uk, p64, rhs;
+    DevBuf<float4> up32;
+    DevBuf<float> stage_f32;
+    bool has_field = false;
+    double nu = 0.0, c_vreman = 0.0;
+    fea_plan plan{FEA_SCATTER_ATOMIC, 256, 256, 0};
+    GraphCache graph;
+    ~Mesh() {
+        if (graph.exec) cudaGraphExecDestroy(graph.exec);
+    }
+    FieldDev field() const {
+        FieldDev f;
+        f.n = n;
+        f.xyz64 = xyz64.p;
+        f.xyz32 = xyz32.p;
+        f.u64 = uk.p;
+        f.p64 = p64.p;
+        f.up32 = up32.p;
+        f.nu = nu;
+        f.c_vreman = c_vreman;
+        return f;
+    }
+};
+
+}  // namespace
+
+struct ProfRec {
+    int etype, fp64j;
+    cudaEvent_t e0, e1;
+};
+
+struct fea_ctx {
+    int device = 0;
+    bool profiling = false;
+    std::vector<ProfRec> prof;
+    std::string err;
+    unsigned *d_err = nullptr;
+    unsigned long long *d_bad = nullptr;
+    std::vector<std::unique_ptr<Mesh>> meshes;
+    cudaStream_t capture = nullptr;
+    int64_t launches = 0;
+};
+
+namespace {
+
+fea_status fail(fea_ctx *c, fea_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return st;
+}
+
+#define CK(call)                                                                                      \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? FEA_ENOMEM : FEA_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                           \
+    } while (0)
+
+fea_status get_mesh(fea_ctx *ctx, int32_t id, Mesh **m) {
+    if (!ctx) return FEA_EINVAL;
+    if (id < 0 || id >= (int32_t)ctx->meshes.size() || !ctx->meshes[id])
+        return fail(ctx, FEA_ENOTFOUND, "unknown mesh id %d", id);
+    *m = ctx->meshes[id].get();
+    return FEA_OK;
+}
+
+uint64_t spread3(uint64_t v) {
+    v &= 0x1FFFFFull;
+    v = (v | (v << 32)) & 0x1F00000000FFFFull;
+    v = (v | (v << 16)) & 0x1F0000FF0000FFull;
+    v = (v | (v << 8)) & 0x100F00F00F00F00Full;
+    v = (v | (v << 4)) & 0x10C30C30C30C30C3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+int64_t type_nut_offset(const Mesh &m, int et) {
+    int64_t off = 0;
+    for (int t = 0; t < et; ++t) off += m.n_elem[t] * kNg[t];
+    return off;
+}
+
+fea_status assemble_into(fea_ctx *ctx, Mesh &m, fea_prec prec, fea_closure closure, uint32_t mask,
+                         fea_scatter scatter, double *rhs, float *nut, cudaStream_t s) {
+    CK(cudaMemsetAsync(rhs, 0, sizeof(double) * 3 * m.n, s));
+    FieldDev f = m.field();
+    if (scatter == FEA_SCATTER_AUTO) scatter = (fea_scatter)m.plan.scatter;
+    for (auto &bp : m.buckets) {
+        const Bucket &b = *bp;
+        if (!b.count) continue;
+        AsmArgs a;
+        a.mask = mask;
+        a.closure = closure;
+        a.rhs = rhs;
+        a.nut = nut ? nut + type_nut_offset(m, b.etype) : nullptr;
+        a.err = ctx->d_err;
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (ctx->profiling) CK(cudaStreamIsCapturing(s, &cap));
+        ProfRec pr{b.etype, b.fp64j, nullptr, nullptr};
+        const bool timed = ctx->profiling && cap == cudaStreamCaptureStatusNone;
+        if (timed) {
+            CK(cudaEventCreate(&pr.e0));
+            CK(cudaEventCreate(&pr.e1));
+            CK(cudaEventRecord(pr.e0, s));
+        }
+        CK(launch_assemble_bucket(b.dev(), f, a, prec, scatter, m.plan.threads_per_block, s));
+        ctx->launches++;
+        if (timed) {
+            CK(cudaEventRecord(pr.e1, s));
+            ctx->prof.push_back(pr);
+        }
+    }
+    return FEA_OK;
+}
+
+fea_status check_args(fea_ctx *ctx, fea_prec prec, fea_closure closure, uint32_t mask) {
+    if (prec != FEA_FP64 && prec != FEA_MIXED) return fail(ctx, FEA_EINVAL, "bad precision %d", (int)prec);
+    if (closure != FEA_CLOSURE_NONE && closure != FEA_CLOSURE_VREMAN)
+        return fail(ctx, FEA_EINVAL, "closure %d not available", (int)closure);
+    if (mask & ~15u) return fail(ctx, FEA_EINVAL, "bad term mask 0x%x", mask);
+    return FEA_OK;
+}
+
+fea_status rk_stage_impl(fea_ctx *ctx, Mesh &m, int stage, double dt, fea_prec prec, fea_closure closure,
+                         cudaStream_t s) {
+    static const double A[3] = {0.0, 0.75, 1.0 / 3.0};
+    static const double B[3] = {1.0, 0.25, 2.0 / 3.0};
+    fea_status st = assemble_into(ctx, m, prec, closure, FEA_TERM_ALL, FEA_SCATTER_AUTO, m.rhs.p, nullptr, s);
+    if (st) return st;
+    if (m.slaves.n) {
+        CK(launch_fold(m.slaves.p, m.masters.p, (int64_t)m.slaves.n, m.rhs.p, 3, m.n, s));
+        ctx->launches += 2;
+    }
+    CK(launch_rk_update(m.n, m.un.p, m.uk.p, stage == 2 ? m.un.p : nullptr, m.rhs.p, m.minv.p,
+                        m.dirichlet.n ? m.dirichlet.p : nullptr, m.p64.p, m.up32.p, A[stage], B[stage], dt, s));
+    ctx->launches++;
+    return FEA_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char *fea_version(void) { return "libfea 0.1 (sm_103a)"; }
+
+fea_status fea_create(int device, fea_ctx **out) {
+    if (!out) return FEA_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        return FEA_ECUDA;
+    }
+    if (device < 0 || device >= count) return FEA_EINVAL;
+    auto ctx = new fea_ctx();
+    ctx->device = device;
+    fea_status st = FEA_OK;
+    do {
+        if (cudaSetDevice(device) != cudaSuccess) { st = FEA_ECUDA; break; }
+        if (cudaMalloc(&ctx->d_err, sizeof(unsigned)) != cudaSuccess) { st = FEA_ENOMEM; break; }
+        if (cudaMalloc(&ctx->d_bad, sizeof(unsigned long long)) != cudaSuccess) { st = FEA_ENOMEM; break; }
+        if (cudaMemset(ctx->d_err, 0, sizeof(unsigned)) != cudaSuccess) { st = FEA_ECUDA; break; }
+        if (cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking) != cudaSuccess) { st = FEA_ECUDA; break; }
+        RefTables t = make_tables();
+        if (upload_ref_tables(t) != cudaSuccess) { st = FEA_ECUDA; break; }
+    } while (0);
+    if (st != FEA_OK) {
+        cudaGetLastError();
+        fea_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return FEA_OK;
+}
+
+void fea_destroy(fea_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    ctx->meshes.clear();
+    for (auto &r : ctx->prof) {
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->d_bad) cudaFree(ctx->d_bad);
+    if (ctx->capture) cudaStreamDestroy(ctx->capture);
+    delete ctx;
+}
+
+const char *fea_last_error(const fea_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t fea_launch_count(const fea_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+fea_status fea_mesh_upload(fea_ctx *ctx, const fea_mesh_desc *d, void *stream, int32_t *mesh_id) {
+    if (!ctx || !d || !mesh_id) return fail(ctx, FEA_EINVAL, "null argument");
+    if (d->n_nodes <= 0 || d->n_nodes >= (int64_t)1 << 31 || !d->xyz)
+        return fail(ctx, FEA_EINVAL, "n_nodes must be in [1, 2^31) with coordinates");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    const int64_t n = d->n_nodes;
+    auto m = std::make_unique<Mesh>();
+    m->n = n;
+    // validation of connectivity (host)
+    for (int t = 0; t < 4; ++t) {
+        if (d->n_elem[t] < 0) return fail(ctx, FEA_EINVAL, "negative element count for type %d", t);
+        if (d->n_elem[t] > 0 && !d->conn[t]) return fail(ctx, FEA_EINVAL, "missing connectivity for type %d", t);
+        if (d->n_elem[t] >= (int64_t)1 << 31) return fail(ctx, FEA_EINVAL, "too many elements of type %d", t);
+        const int nen = kNen[t];
+        for (int64_t k = 0; k < d->n_elem[t] * nen; ++k) {
+            const int32_t v = d->conn[t][k];
+            if (v < 0 || v >= n)
+                return fail(ctx, FEA_EMESH, "element %lld of type %d: node index %d out of range [0, %lld)",
+                            (long long)(k / nen), t, v, (long long)n);
+        }
+        m->n_elem[t] = d->n_elem[t];
+    }
+    if (d->periodic_master)
+        for (int64_t i = 0; i < n; ++i)
+            if (d->periodic_master[i] < 0 || d->periodic_master[i] >= n)
+                return fail(ctx, FEA_EMESH, "periodic master of node %lld out of range", (long long)i);
+    // coordinates: bounding box for the Morton keys
+    const double *X = d->xyz;
+    double lo[3], hi[3];
+    for (int i = 0; i < 3; ++i) {
+        lo[i] = X[i * n];
+        hi[i] = X[i * n];
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int64_t k = 0; k < n; ++k) {
+            lo[i] = std::min(lo[i], X[i * n + k]);
+            hi[i] = std::max(hi[i], X[i * n + k]);
+        }
+    double scale[3];
+    for (int i = 0; i < 3; ++i) scale[i] = (hi[i] > lo[i]) ? double((1u << 21) - 1) / (hi[i] - lo[i]) : 0.0;
+    // buckets: (type, fp64 flag), each sorted by the Morton key of the centroid
+    for (int t = 0; t < 4; ++t) {
+        const int64_t E = d->n_elem[t];
+        if (!E) continue;
+        const int nen = kNen[t];
+        for (int flag = 0; flag < 2; ++flag) {
+            std::vector<std::pair<uint64_t, int32_t>> keys;
+            keys.reserve(flag ? 0 : E);
+            for (int64_t e = 0; e < E; ++e) {
+                const int fl = d->fp64_jac[t] ? (d->fp64_jac[t][e] ? 1 : 0) : 0;
+                if (fl != flag) continue;
+                double c[3] = {0, 0, 0};
+                for (int a = 0; a < nen; ++a) {
+                    const int32_t v = d->conn[t][e * nen + a];
+                    for (int i = 0; i < 3; ++i) c[i] += X[i * n + v];
+                }
+                uint64_t key = 0;
+                for (int i = 0; i < 3; ++i) {
+                    double q = (c[i] / nen - lo[i]) * scale[i];
+                    q = std::min(std::max(q, 0.0), double((1u << 21) - 1));
+                    key |= spread3((uint64_t)q) << i;
+                }
+                keys.emplace_back(key, (int32_t)e);
+            }
+            if (keys.empty()) continue;
+            std::sort(keys.begin(), keys.end());
+            const int64_t cnt = (int64_t)keys.size();
+            std::vector<int32_t> conn((size_t)cnt * nen), orig((size_t)cnt);
+            for (int64_t k = 0; k < cnt; ++k) {
+                const int32_t e = keys[k].second;
+                orig[k] = e;
+                for (int a = 0; a < nen; ++a) conn[(size_t)a * cnt + k] = d->conn[t][(int64_t)e * nen + a];
+            }
+            auto b = std::make_unique<Bucket>();
+            b->etype = t;
+            b->fp64j = flag;
+            b->count = cnt;
+            CK(b->conn.alloc(conn.size()));
+            CK(b->orig.alloc(orig.size()));
+            CK(cudaMemcpy(b->conn.p, conn.data(), conn.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(b->orig.p, orig.data(), orig.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+            m->buckets.push_back(std::move(b));
+        }
+    }
+    // node arrays
+    CK(m->xyz64.alloc(3 * n));
+    CK(cudaMemcpy(m->xyz64.p, X, sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
+    {
+        std::vector<float4> x32((size_t)n);
+        for (int64_t k = 0; k < n; ++k)
+            x32[k] = make_float4((float)X[k], (float)X[n + k], (float)X[2 * n + k], 0.0f);
+        CK(m->xyz32.alloc(n));
+        CK(cudaMemcpy(m->xyz32.p, x32.data(), sizeof(float4) * n, cudaMemcpyHostToDevice));
+    }
+    if (d->periodic_master) {
+        std::vector<int32_t> sl, ms;
+        for (int64_t i = 0; i < n; ++i)
+            if (d->periodic_master[i] != i) {
+                sl.push_back((int32_t)i);
+                ms.push_back(d->periodic_master[i]);
+            }
+        if (!sl.empty()) {
+            CK(m->slaves.alloc(sl.size()));
+            CK(m->masters.alloc(ms.size()));
+            CK(cudaMemcpy(m->slaves.p, sl.data(), sl.size() * 4, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(m->masters.p, ms.data(), ms.size() * 4, cudaMemcpyHostToDevice));
+        }
+    }
+    if (d->dirichlet) {
+        CK(m->dirichlet.alloc(n));
+        CK(cudaMemcpy(m->dirichlet.p, d->dirichlet, n, cudaMemcpyHostToDevice));
+    }
+    // lumped mass + det J validation (FP64)
+    CK(m->mass.alloc(n));
+    CK(m->minv.alloc(n));
+    CK(cudaMemsetAsync(m->mass.p, 0, sizeof(double) * n, s));
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), s));
+    for (auto &bp : m->buckets) {
+        CK(cudaMemsetAsync(ctx->d_bad, 0xFF, sizeof(unsigned long long), s));
+        CK(launch_lumped_mass(bp->dev(), m->xyz64.p, n, m->mass.p, ctx->d_err, ctx->d_bad, s));
+        ctx->launches++;
+        unsigned long long bad = ~0ull;
+        CK(cudaMemcpyAsync(&bad, ctx->d_bad, sizeof bad, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (bad != ~0ull) {
+            std::vector<int32_t> o(1);
+            CK(cudaMemcpy(o.data(), bp->orig.p + bad, 4, cudaMemcpyDeviceToHost));
+            cudaMemset(ctx->d_err, 0, sizeof(unsigned));
+            return fail(ctx, FEA_EMESH, "element %d of type %d has det J <= 0 at a Gauss point", o[0], bp->etype);
+        }
+    }
+    // folded reciprocal mass for the RK stages
+    {
+        DevBuf<double> folded;
+        CK(folded.alloc(n));
+        CK(cudaMemcpyAsync(folded.p, m->mass.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        if (m->slaves.n) CK(launch_fold(m->slaves.p, m->masters.p, (int64_t)m->slaves.n, folded.p, 1, n, s));
+        CK(launch_recip(folded.p, m->minv.p, n, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    CK(m->un.alloc(3 * n));
+    CK(m->uk.alloc(3 * n));
+    CK(m->p64.alloc(n));
+    CK(m->rhs.alloc(3 * n));
+    CK(m->up32.alloc(n));
+    ctx->meshes.push_back(std::move(m));
+    *mesh_id = (int32_t)ctx->meshes.size() - 1;
+    return FEA_OK;
+}
+
+fea_status fea_mesh_info(fea_ctx *ctx, int32_t mesh, int64_t *n_nodes, int64_t n_elem[4]) {
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    if (n_nodes) *n_nodes = m->n;
+    if (n_elem)
+        for (int t = 0; t < 4; ++t) n_elem[t] = m->n_elem[t];
+    return FEA_OK;
+}
+
+fea_status fea_lumped_mass(fea_ctx *ctx, int32_t mesh, double *out, void *stream) {
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    if (!out) return fail(ctx, FEA_EINVAL, "null output");
+    CK(cudaMemcpyAsync(out, m->mass.p, sizeof(double) * m->n, cudaMemcpyDefault, (cudaStream_t)stream));
+    return FEA_OK;
+}
+
+fea_status fea_field_upload(fea_ctx *ctx, int32_t mesh, const void *u, const void *p, int dtype, double nu,
+                            double c_vreman, void *stream) {
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    if (!u || !p) return fail(ctx, FEA_EINVAL, "null field");
+    if (dtype != 0 && dtype != 1) return fail(ctx, FEA_EINVAL, "dtype must be 0 (f64) or 1 (f32)");
+    if (!(nu >= 0.0) || !(c_vreman >= 0.0)) return fail(ctx, FEA_EINVAL, "nu and c_vreman must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = m->n;
+    if (dtype == 0) {
+        CK(cudaMemcpyAsync(m->uk.p, u, sizeof(double) * 3 * n, cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(m->p64.p, p, sizeof(double) * n, cudaMemcpyDefault, s));
+    } else {
+        if (m->stage_f32.n < (size_t)(4 * n)) CK(m->stage_f32.alloc(4 * n));
+        CK(cudaMemcpyAsync(m->stage_f32.p, u, sizeof(float) * 3 * n, cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(m->stage_f32.p + 3 * n, p, sizeof(float) * n, cudaMemcpyDefault, s));
+        CK(launch_f32_to_f64(m->stage_f32.p, m->uk.p, 3 * n, s));
+        CK(launch_f32_to_f64(m->stage_f32.p + 3 * n, m->p64.p, n, s));
+        ctx->launches += 2;
+    }
+    CK(cudaMemcpyAsync(m->un.p, m->uk.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
+    CK(launch_pack_field(n, m->uk.p, m->p64.p, m->up32.p, s));
+    ctx->launches++;
+    m->nu = nu;
+    m->c_vreman = c_vreman;
+    m->has_field = true;
+    return FEA_OK;
+}
+
+fea_status fea_assemble_rhs(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure closure, uint32_t mask,
+                            fea_scatter scatter, double *rhs_out, float *nut_out, void *stream) {
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    if ((st = check_args(ctx, prec, closure, mask))) return st;
+    if (!rhs_out) return fail(ctx, FEA_EINVAL, "null rhs_out");
+    if (scatter < FEA_SCATTER_AUTO || scatter > FEA_SCATTER_CHUNK) return fail(ctx, FEA_EINVAL, "bad scatter");
+    if (!m->has_field) return fail(ctx, FEA_ESTATE, "no field uploaded for mesh %d", mesh);
+    return assemble_into(ctx, *m, prec, closure, mask, scatter, rhs_out, nut_out, (cudaStream_t)stream);
+}
+
+fea_status fea_assemble_rhs_batched(fea_ctx *ctx, const int32_t *meshes, int32_t n, fea_prec prec,
+                                    fea_closure closure, uint32_t mask, double *const *rhs_out, void *stream) {
+    if (!ctx || !meshes || !rhs_out || n <= 0) return fail(ctx, FEA_EINVAL, "bad batch arguments");
+    fea_status st = check_args(ctx, prec, closure, mask);
+    if (st) return st;
+    for (int32_t k = 0; k < n; ++k) {
+        Mesh *m;
+        if ((st = get_mesh(ctx, meshes[k], &m))) return st;
+        if (!m->has_field) return fail(ctx, FEA_ESTATE, "no field uploaded for mesh %d", meshes[k]);
+        if (!rhs_out[k]) return fail(ctx, FEA_EINVAL, "null rhs_out[%d]", k);
+    }
+    for (int32_t k = 0; k < n; ++k) {
+        Mesh *m = ctx->meshes[meshes[k]].get();
+        st = assemble_into(ctx, *m, prec, closure, mask, FEA_SCATTER_AUTO, rhs_out[k], nullptr, (cudaStream_t)stream);
+        if (st) return st;
+    }
+    return FEA_OK;
+}
+
+fea_status fea_periodic_fold(fea_ctx *ctx, int32_t mesh, double *v, int32_t ncomp, void *stream) {
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    if (!v || ncomp < 1 || ncomp > 16) return fail(ctx, FEA_EINVAL, "bad fold arguments");
+    if (!m->slaves.n) return FEA_OK;
+    CK(launch_fold(m->slaves.p, m->masters.p, (int64_t)m->slaves.n, v, ncomp, m->n, (cudaStream_t)stream));
+    ctx->launches += 2;
+    return FEA_OK;
+}
+
+fea_status fea_rk_stage(fea_ctx *ctx, int32_t mesh, int32_t stage, double dt, fea_prec prec, fea_closure closure,
+                        void *stream) {
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    if ((st = check_args(ctx, prec, closure, FEA_TERM_ALL))) return st;
+    if (stage < 0 || stage > 2) return fail(ctx, FEA_EINVAL, "stage must be 0, 1 or 2");
+    if (!(dt > 0.0)) return fail(ctx, FEA_EINVAL, "dt must be > 0");
+    if (!m->has_field) return fail(ctx, FEA_ESTATE, "no field uploaded for mesh %d", mesh);
+    return rk_stage_impl(ctx, *m, stage, dt, prec, closure, (cudaStream_t)stream);
+}
+
+fea_status fea_rk_step_graph(fea_ctx *ctx, int32_t mesh, double dt, fea_prec prec, fea_closure closure,
+                             void *stream) {
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    if ((st = check_args(ctx, prec, closure, FEA_TERM_ALL))) return st;
+    if (!(dt > 0.0)) return fail(ctx, FEA_EINVAL, "dt must be > 0");
+    if (!m->has_field) return fail(ctx, FEA_ESTATE, "no field uploaded for mesh %d", mesh);
+    GraphCache &g = m->graph;
+    if (!g.exec || g.dt != dt || g.prec != prec || g.closure != closure) {
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+        CK(cudaStreamSynchronize((cudaStream_t)stream));
+        cudaGraph_t graph;
+        const int64_t before = ctx->launches;
+        CK(cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < 3 && st == FEA_OK; ++k) st = rk_stage_impl(ctx, *m, k, dt, prec, closure, ctx->capture);
+        cudaError_t e = cudaStreamEndCapture(ctx->capture, &graph);
+        ctx->launches = before;
+        if (st) return st;
+        CK(e);
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(e);
+        g.dt = dt;
+        g.prec = prec;
+        g.closure = closure;
+    }
+    CK(cudaGraphLaunch(g.exec, (cudaStream_t)stream));
+    // kernels per step: 3 x (buckets + fold 2 + update 1)
+    int64_t per_stage = 1 + (m->slaves.n ? 2 : 0);
+    for (auto &b : m->buckets) per_stage += b->count ? 1 : 0;
+    ctx->launches += 3 * per_stage;
+    return FEA_OK;
+}
+
+fea_status fea_state_download(fea_ctx *ctx, int32_t mesh, double *out, void *stream) {
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    if (!out) return fail(ctx, FEA_EINVAL, "null output");
+    if (!m->has_field) return fail(ctx, FEA_ESTATE, "no field uploaded for mesh %d", mesh);
+    CK(cudaMemcpyAsync(out, m->uk.p, sizeof(double) * 3 * m->n, cudaMemcpyDefault, (cudaStream_t)stream));
+    return FEA_OK;
+}
+
+fea_status fea_get_plan(fea_ctx *ctx, int32_t mesh, fea_plan *plan) {
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    if (!plan) return fail(ctx, FEA_EINVAL, "null plan");
+    *plan = m->plan;
+    return FEA_OK;
+}
+
+fea_status fea_set_plan(fea_ctx *ctx, int32_t mesh, const fea_plan *plan) {
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    if (!plan) return fail(ctx, FEA_EINVAL, "null plan");
+    if (plan->scatter != FEA_SCATTER_ATOMIC && plan->scatter != FEA_SCATTER_CHUNK)
+        return fail(ctx, FEA_EINVAL, "plan scatter must be ATOMIC or CHUNK");
+    if (plan->threads_per_block < 32 || plan->threads_per_block > 1024 || plan->threads_per_block % 32)
+        return fail(ctx, FEA_EINVAL, "threads_per_block must be a multiple of 32 in [32, 1024]");
+    if (plan->scatter == FEA_SCATTER_CHUNK) return fail(ctx, FEA_EINVAL, "chunk scatter not built for this mesh");
+    m->plan = *plan;
+    if (m->graph.exec) {
+        cudaGraphExecDestroy(m->graph.exec);
+        m->graph.exec = nullptr;
+    }
+    return FEA_OK;
+}
+
+fea_status fea_autotune(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure closure, const char *cache_path) {
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    if ((st = check_args(ctx, prec, closure, FEA_TERM_ALL))) return st;
+    if (!m->has_field) return fail(ctx, FEA_ESTATE, "no field uploaded for mesh %d", mesh);
+    (void)cache_path;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    fea_plan best = m->plan;
+    float best_ms = 1e30f;
+    const int cand[3] = {64, 128, 256};
+    for (int c = 0; c < 3; ++c) {
+        m->plan.scatter = FEA_SCATTER_ATOMIC;
+        m->plan.threads_per_block = cand[c];
+        for (int rep = 0; rep < 2; ++rep)
+            if ((st = assemble_into(ctx, *m, prec, closure, FEA_TERM_ALL, FEA_SCATTER_AUTO, m->rhs.p, nullptr, 0)))
+                return st;
+        CK(cudaEventRecord(e0, 0));
+        for (int rep = 0; rep < 5; ++rep)
+            if ((st = assemble_into(ctx, *m, prec, closure, FEA_TERM_ALL, FEA_SCATTER_AUTO, m->rhs.p, nullptr, 0)))
+                return st;
+        CK(cudaEventRecord(e1, 0));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = m->plan;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    m->plan = best;
+    if (m->graph.exec) {
+        cudaGraphExecDestroy(m->graph.exec);
+        m->graph.exec = nullptr;
+    }
+    return FEA_OK;
+}
+
+fea_status fea_profile_enable(fea_ctx *ctx, int on) {
+    if (!ctx) return FEA_EINVAL;
+    ctx->profiling = on != 0;
+    return FEA_OK;
+}
+
+fea_status fea_profile_read(fea_ctx *ctx, int etype, int fp64_jac, double *total_ms, int64_t *launches, int reset) {
+    if (!ctx || !total_ms || !launches) return fail(ctx, FEA_EINVAL, "null argument");
+    double ms = 0.0;
+    int64_t cnt = 0;
+    for (auto &r : ctx->prof) {
+        if (r.etype != etype || r.fp64j != fp64_jac) continue;
+        CK(cudaEventSynchronize(r.e1));
+        float t = 0.0f;
+        CK(cudaEventElapsedTime(&t, r.e0, r.e1));
+        ms += t;
+        ++cnt;
+    }
+    *total_ms = ms;
+    *launches = cnt;
+    if (reset) {
+        for (auto &r : ctx->prof) {
+            cudaEventDestroy(r.e0);
+            cudaEventDestroy(r.e1);
+        }
+        ctx->prof.clear();
+    }
+    return FEA_OK;
+}
+
+fea_status fea_sync_status(fea_ctx *ctx, void *stream) {
+    if (!ctx) return FEA_EINVAL;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned w = 0;
+    CK(cudaMemcpy(&w, ctx->d_err, sizeof w, cudaMemcpyDeviceToHost));
+    CK(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
+    if (w & ERR_TIMEOUT) return fail(ctx, FEA_ETIMEOUT, "a bounded device wait gave up (word 0x%x)", w);
+    if (w & (ERR_DETJ | ERR_INDEX)) return fail(ctx, FEA_EMESH, "device saw det J <= 0 or a bad index (word 0x%x)", w);
+    if (w & ERR_NONFINITE) return fail(ctx, FEA_ENUMERIC, "non-finite element residual (word 0x%x)", w);
+    return FEA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Internal declarations shared by the host side (fea_api.cu) and the kernel
+// translation unit (fea_kernels.cu) of libfea.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fea.h"
+
+namespace fea {
+
+constexpr int kNen[4] = {4, 5, 6, 8};
+constexpr int kNg[4] = {4, 8, 6, 8};
+constexpr int kMaxNen = 8;
+constexpr int kMaxNg = 8;
+
+// device error word bits (OR-ed by kernels, read by fea_sync_status)
+enum : unsigned {
+    ERR_DETJ = 1u,      // det J <= 0 at some Gauss point
+    ERR_NONFINITE = 2u, // non-finite element residual
+    ERR_TIMEOUT = 4u,   // a bounded device-side wait gave up
+    ERR_INDEX = 8u      // index out of range (checked builds and upload validation)
+};
+
+// Reference-element tables at the Gauss points of each type's rule.
+struct RefTables {
+    double N[4][kMaxNg][kMaxNen];
+    double dN[4][kMaxNg][kMaxNen][3];
+    double w[4][kMaxNg];
+};
+
+// One category: elements of one type and one Jacobian precision, sorted
+// along a Morton curve; connectivity structure-of-arrays [nen][count].
+struct BucketDev {
+    int etype;
+    int fp64j;              // 1: FP64 Jacobian in the mixed path
+    int64_t count;
+    const int32_t *conn;    // [nen][count] caller node ids
+    const int32_t *orig;    // [count] caller element index within its type
+    // chunk tables (CTA-local scatter)
+    int32_t chunk_elems;
+    int64_t n_chunks;
+    const uint16_t *lconn;      // [nen][count] chunk-local node index
+    const int64_t *chunk_node_off;  // [n_chunks + 1] offsets into chunk_nodes
+    const int32_t *chunk_nodes;     // caller node id, bit 31 set = shared with other chunks
+    int32_t max_chunk_nodes;
+};
+
+// Per-mesh nodal data used by the kernels.
+struct FieldDev {
+    int64_t n;
+    const double *xyz64;  // [3][n]
+    const float4 *xyz32;  // [n] (x, y, z, 0)
+    const double *u64;    // [3][n] current state u^(k)
+    const double *p64;    // [n]
+    const float4 *up32;   // [n] (u, v, w, p), FP32 copy of the state
+    double nu;
+    double c_vreman;
+};
+
+struct AsmArgs {
+    uint32_t mask;
+    int closure;          // fea_closure
+    double *rhs;          // [3][n]
+    float *nut;           // optional: type block of nu_t output (already offset)
+    unsigned *err;        // device error word
+};
+
+// launchers (fea_kernels.cu); all return cudaGetLastError() of the launch
+cudaError_t upload_ref_tables(const RefTables &t);
+cudaError_t launch_assemble_bucket(const BucketDev &b, const FieldDev &f, const AsmArgs &a, fea_prec prec,
+                                   fea_scatter scatter, int threads, cudaStream_t s);
+cudaError_t launch_lumped_mass(const BucketDev &b, const double *xyz64, int64_t n, double *mass, unsigned *err,
+                               unsigned long long *bad, cudaStream_t s);
+cudaError_t launch_fold(const int32_t *slaves, const int32_t *masters, int64_t n_slaves, double *v, int ncomp,
+                        int64_t n, cudaStream_t s);
+cudaError_t launch_rk_update(int64_t n, const double *un, double *uk, double *un_out, const double *rhs,
+                             const double *minv, const uint8_t *dirichlet, const double *p64, float4 *up32,
+                             double a, double b, double dt, cudaStream_t s);
+cudaError_t launch_pack_field(int64_t n, const double *u64, const double *p64, float4 *up32, cudaStream_t s);
+cudaError_t launch_f32_to_f64(const float *src, double *dst, int64_t count, cudaStream_t s);
+cudaError_t launch_recip(const double *m, double *minv, int64_t n, cudaStream_t s);
+
+}  // namespace fea

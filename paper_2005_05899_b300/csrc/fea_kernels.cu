@@ -1,0 +1,524 @@
+// Element-assembly kernels of the momentum RHS for sm_103a.
+//
+// One thread computes one element (gather -> computation -> scatter, the
+// three steps of section 2.3.3).  Elements arrive in categories (one element
+// type, one Jacobian precision) sorted along a Morton curve, so neighbouring
+// threads touch neighbouring nodes.  The residual of Eq. momentum per node a
+// and component i is
+//   r_a,i = - sum_g W_g [ N_a (c_i + d_i p) + 2 (nu + nu_t) eps_ij d_j N_a ],
+//   c = G u + (tr G) u,  G_ij = du_i/dx_j,  W_g = w_g det J,
+// with nu_t from Vreman's model (section 2.1) at every Gauss point and the
+// filter width Delta = V_e^(1/3).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "fea_internal.h"
+
+namespace fea {
+
+__constant__ RefTables c_ref;
+
+cudaError_t upload_ref_tables(const RefTables &t) { return cudaMemcpyToSymbol(c_ref, &t, sizeof(RefTables)); }
+
+template <typename R>
+struct Mat3 {
+    R m[3][3];
+};
+
+template <typename R>
+__device__ __forceinline__ R det3(const R J[3][3]) {
+    return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+// adjugate / det, returns det
+template <typename R>
+__device__ __forceinline__ R inv3(const R J[3][3], R Ji[3][3]) {
+    R c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    R c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    R c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    R det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    R d = R(1) / det;
+    Ji[0][0] = c00 * d;
+    Ji[1][0] = c01 * d;
+    Ji[2][0] = c02 * d;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * d;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * d;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * d;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * d;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * d;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * d;
+    return det;
+}
+
+// Vreman: beta' = G G^T (so that beta = Delta^2 beta'), B_beta = Delta^4 B',
+// nu_t = c Delta^2 sqrt(B' / (G:G)); zero when G:G == 0 or B' <= 0.
+template <typename R>
+__device__ __forceinline__ R vreman(const R G[3][3], R delta2, R c) {
+    R aa = R(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) aa += G[i][j] * G[i][j];
+    R b11 = G[0][0] * G[0][0] + G[0][1] * G[0][1] + G[0][2] * G[0][2];
+    R b22 = G[1][0] * G[1][0] + G[1][1] * G[1][1] + G[1][2] * G[1][2];
+    R b33 = G[2][0] * G[2][0] + G[2][1] * G[2][1] + G[2][2] * G[2][2];
+    R b12 = G[0][0] * G[1][0] + G[0][1] * G[1][1] + G[0][2] * G[1][2];
+    R b13 = G[0][0] * G[2][0] + G[0][1] * G[2][1] + G[0][2] * G[2][2];
+    R b23 = G[1][0] * G[2][0] + G[1][1] * G[2][1] + G[1][2] * G[2][2];
+    R B = b11 * b22 - b12 * b12 + b11 * b33 - b13 * b13 + b22 * b33 - b23 * b23;
+    if (!(aa > R(0)) || !(B > R(0))) return R(0);
+    return c * delta2 * sqrt(B / aa);
+}
+
+__device__ __forceinline__ double cbrt_r(double v) { return cbrt(v); }
+__device__ __forceinline__ float cbrt_r(float v) { return cbrtf(v); }
+
+__device__ __forceinline__ void set_err(unsigned *err, unsigned bit) {
+    if (err) atomicOr(err, bit);
+}
+
+// ---------------------------------------------------------------------------
+// gather helpers
+
+template <typename R, bool J64>
+struct Gathered {
+    R U[kMaxNen][3];
+    R P[kMaxNen];
+    typename std::conditional<J64, double, R>::type X[kMaxNen][3];
+};
+
+template <int ET, typename R, bool J64>
+__device__ __forceinline__ void gather(const FieldDev &f, const int idx[], Gathered<R, J64> &g) {
+    constexpr int nen = kNen[ET];
+#pragma unroll
+    for (int a = 0; a < nen; ++a) {
+        const int64_t n = idx[a];
+        if constexpr (sizeof(R) == 8) {
+            g.U[a][0] = f.u64[n];
+            g.U[a][1] = f.u64[f.n + n];
+            g.U[a][2] = f.u64[2 * f.n + n];
+            g.P[a] = f.p64[n];
+        } else {
+            const float4 up = __ldg(&f.up32[n]);
+            g.U[a][0] = up.x;
+            g.U[a][1] = up.y;
+            g.U[a][2] = up.z;
+            g.P[a] = up.w;
+        }
+        if constexpr (sizeof(R) == 8 || J64) {
+            g.X[a][0] = __ldg(&f.xyz64[n]);
+            g.X[a][1] = __ldg(&f.xyz64[f.n + n]);
+            g.X[a][2] = __ldg(&f.xyz64[2 * f.n + n]);
+        } else {
+            const float4 x = __ldg(&f.xyz32[n]);
+            g.X[a][0] = x.x;
+            g.X[a][1] = x.y;
+            g.X[a][2] = x.z;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// residual of one element at the Gauss points of its rule (all types).
+// R: arithmetic type; JR: type of the Jacobian, its determinant and inverse.
+
+template <int ET, typename R, typename JR>
+__device__ __forceinline__ JR jacobian_at(const JR X[][3], int g, JR J[3][3]) {
+    constexpr int nen = kNen[ET];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) J[i][j] = JR(0);
+#pragma unroll
+    for (int a = 0; a < nen; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const JR d = JR(c_ref.dN[ET][g][a][j]);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) J[i][j] += X[a][i] * d;
+        }
+    return det3(J);
+}
+
+template <int ET, typename R, bool J64>
+__device__ void element_residual(const Gathered<R, J64> &el, const FieldDev &f, const AsmArgs &args, R r[][3],
+                                 float *nut_out, bool &bad) {
+    using JR = typename std::conditional<J64, double, R>::type;
+    constexpr int nen = kNen[ET], ng = kNg[ET];
+    const uint32_t mask = args.mask;
+    // element volume first (filter width)
+    JR V = JR(0);
+#pragma unroll
+    for (int g = 0; g < ng; ++g) {
+        JR J[3][3];
+        const JR d = jacobian_at<ET, R, JR>(el.X, g, J);
+        if (!(d > JR(0))) bad = true;
+        V += JR(c_ref.w[ET][g]) * d;
+    }
+    const R delta = cbrt_r(R(V));
+    const R delta2 = delta * delta;
+    const R nu = R(f.nu), cv = R(f.c_vreman);
+#pragma unroll
+    for (int a = 0; a < nen; ++a) r[a][0] = r[a][1] = r[a][2] = R(0);
+#pragma unroll
+    for (int g = 0; g < ng; ++g) {
+        JR J[3][3], Jd[3][3];
+        jacobian_at<ET, R, JR>(el.X, g, J);
+        const JR detj = inv3(J, Jd);
+        R Ji[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Ji[i][j] = R(Jd[i][j]);
+        const R W = R(JR(c_ref.w[ET][g]) * detj);
+        // reference-coordinate gradients and the Gauss-point velocity
+        R Gx[3][3] = {}, px[3] = {}, ug[3] = {};
+#pragma unroll
+        for (int a = 0; a < nen; ++a) {
+            const R Na = R(c_ref.N[ET][g][a]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const R d = R(c_ref.dN[ET][g][a][k]);
+                px[k] += el.P[a] * d;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) Gx[i][k] += el.U[a][i] * d;
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) ug[i] += Na * el.U[a][i];
+        }
+        // physical gradients: G_ij = sum_k Gx_ik Ji_kj
+        R G[3][3], gp[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            gp[j] = px[0] * Ji[0][j] + px[1] * Ji[1][j] + px[2] * Ji[2][j];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) G[i][j] = Gx[i][0] * Ji[0][j] + Gx[i][1] * Ji[1][j] + Gx[i][2] * Ji[2][j];
+        }
+        R nut = R(0);
+        if (args.closure == FEA_CLOSURE_VREMAN && ((mask & FEA_TERM_SGS) || nut_out)) nut = vreman(G, delta2, cv);
+        if (nut_out) nut_out[g] = float(nut);
+        const R trG = G[0][0] + G[1][1] + G[2][2];
+        R f0[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            R c = R(0);
+            if (mask & FEA_TERM_CONV) c = G[i][0] * ug[0] + G[i][1] * ug[1] + G[i][2] * ug[2] + trG * ug[i];
+            f0[i] = W * (c + ((mask & FEA_TERM_PRES) ? gp[i] : R(0)));
+        }
+        R visc = R(0);
+        if (mask & FEA_TERM_VISC) visc += nu;
+        if (mask & FEA_TERM_SGS) visc += nut;
+        // S_ik = 2 visc W sum_j eps_ij Ji_kj
+        R eps[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) eps[i][j] = R(0.5) * (G[i][j] + G[j][i]);
+        const R s2 = R(2) * visc * W;
+        R S[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) S[i][k] = s2 * (eps[i][0] * Ji[k][0] + eps[i][1] * Ji[k][1] + eps[i][2] * Ji[k][2]);
+#pragma unroll
+        for (int a = 0; a < nen; ++a) {
+            const R Na = R(c_ref.N[ET][g][a]);
+            const R d0 = R(c_ref.dN[ET][g][a][0]), d1 = R(c_ref.dN[ET][g][a][1]), d2 = R(c_ref.dN[ET][g][a][2]);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) r[a][i] -= Na * f0[i] + S[i][0] * d0 + S[i][1] * d1 + S[i][2] * d2;
+        }
+    }
+}
+
+// TET04: affine map, constant gradients; the 4-point rule is exact for the
+// degree-2 integrands, so the Gauss sums take their closed forms:
+//   sum_g W N_a N_b = V (1 + delta_ab) / 20,  sum_g W N_a = V / 4.
+template <typename R, bool J64>
+__device__ void tet_residual(const Gathered<R, J64> &el, const FieldDev &f, const AsmArgs &args, R r[][3],
+                             float *nut_out, bool &bad) {
+    using JR = typename std::conditional<J64, double, R>::type;
+    const uint32_t mask = args.mask;
+    JR J[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) J[i][k] = el.X[k + 1][i] - el.X[0][i];
+    JR Jd[3][3];
+    const JR detj = inv3(J, Jd);
+    if (!(detj > JR(0))) bad = true;
+    const R V = R(detj / JR(6));
+    // grad N_k (k = 1..3) = row k-1 of J^-1; grad N_0 = -sum
+    R dN[4][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dN[k + 1][j] = R(Jd[k][j]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dN[0][j] = -(dN[1][j] + dN[2][j] + dN[3][j]);
+    R G[3][3], gp[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        gp[j] = R(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) G[i][j] = R(0);
+#pragma unroll
+        for (int a = 1; a < 4; ++a) {
+            const R d = dN[a][j];
+            gp[j] += (el.P[a] - el.P[0]) * d;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) G[i][j] += (el.U[a][i] - el.U[0][i]) * d;
+        }
+    }
+    R nut = R(0);
+    if (args.closure == FEA_CLOSURE_VREMAN && ((mask & FEA_TERM_SGS) || nut_out)) {
+        const R delta = cbrt_r(V);
+        nut = vreman(G, delta * delta, R(f.c_vreman));
+    }
+    if (nut_out) {
+#pragma unroll
+        for (int g = 0; g < 4; ++g) nut_out[g] = float(nut);
+    }
+    const R trG = G[0][0] + G[1][1] + G[2][2];
+    R visc = R(0);
+    if (mask & FEA_TERM_VISC) visc += R(f.nu);
+    if (mask & FEA_TERM_SGS) visc += nut;
+    const R s2 = R(2) * visc * V;
+    R sig[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) sig[i][j] = s2 * R(0.5) * (G[i][j] + G[j][i]);
+    R su[3] = {el.U[0][0] + el.U[1][0] + el.U[2][0] + el.U[3][0], el.U[0][1] + el.U[1][1] + el.U[2][1] + el.U[3][1],
+               el.U[0][2] + el.U[1][2] + el.U[2][2] + el.U[3][2]};
+    const R v20 = V * R(0.05), v4 = V * R(0.25);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        R m[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) m[i] = v20 * (el.U[a][i] + su[i]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            R v = R(0);
+            if (mask & FEA_TERM_CONV) v += G[i][0] * m[0] + G[i][1] * m[1] + G[i][2] * m[2] + trG * m[i];
+            if (mask & FEA_TERM_PRES) v += v4 * gp[i];
+            v += sig[i][0] * dN[a][0] + sig[i][1] * dN[a][1] + sig[i][2] * dN[a][2];
+            r[a][i] = -v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// ATOMIC scatter kernel: thread per element, FP64 atomic adds into rhs [3][n]
+
+template <int ET, typename R, bool J64>
+__global__ void __launch_bounds__(256) k_assemble_atomic(BucketDev b, FieldDev f, AsmArgs args) {
+    constexpr int nen = kNen[ET], ng = kNg[ET];
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= b.count) return;
+    int idx[nen];
+#pragma unroll
+    for (int a = 0; a < nen; ++a) idx[a] = __ldg(&b.conn[(int64_t)a * b.count + e]);
+    Gathered<R, J64> el;
+    gather<ET, R, J64>(f, idx, el);
+    R r[kMaxNen][3];
+    bool bad = false;
+    float *nut = args.nut ? args.nut + (int64_t)__ldg(&b.orig[e]) * ng : nullptr;
+    if constexpr (ET == FEA_TET04)
+        tet_residual<R, J64>(el, f, args, r, nut, bad);
+    else
+        element_residual<ET, R, J64>(el, f, args, r, nut, bad);
+    R chk = R(0);
+#pragma unroll
+    for (int a = 0; a < nen; ++a) chk += r[a][0] + r[a][1] + r[a][2];
+    if (bad) set_err(args.err, ERR_DETJ);
+    if (!isfinite(chk)) set_err(args.err, ERR_NONFINITE);
+#pragma unroll
+    for (int a = 0; a < nen; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) atomicAdd(&args.rhs[(int64_t)i * f.n + idx[a]], double(r[a][i]));
+}
+
+template <int ET>
+static cudaError_t launch_atomic_t(const BucketDev &b, const FieldDev &f, const AsmArgs &a, fea_prec prec,
+                                   int threads, cudaStream_t s) {
+    const unsigned blocks = (unsigned)((b.count + threads - 1) / threads);
+    if (prec == FEA_FP64)
+        k_assemble_atomic<ET, double, false><<<blocks, threads, 0, s>>>(b, f, a);
+    else if (b.fp64j)
+        k_assemble_atomic<ET, float, true><<<blocks, threads, 0, s>>>(b, f, a);
+    else
+        k_assemble_atomic<ET, float, false><<<blocks, threads, 0, s>>>(b, f, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_bucket(const BucketDev &b, const FieldDev &f, const AsmArgs &a, fea_prec prec,
+                                   fea_scatter scatter, int threads, cudaStream_t s) {
+    if (b.count == 0) return cudaSuccess;
+    if (threads > 256) threads = 256;
+    (void)scatter;
+    switch (b.etype) {
+        case FEA_TET04: return launch_atomic_t<FEA_TET04>(b, f, a, prec, threads, s);
+        case FEA_PYR05: return launch_atomic_t<FEA_PYR05>(b, f, a, prec, threads, s);
+        case FEA_PEN06: return launch_atomic_t<FEA_PEN06>(b, f, a, prec, threads, s);
+        case FEA_HEX08: return launch_atomic_t<FEA_HEX08>(b, f, a, prec, threads, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// lumped mass (FP64): M_a += sum_g W_g N_a(g); records the first element with
+// det J <= 0 as (bucket-local index) in *bad.
+
+template <int ET>
+__global__ void k_lumped_mass(BucketDev b, const double *xyz, int64_t n, double *mass, unsigned *err,
+                              unsigned long long *bad) {
+    constexpr int nen = kNen[ET], ng = kNg[ET];
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= b.count) return;
+    int idx[nen];
+    double X[nen][3];
+#pragma unroll
+    for (int a = 0; a < nen; ++a) {
+        idx[a] = b.conn[(int64_t)a * b.count + e];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) X[a][i] = xyz[(int64_t)i * n + idx[a]];
+    }
+    double m[nen] = {};
+    bool ok = true;
+#pragma unroll
+    for (int g = 0; g < ng; ++g) {
+        double J[3][3];
+        const double d = jacobian_at<ET, double, double>(X, g, J);
+        if (!(d > 0.0)) ok = false;
+        const double W = c_ref.w[ET][g] * d;
+#pragma unroll
+        for (int a = 0; a < nen; ++a) m[a] += W * c_ref.N[ET][g][a];
+    }
+    if (!ok) {
+        atomicOr(err, ERR_DETJ);
+        atomicMin(bad, (unsigned long long)e);
+    }
+#pragma unroll
+    for (int a = 0; a < nen; ++a) atomicAdd(&mass[idx[a]], m[a]);
+}
+
+cudaError_t launch_lumped_mass(const BucketDev &b, const double *xyz64, int64_t n, double *mass, unsigned *err,
+                               unsigned long long *bad, cudaStream_t s) {
+    if (b.count == 0) return cudaSuccess;
+    const int t = 128;
+    const unsigned blocks = (unsigned)((b.count + t - 1) / t);
+    switch (b.etype) {
+        case FEA_TET04: k_lumped_mass<FEA_TET04><<<blocks, t, 0, s>>>(b, xyz64, n, mass, err, bad); break;
+        case FEA_PYR05: k_lumped_mass<FEA_PYR05><<<blocks, t, 0, s>>>(b, xyz64, n, mass, err, bad); break;
+        case FEA_PEN06: k_lumped_mass<FEA_PEN06><<<blocks, t, 0, s>>>(b, xyz64, n, mass, err, bad); break;
+        case FEA_HEX08: k_lumped_mass<FEA_HEX08><<<blocks, t, 0, s>>>(b, xyz64, n, mass, err, bad); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// periodic fold: add slaves into masters, then copy back
+
+__global__ void k_fold_add(const int32_t *slaves, const int32_t *masters, int64_t ns, double *v, int ncomp, int64_t n) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ns) return;
+    const int64_t s = slaves[k], m = masters[k];
+    for (int c = 0; c < ncomp; ++c) atomicAdd(&v[c * n + m], v[c * n + s]);
+}
+
+__global__ void k_fold_copy(const int32_t *slaves, const int32_t *masters, int64_t ns, double *v, int ncomp,
+                            int64_t n) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ns) return;
+    const int64_t s = slaves[k], m = masters[k];
+    for (int c = 0; c < ncomp; ++c) v[c * n + s] = v[c * n + m];
+}
+
+cudaError_t launch_fold(const int32_t *slaves, const int32_t *masters, int64_t ns, double *v, int ncomp, int64_t n,
+                        cudaStream_t s) {
+    if (ns == 0) return cudaSuccess;
+    const int t = 256;
+    const unsigned blocks = (unsigned)((ns + t - 1) / t);
+    k_fold_add<<<blocks, t, 0, s>>>(slaves, masters, ns, v, ncomp, n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_fold_copy<<<blocks, t, 0, s>>>(slaves, masters, ns, v, ncomp, n);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// RK stage update (streaming): u^(k+1) = a u^n + b (u^(k) + dt R / M), Dirichlet
+// nodes keep u^n; also refreshes the FP32 packed copy (u, v, w, p).
+
+__global__ void k_rk_update(int64_t n, const double *__restrict__ un, double *uk, double *un_out,
+                            const double *__restrict__ rhs, const double *__restrict__ minv,
+                            const uint8_t *__restrict__ dirichlet, const double *__restrict__ p64, float4 *up32,
+                            double a, double b, double dt) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const bool hold = dirichlet && dirichlet[i];
+        const double mi = minv[i];
+        double v[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double u0 = un[c * n + i];
+            v[c] = hold ? u0 : a * u0 + b * (uk[c * n + i] + dt * rhs[c * n + i] * mi);
+            uk[c * n + i] = v[c];
+            if (un_out) un_out[c * n + i] = v[c];
+        }
+        up32[i] = make_float4(float(v[0]), float(v[1]), float(v[2]), float(p64[i]));
+    }
+}
+
+cudaError_t launch_rk_update(int64_t n, const double *un, double *uk, double *un_out, const double *rhs,
+                             const double *minv, const uint8_t *dirichlet, const double *p64, float4 *up32, double a,
+                             double b, double dt, cudaStream_t s) {
+    const int t = 256;
+    const int64_t want = (n + t - 1) / t;
+    const unsigned blocks = (unsigned)(want < 148 * 16 ? (want > 0 ? want : 1) : 148 * 16);
+    k_rk_update<<<blocks, t, 0, s>>>(n, un, uk, un_out, rhs, minv, dirichlet, p64, up32, a, b, dt);
+    return cudaGetLastError();
+}
+
+__global__ void k_pack_field(int64_t n, const double *u64, const double *p64, float4 *up32) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        up32[i] = make_float4(float(u64[i]), float(u64[n + i]), float(u64[2 * n + i]), float(p64[i]));
+}
+
+cudaError_t launch_pack_field(int64_t n, const double *u64, const double *p64, float4 *up32, cudaStream_t s) {
+    const int t = 256;
+    const int64_t want = (n + t - 1) / t;
+    const unsigned blocks = (unsigned)(want < 148 * 16 ? (want > 0 ? want : 1) : 148 * 16);
+    k_pack_field<<<blocks, t, 0, s>>>(n, u64, p64, up32);
+    return cudaGetLastError();
+}
+
+__global__ void k_f32_to_f64(const float *src, double *dst, int64_t count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = double(src[i]);
+}
+
+cudaError_t launch_f32_to_f64(const float *src, double *dst, int64_t count, cudaStream_t s) {
+    const int t = 256;
+    const int64_t want = (count + t - 1) / t;
+    const unsigned blocks = (unsigned)(want < 148 * 16 ? (want > 0 ? want : 1) : 148 * 16);
+    k_f32_to_f64<<<blocks, t, 0, s>>>(src, dst, count);
+    return cudaGetLastError();
+}
+
+__global__ void k_recip(const double *m, double *minv, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        minv[i] = m[i] > 0.0 ? 1.0 / m[i] : 0.0;
+}
+
+cudaError_t launch_recip(const double *m, double *minv, int64_t n, cudaStream_t s) {
+    const int t = 256;
+    const int64_t want = (n + t - 1) / t;
+    const unsigned blocks = (unsigned)(want < 148 * 16 ? (want > 0 ? want : 1) : 148 * 16);
+    k_recip<<<blocks, t, 0, s>>>(m, minv, n);
+    return cudaGetLastError();
+}
+
+}  // namespace fea

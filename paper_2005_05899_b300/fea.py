@@ -1,0 +1,289 @@
+"""Python binding of libfea (include/fea.h): argument marshalling only.
+
+Every step of the assembly runs in the CUDA library; this module converts
+torch tensors / numpy arrays to pointers, checks return codes and raises
+FeaError with the library's message.  There is no CPU fallback: if the
+shared library is missing or no CUDA device is usable, the calls fail.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfea.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EMESH, ENUMERIC, ETIMEOUT, ESTATE, ENOTFOUND = range(9)
+STATUS_NAMES = ("OK", "EINVAL", "ENOMEM", "ECUDA", "EMESH", "ENUMERIC", "ETIMEOUT", "ESTATE", "ENOTFOUND")
+TET04, PYR05, PEN06, HEX08 = 0, 1, 2, 3
+NNODE = (4, 5, 6, 8)
+NGAUSS = (4, 8, 6, 8)
+PREC = {"fp64": 0, "mixed": 1}
+CLOSURE = {"none": 0, "vreman": 1, "mlp": 2}
+SCATTER = {"auto": 0, "atomic": 1, "chunk": 2}
+TERM_CONV, TERM_VISC, TERM_SGS, TERM_PRES, TERM_ALL = 1, 2, 4, 8, 15
+
+EXPORTED = (
+    "fea_create", "fea_destroy", "fea_last_error", "fea_version", "fea_mesh_upload", "fea_mesh_info",
+    "fea_lumped_mass", "fea_field_upload", "fea_assemble_rhs", "fea_assemble_rhs_batched", "fea_periodic_fold",
+    "fea_rk_stage", "fea_rk_step_graph", "fea_state_download", "fea_get_plan", "fea_set_plan", "fea_autotune",
+    "fea_sync_status", "fea_launch_count", "fea_profile_enable", "fea_profile_read",
+)
+
+
+class FeaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"FEA_{name}: {msg}")
+        self.status = status
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("xyz", ctypes.POINTER(ctypes.c_double)),
+                ("n_elem", ctypes.c_int64 * 4), ("conn", ctypes.POINTER(ctypes.c_int32) * 4),
+                ("periodic_master", ctypes.POINTER(ctypes.c_int32)), ("dirichlet", ctypes.POINTER(ctypes.c_uint8)),
+                ("fp64_jac", ctypes.POINTER(ctypes.c_uint8) * 4)]
+
+
+class Plan(ctypes.Structure):
+    _fields_ = [("scatter", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
+                ("chunk_elems", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {"scatter": self.scatter, "threads_per_block": self.threads_per_block,
+                "chunk_elems": self.chunk_elems}
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libfea.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise FeaError(ECUDA, f"{LIB_PATH} is missing: run paper_2005_05899_b300/build.py (no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, u32, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double
+        L.fea_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp)]
+        L.fea_destroy.argtypes = [vp]
+        L.fea_destroy.restype = None
+        L.fea_last_error.argtypes = [vp]
+        L.fea_last_error.restype = ctypes.c_char_p
+        L.fea_version.restype = ctypes.c_char_p
+        L.fea_launch_count.argtypes = [vp]
+        L.fea_launch_count.restype = i64
+        L.fea_mesh_upload.argtypes = [vp, ctypes.POINTER(MeshDesc), vp, ctypes.POINTER(i32)]
+        L.fea_mesh_info.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.fea_lumped_mass.argtypes = [vp, i32, vp, vp]
+        L.fea_field_upload.argtypes = [vp, i32, vp, vp, ctypes.c_int, dbl, dbl, vp]
+        L.fea_assemble_rhs.argtypes = [vp, i32, ctypes.c_int, ctypes.c_int, u32, ctypes.c_int, vp, vp, vp]
+        L.fea_assemble_rhs_batched.argtypes = [vp, ctypes.POINTER(i32), i32, ctypes.c_int, ctypes.c_int, u32,
+                                               ctypes.POINTER(vp), vp]
+        L.fea_periodic_fold.argtypes = [vp, i32, vp, i32, vp]
+        L.fea_rk_stage.argtypes = [vp, i32, i32, dbl, ctypes.c_int, ctypes.c_int, vp]
+        L.fea_rk_step_graph.argtypes = [vp, i32, dbl, ctypes.c_int, ctypes.c_int, vp]
+        L.fea_state_download.argtypes = [vp, i32, vp, vp]
+        L.fea_get_plan.argtypes = [vp, i32, ctypes.POINTER(Plan)]
+        L.fea_set_plan.argtypes = [vp, i32, ctypes.POINTER(Plan)]
+        L.fea_autotune.argtypes = [vp, i32, ctypes.c_int, ctypes.c_int, ctypes.c_char_p]
+        L.fea_sync_status.argtypes = [vp, vp]
+        L.fea_profile_enable.argtypes = [vp, ctypes.c_int]
+        L.fea_profile_read.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(dbl), ctypes.POINTER(i64),
+                                       ctypes.c_int]
+        for name in EXPORTED:
+            f = getattr(L, name)
+            if f.restype is ctypes.c_int and name not in ("fea_destroy",):
+                f.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(t) -> int:
+    """Address of a torch tensor (any device) or a numpy array (host)."""
+    if t is None:
+        return 0
+    if isinstance(t, np.ndarray):
+        assert t.flags.c_contiguous
+        return t.ctypes.data
+    assert t.is_contiguous(), "tensor must be contiguous"
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Context:
+    """One libfea context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._lib = lib()
+        h = ctypes.c_void_p()
+        st = self._lib.fea_create(device, ctypes.byref(h))
+        if st != OK:
+            raise FeaError(st, f"fea_create(device={device}) failed (no usable CUDA device?)")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.fea_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, st: int):
+        if st != OK:
+            raise FeaError(st, self._lib.fea_last_error(self.handle).decode())
+
+    @property
+    def launch_count(self) -> int:
+        return int(self._lib.fea_launch_count(self.handle))
+
+    def profile(self, on: bool = True):
+        self.check(self._lib.fea_profile_enable(self.handle, 1 if on else 0))
+
+    def profile_read(self, etype: int, fp64_jac: int = 0, reset: bool = False):
+        """(summed kernel ms, launches) of one category since the last reset."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        self.check(self._lib.fea_profile_read(self.handle, etype, fp64_jac, ctypes.byref(ms), ctypes.byref(n),
+                                              1 if reset else 0))
+        return ms.value, n.value
+
+    def sync_status(self, stream=None):
+        self.check(self._lib.fea_sync_status(self.handle, _stream(stream)))
+
+    def upload_mesh(self, mesh, stream=None) -> "DeviceMesh":
+        """mesh: meshgen.Mesh-like object (xyz (N,3), conn dict, optional
+        periodic_master, dirichlet, fp64_flag).  Host arrays only."""
+        xyz = np.ascontiguousarray(np.asarray(mesh.xyz, dtype=np.float64).T)
+        keep = [xyz]
+        d = MeshDesc()
+        d.n_nodes = xyz.shape[1]
+        d.xyz = xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        n_elem = [0, 0, 0, 0]
+        for t in range(4):
+            c = mesh.conn.get(t)
+            if c is not None and len(c):
+                c = np.ascontiguousarray(c, dtype=np.int32)
+                keep.append(c)
+                d.conn[t] = c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+                d.n_elem[t] = c.shape[0]
+                n_elem[t] = c.shape[0]
+            f = getattr(mesh, "fp64_flag", {}).get(t) if getattr(mesh, "fp64_flag", None) else None
+            if f is not None and len(f):
+                f = np.ascontiguousarray(f, dtype=np.uint8)
+                keep.append(f)
+                d.fp64_jac[t] = f.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        if getattr(mesh, "periodic_master", None) is not None:
+            pm = np.ascontiguousarray(mesh.periodic_master, dtype=np.int32)
+            keep.append(pm)
+            d.periodic_master = pm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        if getattr(mesh, "dirichlet", None) is not None:
+            dm = np.ascontiguousarray(mesh.dirichlet, dtype=np.uint8)
+            keep.append(dm)
+            d.dirichlet = dm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        mid = ctypes.c_int32(-1)
+        self.check(self._lib.fea_mesh_upload(self.handle, ctypes.byref(d), _stream(stream), ctypes.byref(mid)))
+        return DeviceMesh(self, mid.value, xyz.shape[1], n_elem)
+
+    def assemble_batched(self, meshes: Sequence["DeviceMesh"], outs, prec="mixed", closure="vreman",
+                         mask=TERM_ALL, stream=None):
+        n = len(meshes)
+        ids = (ctypes.c_int32 * n)(*[m.id for m in meshes])
+        ptrs = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
+        self.check(self._lib.fea_assemble_rhs_batched(self.handle, ids, n, PREC[prec], CLOSURE[closure], mask,
+                                                      ptrs, _stream(stream)))
+
+
+class DeviceMesh:
+    def __init__(self, ctx: Context, mid: int, n_nodes: int, n_elem):
+        self.ctx = ctx
+        self.id = mid
+        self.n_nodes = n_nodes
+        self.n_elem = list(n_elem)
+
+    @property
+    def n_elem_total(self) -> int:
+        return sum(self.n_elem)
+
+    @property
+    def n_gauss_total(self) -> int:
+        return sum(e * g for e, g in zip(self.n_elem, NGAUSS))
+
+    def _L(self):
+        return self.ctx._lib
+
+    def upload_field(self, u, p, nu: float, c_vreman: float = 0.07, stream=None):
+        """u: [3][n] (or (n,3) numpy, transposed here), p: [n]; float64 or float32;
+        torch tensor (any device) or numpy (host)."""
+        if isinstance(u, np.ndarray) and u.ndim == 2 and u.shape == (self.n_nodes, 3):
+            u = np.ascontiguousarray(u.T)
+        dtype = 0
+        if isinstance(u, np.ndarray):
+            dtype = 0 if u.dtype == np.float64 else 1
+            u = np.ascontiguousarray(u)
+            p = np.ascontiguousarray(p, dtype=u.dtype)
+        else:
+            import torch
+            dtype = 0 if u.dtype == torch.float64 else 1
+        self._keep = (u, p)
+        self.ctx.check(self._L().fea_field_upload(self.ctx.handle, self.id, _ptr(u), _ptr(p), dtype, float(nu),
+                                                  float(c_vreman), _stream(stream)))
+
+    def assemble(self, out, prec="mixed", closure="vreman", mask=TERM_ALL, scatter="auto", nut_out=None,
+                 stream=None):
+        """out: float64 device tensor [3][n] (overwritten); nut_out: optional
+        float32 device tensor [n_gauss_total]."""
+        self.ctx.check(self._L().fea_assemble_rhs(self.ctx.handle, self.id, PREC[prec], CLOSURE[closure], mask,
+                                                  SCATTER[scatter], _ptr(out), _ptr(nut_out), _stream(stream)))
+        return out
+
+    def lumped_mass(self, out, stream=None):
+        self.ctx.check(self._L().fea_lumped_mass(self.ctx.handle, self.id, _ptr(out), _stream(stream)))
+        return out
+
+    def fold(self, v, stream=None):
+        ncomp = 1 if v.dim() == 1 else v.shape[0]
+        self.ctx.check(self._L().fea_periodic_fold(self.ctx.handle, self.id, _ptr(v), ncomp, _stream(stream)))
+        return v
+
+    def rk_stage(self, stage: int, dt: float, prec="mixed", closure="vreman", stream=None):
+        self.ctx.check(self._L().fea_rk_stage(self.ctx.handle, self.id, stage, float(dt), PREC[prec],
+                                              CLOSURE[closure], _stream(stream)))
+
+    def rk_step_graph(self, dt: float, prec="mixed", closure="vreman", stream=None):
+        self.ctx.check(self._L().fea_rk_step_graph(self.ctx.handle, self.id, float(dt), PREC[prec],
+                                                   CLOSURE[closure], _stream(stream)))
+
+    def state(self, out, stream=None):
+        self.ctx.check(self._L().fea_state_download(self.ctx.handle, self.id, _ptr(out), _stream(stream)))
+        return out
+
+    def get_plan(self) -> Plan:
+        p = Plan()
+        self.ctx.check(self._L().fea_get_plan(self.ctx.handle, self.id, ctypes.byref(p)))
+        return p
+
+    def set_plan(self, scatter="atomic", threads_per_block=256, chunk_elems=256):
+        p = Plan(SCATTER[scatter], threads_per_block, chunk_elems, 0)
+        self.ctx.check(self._L().fea_set_plan(self.ctx.handle, self.id, ctypes.byref(p)))
+
+    def autotune(self, prec="mixed", closure="vreman", cache_path: Optional[str] = None):
+        self.ctx.check(self._L().fea_autotune(self.ctx.handle, self.id, PREC[prec], CLOSURE[closure],
+                                              cache_path.encode() if cache_path else None))
+        return self.get_plan()
