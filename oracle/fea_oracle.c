@@ -27,7 +27,9 @@
  *     triangle x 2-point Gauss; HEX08 2x2x2 Gauss; PYR05 8-point collapsed
  *     (Duffy) rule with 2-point Gauss-Jacobi(2,0) in the axial direction;
  *   - Vreman filter width Delta = V_e^(1/3), V_e = sum_g W_g;
- *   - Vreman nu_t = 0 when alpha:alpha == 0 or B_beta <= 0;
+ *   - Vreman nu_t = 0 when alpha:alpha == 0 or B_beta <= 0, with B_beta
+ *     summed as squared cross products of the rows of G (Lagrange identity,
+ *     equal to the printed minor-difference form up to rounding);
  *   - pressure term in gradient form, viscous term in 2 eps form, natural
  *     boundary terms dropped.
  *
@@ -287,24 +289,33 @@ int orc_element_geometry(int etype, const double *X /*[nen][3]*/, double *N /*[n
 /* ---------------------------------------------------------------------- */
 /* Vreman (2004) eddy viscosity at one point, with G_ij = du_i/dx_j:
  *   alpha_ij = du_j/dx_i = G_ji,
- *   beta_ij  = Delta^2 sum_m alpha_mi alpha_mj,
+ *   beta_ij  = Delta^2 sum_m alpha_mi alpha_mj   (beta = Delta^2 alpha^T alpha),
  *   B_beta   = b11 b22 - b12^2 + b11 b33 - b13^2 + b22 b33 - b23^2,
- *   nu_t     = c sqrt(B_beta / (alpha_ij alpha_ij)),  0 if alpha:alpha == 0 or B_beta <= 0. */
+ *   nu_t     = c sqrt(B_beta / (alpha_ij alpha_ij)),  0 if alpha:alpha == 0 or B_beta <= 0.
+ * Each term b_ii b_jj - b_ij^2 is a principal 2x2 minor of the Gram matrix
+ * alpha^T alpha, equal (Lagrange identity) to Delta^4 |a_i x a_j|^2 with a_i
+ * the i-th column of alpha, i.e. the i-th row of G.  B_beta is evaluated in
+ * that sum-of-squares form: the same number up to rounding, without the
+ * cancellation of the difference form where B_beta -> 0 (then the square
+ * root would amplify rounding to ~1e-8 relative in nu_t). */
+static void cross3(const double *a, const double *b, double *c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
 double orc_vreman(const double *G /*[3][3]*/, double delta, double c) {
-    double al[3][3], be[3][3], aa = 0.0;
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            al[i][j] = G[3 * j + i];
-            aa += al[i][j] * al[i][j];
-        }
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            double s = 0.0;
-            for (int m = 0; m < 3; ++m) s += al[m][i] * al[m][j];
-            be[i][j] = delta * delta * s;
-        }
-    const double B = be[0][0] * be[1][1] - be[0][1] * be[0][1] + be[0][0] * be[2][2] - be[0][2] * be[0][2]
-                   + be[1][1] * be[2][2] - be[1][2] * be[1][2];
+    double aa = 0.0;
+    for (int k = 0; k < 9; ++k) aa += G[k] * G[k];
+    const double *a1 = G, *a2 = G + 3, *a3 = G + 6;   /* columns of alpha = rows of G */
+    double x12[3], x13[3], x23[3];
+    cross3(a1, a2, x12);
+    cross3(a1, a3, x13);
+    cross3(a2, a3, x23);
+    double minors = 0.0;
+    for (int i = 0; i < 3; ++i) minors += x12[i] * x12[i] + x13[i] * x13[i] + x23[i] * x23[i];
+    const double d2 = delta * delta;
+    const double B = d2 * d2 * minors;
     if (aa == 0.0 || B <= 0.0) return 0.0;
     return c * sqrt(B / aa);
 }

@@ -52,8 +52,11 @@ __device__ __forceinline__ R inv3(const R J[3][3], R Ji[3][3]) {
     return det;
 }
 
-// Vreman: beta' = G G^T (so that beta = Delta^2 beta'), B_beta = Delta^4 B',
-// nu_t = c Delta^2 sqrt(B' / (G:G)); zero when G:G == 0 or B' <= 0.
+// Vreman: beta = Delta^2 alpha^T alpha with alpha = G^T, so every principal
+// 2x2 minor of beta is Delta^4 |g_i x g_j|^2 (g_i = row i of G, Lagrange
+// identity) and B_beta = Delta^4 (|g1 x g2|^2 + |g1 x g3|^2 + |g2 x g3|^2):
+// a sum of squares, free of the cancellation of the difference form.
+// nu_t = c Delta^2 sqrt(B' / (G:G)), zero when G:G == 0 or B' == 0.
 template <typename R>
 __device__ __forceinline__ R vreman(const R G[3][3], R delta2, R c) {
     R aa = R(0);
@@ -61,13 +64,15 @@ __device__ __forceinline__ R vreman(const R G[3][3], R delta2, R c) {
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) aa += G[i][j] * G[i][j];
-    R b11 = G[0][0] * G[0][0] + G[0][1] * G[0][1] + G[0][2] * G[0][2];
-    R b22 = G[1][0] * G[1][0] + G[1][1] * G[1][1] + G[1][2] * G[1][2];
-    R b33 = G[2][0] * G[2][0] + G[2][1] * G[2][1] + G[2][2] * G[2][2];
-    R b12 = G[0][0] * G[1][0] + G[0][1] * G[1][1] + G[0][2] * G[1][2];
-    R b13 = G[0][0] * G[2][0] + G[0][1] * G[2][1] + G[0][2] * G[2][2];
-    R b23 = G[1][0] * G[2][0] + G[1][1] * G[2][1] + G[1][2] * G[2][2];
-    R B = b11 * b22 - b12 * b12 + b11 * b33 - b13 * b13 + b22 * b33 - b23 * b23;
+    R B = R(0);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const int i = p == 2 ? 1 : 0, j = p == 0 ? 1 : 2;   // (0,1), (0,2), (1,2)
+        const R x = G[i][1] * G[j][2] - G[i][2] * G[j][1];
+        const R y = G[i][2] * G[j][0] - G[i][0] * G[j][2];
+        const R z = G[i][0] * G[j][1] - G[i][1] * G[j][0];
+        B += x * x + y * y + z * z;
+    }
     if (!(aa > R(0)) || !(B > R(0))) return R(0);
     return c * delta2 * sqrt(B / aa);
 }

@@ -422,3 +422,24 @@ def test_bad_inputs_are_rejected():
     oob[0, 0] = 7
     with pytest.raises(O.OracleError):
         O.assemble_rhs(O.OracleMesh(m.xyz, {O.TET04: oob}), np.zeros((4, 3)), np.zeros(4), 0.1)
+
+
+def test_vreman_sum_of_squares_equals_printed_difference_form():
+    """B_beta as the sum of principal 2x2 minors of beta (the printed form)
+    equals the sum of squared cross products of the rows of G; both forms
+    agree to round-off wherever B_beta is not near zero, and the oracle's
+    sum-of-squares form stays non-negative where the printed form cancels."""
+    rng = np.random.default_rng(31)
+    c, delta = 0.07, 0.4
+    for _ in range(200):
+        G = rng.standard_normal((3, 3))
+        al = G.T
+        be = delta ** 2 * al.T @ al
+        B = (be[0, 0] * be[1, 1] - be[0, 1] ** 2 + be[0, 0] * be[2, 2] - be[0, 2] ** 2
+             + be[1, 1] * be[2, 2] - be[1, 2] ** 2)
+        expect = c * math.sqrt(B / np.sum(al * al)) if B > 0 else 0.0
+        assert math.isclose(O.vreman(G, delta, c), expect, rel_tol=1e-12)
+    # nearly parallel rows: B_beta ~ 1e-20 relative, still >= 0 and tiny
+    G = np.array([[1.0, 2.0, 3.0], [1.0, 2.0, 3.0 + 1e-10], [0, 0, 0]])
+    v = O.vreman(G, delta, c)
+    assert 0.0 <= v < 1e-9
