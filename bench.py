@@ -220,9 +220,8 @@ def run_ours(args):
     dm = ctx.upload_mesh(mesh)
     log(f"[bench] upload {time.time() - t:.1f}s")
     dm.upload_field(field.u, field.p, field.nu, field.c_vreman)
-    if args.autotune:
-        plan = dm.autotune(prec="mixed", closure="vreman")
-        log(f"[bench] plan {plan.as_dict()}")
+    plan = dm.autotune(prec="mixed", closure="vreman") if args.autotune else dm.get_plan()
+    log(f"[bench] plan {plan.as_dict()}")
     E = mesh.n_elem_total
     stream = torch.cuda.current_stream()
 
@@ -300,7 +299,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "accumulation": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "elements": E, "nodes": dm.n_nodes,
                        "counts": mesh.counts(), "l2": "inputs larger than L2 (no flush needed)",
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU", "plan": plan.as_dict()},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": "TET04 assembly (mixed, Vreman)",
                          "peak_kind": f"{peak_kind} hbm_gbs", "alg_bytes_per_launch": alg,
@@ -325,7 +324,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-axis", type=int, default=170, help="grid nodes per axis of the airplane-like mesh")
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default launch plan instead of timing the candidates")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()

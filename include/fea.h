@@ -109,10 +109,12 @@ typedef struct {
 
 /* Launch plan of one mesh (chosen by fea_autotune or set by hand). */
 typedef struct {
-    int32_t scatter;            /* fea_scatter (not AUTO) */
-    int32_t threads_per_block;  /* element kernels: 64..1024, multiple of 32 */
-    int32_t chunk_elems;        /* elements per chunk for FEA_SCATTER_CHUNK */
-    int32_t reserved;
+    int32_t scatter;            /* fea_scatter (not AUTO); FEA_FP64 always uses ATOMIC */
+    int32_t threads_per_block;  /* element kernels: multiple of 32 in [32, 1024] (capped at 256) */
+    int32_t chunk_elems;        /* elements per chunk for FEA_SCATTER_CHUNK: multiple of 32 in [32, 4096] */
+    int32_t chunk_acc;          /* FEA_SCATTER_CHUNK nodal sums inside a chunk: 0 = FP32,
+                                   1 = compensated two-float sums (about 48 significant bits);
+                                   sums across chunks are FP64 atomics in both cases */
 } fea_plan;
 
 /* ---- context ------------------------------------------------------------ */

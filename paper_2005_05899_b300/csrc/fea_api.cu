@@ -164,6 +164,7 @@ RefTables make_tables() {
             double N[kMaxNen], dN[kMaxNen][3];
             shape_at(et, pts[g], N, dN);
             T.w[et][g] = w[g];
+            for (int j = 0; j < 3; ++j) T.xi[et][g][j] = pts[g][j];
             for (int a = 0; a < kNen[et]; ++a) {
                 T.N[et][g][a] = N[a];
                 for (int j = 0; j < 3; ++j) T.dN[et][g][a][j] = dN[a][j];
@@ -199,13 +200,17 @@ struct DevBuf {
 struct Bucket {
     int etype = 0, fp64j = 0;
     int64_t count = 0;
+    std::vector<int32_t> conn_h;  // host copy [nen][count] (chunk tables are rebuilt from it)
     DevBuf<int32_t> conn, orig;
-    DevBuf<uint16_t> lconn;
-    DevBuf<int64_t> chunk_off;
-    DevBuf<int32_t> chunk_nodes;
+    // chunk tables
     int32_t chunk_elems = 0;
     int64_t n_chunks = 0;
     int32_t max_chunk_nodes = 0;
+    DevBuf<uint16_t> lconn;
+    DevBuf<int64_t> chunk_off;
+    DevBuf<int32_t> chunk_nodes;
+    DevBuf<float4> chunk_rec;
+    DevBuf<uint32_t> inc_range;
     BucketDev dev() const {
         BucketDev b;
         b.etype = etype;
@@ -218,6 +223,8 @@ struct Bucket {
         b.lconn = lconn.p;
         b.chunk_node_off = chunk_off.p;
         b.chunk_nodes = chunk_nodes.p;
+        b.chunk_rec = chunk_rec.p;
+        b.inc_range = inc_range.p;
         b.max_chunk_nodes = max_chunk_nodes;
         return b;
     }
@@ -244,7 +251,9 @@ struct Mesh {
     DevBuf<float> stage_f32;
     bool has_field = false;
     double nu = 0.0, c_vreman = 0.0;
-    fea_plan plan{FEA_SCATTER_ATOMIC, 256, 256, 0};
+    std::vector<double> xyz_h;          // host FP64 coordinates [3][n] (chunk-local offsets)
+    std::vector<int32_t> inc_total;     // element incidences per node over all buckets
+    fea_plan plan{FEA_SCATTER_CHUNK, 256, 256, 0};
     GraphCache graph;
     ~Mesh() {
         if (graph.exec) cudaGraphExecDestroy(graph.exec);
@@ -272,6 +281,7 @@ struct ProfRec {
 
 struct fea_ctx {
     int device = 0;
+    int sms = 148;
     bool profiling = false;
     std::vector<ProfRec> prof;
     std::string err;
@@ -279,6 +289,8 @@ struct fea_ctx {
     unsigned long long *d_bad = nullptr;
     std::vector<std::unique_ptr<Mesh>> meshes;
     cudaStream_t capture = nullptr;
+    cudaStream_t side = nullptr;      // FP64-Jacobian categories run here, overlapped
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t launches = 0;
 };
 
@@ -326,35 +338,158 @@ int64_t type_nut_offset(const Mesh &m, int et) {
     return off;
 }
 
+// Chunk tables of one bucket for chunks of C elements (see BucketDev).
+fea_status build_chunks(fea_ctx *ctx, Mesh &m, Bucket &b, int C) {
+    const int nen = kNen[b.etype];
+    const int np = lconn_pitch(b.etype);
+    const int64_t cnt = b.count;
+    const int64_t nch = (cnt + C - 1) / C;
+    std::vector<uint16_t> lconn((size_t)2 * np * cnt, 0);
+    std::vector<int64_t> off((size_t)nch + 1, 0);
+    std::vector<int32_t> nodes_n((size_t)nch, 0);
+    std::vector<float4> recs;
+    std::vector<uint32_t> ranges;
+    recs.reserve((size_t)(cnt / 2 + 64));
+    ranges.reserve((size_t)(cnt / 2 + 64));
+    std::vector<int32_t> ids((size_t)nen * C), uniq, lcount, order, rank, lstart, fillp;
+    std::vector<int32_t> tmp((size_t)nen * C);
+    int32_t maxL = 0;
+    const int64_t n = m.n;
+    for (int64_t k = 0; k < nch; ++k) {
+        const int64_t e0 = k * C;
+        const int ne = (int)std::min<int64_t>(C, cnt - e0);
+        size_t q = 0;
+        for (int a = 0; a < nen; ++a)
+            for (int el = 0; el < ne; ++el) ids[q++] = b.conn_h[(size_t)a * cnt + e0 + el];
+        uniq.assign(ids.begin(), ids.begin() + q);
+        std::sort(uniq.begin(), uniq.end());
+        uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+        const int L = (int)uniq.size();
+        if (L > 65532 || nen * ne > 65535)
+            return fail(ctx, FEA_EINVAL, "chunk of %d elements is too large for 16-bit local indices", C);
+        maxL = std::max(maxL, (L + 3) & ~3);
+        // incidence of every (element, vertex) as an index into uniq
+        lcount.assign(L, 0);
+        q = 0;
+        for (int a = 0; a < nen; ++a)
+            for (int el = 0; el < ne; ++el) {
+                const int l = (int)(std::lower_bound(uniq.begin(), uniq.end(), ids[q]) - uniq.begin());
+                tmp[q++] = l;
+                lcount[l]++;
+            }
+        // local order: decreasing incidence count, then node id (uniform loops in the node phase)
+        order.resize(L);
+        for (int l = 0; l < L; ++l) order[l] = l;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return lcount[x] > lcount[y]; });
+        rank.resize(L);
+        for (int l = 0; l < L; ++l) rank[order[l]] = l;
+        lstart.assign(L + 1, 0);
+        for (int l = 0; l < L; ++l) lstart[l + 1] = lstart[l] + lcount[order[l]];
+        fillp.assign(lstart.begin(), lstart.end() - 1);
+        q = 0;
+        for (int a = 0; a < nen; ++a)
+            for (int el = 0; el < ne; ++el) {
+                const int l = rank[tmp[q++]];
+                uint16_t *rec = &lconn[(size_t)2 * np * (e0 + el)];
+                rec[a] = (uint16_t)l;
+                rec[np + a] = (uint16_t)(fillp[l]++);
+            }
+        const double ox = m.xyz_h[uniq[0]], oy = m.xyz_h[n + uniq[0]], oz = m.xyz_h[2 * n + uniq[0]];
+        for (int l = 0; l < L; ++l) {
+            const int32_t id = uniq[order[l]];
+            const bool shared = lcount[order[l]] != m.inc_total[id];
+            const uint32_t bits = (uint32_t)id | (shared ? 0x80000000u : 0u);
+            float w;
+            memcpy(&w, &bits, 4);
+            recs.push_back(make_float4((float)(m.xyz_h[id] - ox), (float)(m.xyz_h[n + id] - oy),
+                                       (float)(m.xyz_h[2 * n + id] - oz), w));
+            ranges.push_back((uint32_t)lstart[l] | ((uint32_t)lcount[order[l]] << 16));
+        }
+        const int Lp = (L + 3) & ~3;   // pad to 16-byte multiples; pad entries are never read
+        for (int l = L; l < Lp; ++l) {
+            recs.push_back(recs[recs.size() - 1]);
+            ranges.push_back(0u);
+        }
+        nodes_n[k] = L;
+        off[k + 1] = off[k] + Lp;
+    }
+    CK(b.lconn.alloc(lconn.size()));
+    CK(b.chunk_off.alloc(off.size()));
+    CK(b.chunk_nodes.alloc(nodes_n.size()));
+    CK(b.chunk_rec.alloc(recs.size()));
+    CK(b.inc_range.alloc(ranges.size()));
+    CK(cudaMemcpy(b.lconn.p, lconn.data(), lconn.size() * 2, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b.chunk_off.p, off.data(), off.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b.chunk_nodes.p, nodes_n.data(), nodes_n.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b.chunk_rec.p, recs.data(), recs.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b.inc_range.p, ranges.data(), ranges.size() * 4, cudaMemcpyHostToDevice));
+    b.chunk_elems = C;
+    b.n_chunks = nch;
+    b.max_chunk_nodes = maxL;
+    return FEA_OK;
+}
+
+fea_status ensure_chunks(fea_ctx *ctx, Mesh &m, int C) {
+    for (auto &bp : m.buckets) {
+        if (bp->count == 0 || (bp->lconn.p && bp->chunk_elems == C)) continue;
+        fea_status st = build_chunks(ctx, m, *bp, C);
+        if (st) return st;
+    }
+    return FEA_OK;
+}
+
 fea_status assemble_into(fea_ctx *ctx, Mesh &m, fea_prec prec, fea_closure closure, uint32_t mask,
                          fea_scatter scatter, double *rhs, float *nut, cudaStream_t s) {
     CK(cudaMemsetAsync(rhs, 0, sizeof(double) * 3 * m.n, s));
     FieldDev f = m.field();
     if (scatter == FEA_SCATTER_AUTO) scatter = (fea_scatter)m.plan.scatter;
-    for (auto &bp : m.buckets) {
-        const Bucket &b = *bp;
-        if (!b.count) continue;
-        AsmArgs a;
-        a.mask = mask;
-        a.closure = closure;
-        a.rhs = rhs;
-        a.nut = nut ? nut + type_nut_offset(m, b.etype) : nullptr;
-        a.err = ctx->d_err;
-        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-        if (ctx->profiling) CK(cudaStreamIsCapturing(s, &cap));
-        ProfRec pr{b.etype, b.fp64j, nullptr, nullptr};
-        const bool timed = ctx->profiling && cap == cudaStreamCaptureStatusNone;
-        if (timed) {
-            CK(cudaEventCreate(&pr.e0));
-            CK(cudaEventCreate(&pr.e1));
-            CK(cudaEventRecord(pr.e0, s));
+    // FP64-Jacobian categories (FP64 pipe) go first, on a side stream, so
+    // that they overlap the FP32-bound categories on the caller's stream.
+    bool forked = false;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (auto &bp : m.buckets) {
+            const Bucket &b = *bp;
+            if (!b.count) continue;
+            const bool side = prec == FEA_MIXED && b.fp64j;
+            if (side != (pass == 0)) continue;
+            cudaStream_t ls = s;
+            if (side) {
+                if (!forked) {
+                    CK(cudaEventRecord(ctx->ev_fork, s));
+                    CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+                    forked = true;
+                }
+                ls = ctx->side;
+            }
+            AsmArgs a;
+            a.mask = mask;
+            a.closure = closure;
+            a.rhs = rhs;
+            a.nut = nut ? nut + type_nut_offset(m, b.etype) : nullptr;
+            a.err = ctx->d_err;
+            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+            if (ctx->profiling) CK(cudaStreamIsCapturing(s, &cap));
+            ProfRec pr{b.etype, b.fp64j, nullptr, nullptr};
+            const bool timed = ctx->profiling && cap == cudaStreamCaptureStatusNone;
+            if (timed) {
+                CK(cudaEventCreate(&pr.e0));
+                CK(cudaEventCreate(&pr.e1));
+                CK(cudaEventRecord(pr.e0, ls));
+            }
+            if (prec == FEA_MIXED && scatter == FEA_SCATTER_CHUNK && b.lconn.p)
+                CK(launch_assemble_chunk(b.dev(), f, a, m.plan.threads_per_block, m.plan.chunk_acc, ls));
+            else
+                CK(launch_assemble_bucket(b.dev(), f, a, prec, FEA_SCATTER_ATOMIC, m.plan.threads_per_block, ls));
+            ctx->launches++;
+            if (timed) {
+                CK(cudaEventRecord(pr.e1, ls));
+                ctx->prof.push_back(pr);
+            }
         }
-        CK(launch_assemble_bucket(b.dev(), f, a, prec, scatter, m.plan.threads_per_block, s));
-        ctx->launches++;
-        if (timed) {
-            CK(cudaEventRecord(pr.e1, s));
-            ctx->prof.push_back(pr);
-        }
+    }
+    if (forked) {
+        CK(cudaEventRecord(ctx->ev_join, ctx->side));
+        CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
     }
     return FEA_OK;
 }
@@ -404,10 +539,17 @@ fea_status fea_create(int device, fea_ctx **out) {
     fea_status st = FEA_OK;
     do {
         if (cudaSetDevice(device) != cudaSuccess) { st = FEA_ECUDA; break; }
+        if (cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+            st = FEA_ECUDA;
+            break;
+        }
         if (cudaMalloc(&ctx->d_err, sizeof(unsigned)) != cudaSuccess) { st = FEA_ENOMEM; break; }
         if (cudaMalloc(&ctx->d_bad, sizeof(unsigned long long)) != cudaSuccess) { st = FEA_ENOMEM; break; }
         if (cudaMemset(ctx->d_err, 0, sizeof(unsigned)) != cudaSuccess) { st = FEA_ECUDA; break; }
         if (cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking) != cudaSuccess) { st = FEA_ECUDA; break; }
+        if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess) { st = FEA_ECUDA; break; }
+        if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess) { st = FEA_ECUDA; break; }
+        if (cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) { st = FEA_ECUDA; break; }
         RefTables t = make_tables();
         if (upload_ref_tables(t) != cudaSuccess) { st = FEA_ECUDA; break; }
     } while (0);
@@ -431,6 +573,9 @@ void fea_destroy(fea_ctx *ctx) {
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->d_bad) cudaFree(ctx->d_bad);
     if (ctx->capture) cudaStreamDestroy(ctx->capture);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     delete ctx;
 }
 
@@ -444,6 +589,7 @@ fea_status fea_mesh_upload(fea_ctx *ctx, const fea_mesh_desc *d, void *stream, i
         return fail(ctx, FEA_EINVAL, "n_nodes must be in [1, 2^31) with coordinates");
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(ctx->device));
+    fea_status st_up = FEA_OK;
     const int64_t n = d->n_nodes;
     auto m = std::make_unique<Mesh>();
     m->n = n;
@@ -516,6 +662,7 @@ fea_status fea_mesh_upload(fea_ctx *ctx, const fea_mesh_desc *d, void *stream, i
             b->etype = t;
             b->fp64j = flag;
             b->count = cnt;
+            b->conn_h = conn;
             CK(b->conn.alloc(conn.size()));
             CK(b->orig.alloc(orig.size()));
             CK(cudaMemcpy(b->conn.p, conn.data(), conn.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -524,6 +671,10 @@ fea_status fea_mesh_upload(fea_ctx *ctx, const fea_mesh_desc *d, void *stream, i
         }
     }
     // node arrays
+    m->xyz_h.assign(X, X + 3 * n);
+    m->inc_total.assign((size_t)n, 0);
+    for (int t = 0; t < 4; ++t)
+        for (int64_t k = 0; k < d->n_elem[t] * kNen[t]; ++k) m->inc_total[d->conn[t][k]]++;
     CK(m->xyz64.alloc(3 * n));
     CK(cudaMemcpy(m->xyz64.p, X, sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
     {
@@ -579,6 +730,7 @@ fea_status fea_mesh_upload(fea_ctx *ctx, const fea_mesh_desc *d, void *stream, i
         CK(launch_recip(folded.p, m->minv.p, n, s));
         CK(cudaStreamSynchronize(s));
     }
+    if ((st_up = ensure_chunks(ctx, *m, m->plan.chunk_elems))) return st_up;
     CK(m->un.alloc(3 * n));
     CK(m->uk.alloc(3 * n));
     CK(m->p64.alloc(n));
@@ -758,7 +910,16 @@ fea_status fea_set_plan(fea_ctx *ctx, int32_t mesh, const fea_plan *plan) {
         return fail(ctx, FEA_EINVAL, "plan scatter must be ATOMIC or CHUNK");
     if (plan->threads_per_block < 32 || plan->threads_per_block > 1024 || plan->threads_per_block % 32)
         return fail(ctx, FEA_EINVAL, "threads_per_block must be a multiple of 32 in [32, 1024]");
-    if (plan->scatter == FEA_SCATTER_CHUNK) return fail(ctx, FEA_EINVAL, "chunk scatter not built for this mesh");
+    if (plan->scatter == FEA_SCATTER_CHUNK) {
+        if (plan->chunk_elems < 32 || plan->chunk_elems > 4096 || plan->chunk_elems % 32)
+            return fail(ctx, FEA_EINVAL, "chunk_elems must be a multiple of 32 in [32, 4096]");
+        if (plan->chunk_acc != 0 && plan->chunk_acc != 1) return fail(ctx, FEA_EINVAL, "chunk_acc must be 0 or 1");
+        if ((st = ensure_chunks(ctx, *m, plan->chunk_elems))) return st;
+        for (auto &b : m->buckets)
+            if (b->count && chunk_smem_bytes(b->dev()) > 200 * 1024)
+                return fail(ctx, FEA_EINVAL, "chunk of %d elements needs more than 220 KB of shared memory",
+                            plan->chunk_elems);
+    }
     m->plan = *plan;
     if (m->graph.exec) {
         cudaGraphExecDestroy(m->graph.exec);
@@ -779,10 +940,21 @@ fea_status fea_autotune(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure c
     CK(cudaEventCreate(&e1));
     fea_plan best = m->plan;
     float best_ms = 1e30f;
-    const int cand[3] = {64, 128, 256};
-    for (int c = 0; c < 3; ++c) {
-        m->plan.scatter = FEA_SCATTER_ATOMIC;
-        m->plan.threads_per_block = cand[c];
+    std::vector<fea_plan> cands;
+    for (int t : {128, 256}) cands.push_back(fea_plan{FEA_SCATTER_ATOMIC, t, m->plan.chunk_elems, 0});
+    if (prec == FEA_MIXED)
+        for (int C : {256, 512, 1024})
+            for (int t : {128, 256, 512})
+                if (t <= C) cands.push_back(fea_plan{FEA_SCATTER_CHUNK, t, C, m->plan.chunk_acc});
+    for (const fea_plan &cand : cands) {
+        if (cand.scatter == FEA_SCATTER_CHUNK) {
+            if ((st = ensure_chunks(ctx, *m, cand.chunk_elems))) return st;
+            bool fits = true;
+            for (auto &b : m->buckets)
+                if (b->count && chunk_smem_bytes(b->dev()) > 200 * 1024) fits = false;
+            if (!fits) continue;
+        }
+        m->plan = cand;
         for (int rep = 0; rep < 2; ++rep)
             if ((st = assemble_into(ctx, *m, prec, closure, FEA_TERM_ALL, FEA_SCATTER_AUTO, m->rhs.p, nullptr, 0)))
                 return st;
@@ -796,9 +968,10 @@ fea_status fea_autotune(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure c
         CK(cudaEventElapsedTime(&ms, e0, e1));
         if (ms < best_ms) {
             best_ms = ms;
-            best = m->plan;
+            best = cand;
         }
     }
+    if (best.scatter == FEA_SCATTER_CHUNK && (st = ensure_chunks(ctx, *m, best.chunk_elems))) return st;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     m->plan = best;

@@ -24,6 +24,7 @@ enum : unsigned {
 
 // Reference-element tables at the Gauss points of each type's rule.
 struct RefTables {
+    double xi[4][kMaxNg][3];   // Gauss points in reference coordinates
     double N[4][kMaxNg][kMaxNen];
     double dN[4][kMaxNg][kMaxNen][3];
     double w[4][kMaxNg];
@@ -37,13 +38,24 @@ struct BucketDev {
     int64_t count;
     const int32_t *conn;    // [nen][count] caller node ids
     const int32_t *orig;    // [count] caller element index within its type
-    // chunk tables (CTA-local scatter)
-    int32_t chunk_elems;
+    // chunk tables (CTA-local scatter): chunk k holds elements
+    // [k C, min((k+1) C, count)) and the L_k distinct nodes they touch
+    int32_t chunk_elems;            // C
     int64_t n_chunks;
-    const uint16_t *lconn;      // [nen][count] chunk-local node index
-    const int64_t *chunk_node_off;  // [n_chunks + 1] offsets into chunk_nodes
-    const int32_t *chunk_nodes;     // caller node id, bit 31 set = shared with other chunks
-    int32_t max_chunk_nodes;
+    const uint16_t *lconn;          // [count][2][np]: np chunk-local node indices of the
+                                    // element, then the np positions of its incidences in
+                                    // the chunk's node-sorted incidence list (np = 4 for
+                                    // TET04, 8 otherwise; padded for one vector load)
+    const int64_t *chunk_node_off;  // [n_chunks + 1] offsets into chunk_rec / inc_range;
+                                    // each chunk's node list is padded to a multiple of 4
+                                    // entries (16-byte aligned for bulk copies)
+    const int32_t *chunk_nodes;     // [n_chunks] true node count L_k (without padding)
+    const float4 *chunk_rec;        // per local node: FP32 coordinates relative to the
+                                    // chunk's first node, and in .w the bits of the caller
+                                    // node id with bit 31 set if other chunks touch it too
+    const uint32_t *inc_range;      // per local node: first incidence | count << 16; local
+                                    // nodes are ordered by decreasing incidence count
+    int32_t max_chunk_nodes;        // max L_k
 };
 
 // Per-mesh nodal data used by the kernels.
@@ -70,6 +82,13 @@ struct AsmArgs {
 cudaError_t upload_ref_tables(const RefTables &t);
 cudaError_t launch_assemble_bucket(const BucketDev &b, const FieldDev &f, const AsmArgs &a, fea_prec prec,
                                    fea_scatter scatter, int threads, cudaStream_t s);
+cudaError_t launch_assemble_chunk(const BucketDev &b, const FieldDev &f, const AsmArgs &a, int threads,
+                                  int compensated, cudaStream_t s);
+size_t chunk_smem_bytes(const BucketDev &b);
+cudaError_t launch_tet_pipe(const BucketDev &b, const FieldDev &f, const AsmArgs &a, int threads, int sms,
+                           cudaStream_t s);
+size_t tet_pipe_smem_bytes(const BucketDev &b);
+constexpr int lconn_pitch(int etype) { return etype == FEA_TET04 ? 4 : 8; }
 cudaError_t launch_lumped_mass(const BucketDev &b, const double *xyz64, int64_t n, double *mass, unsigned *err,
                                unsigned long long *bad, cudaStream_t s);
 cudaError_t launch_fold(const int32_t *slaves, const int32_t *masters, int64_t n_slaves, double *v, int ncomp,

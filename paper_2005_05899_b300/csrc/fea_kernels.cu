@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "fea_internal.h"
 
@@ -147,37 +148,94 @@ __device__ __forceinline__ JR jacobian_at(const JR X[][3], int g, JR J[3][3]) {
     return det3(J);
 }
 
+// Jacobian of a PEN06 at (r, s, zeta) from per-element edge combinations:
+// the r- and s-columns are linear in zeta, the zeta-column linear in (r, s).
+template <typename JR>
+struct PrismGeom {
+    JR Ar[3], Br[3], As[3], Bs[3], C0[3], Dr[3], Ds[3];
+};
+
+template <typename JR>
+__device__ __forceinline__ void prism_geom(const JR X[][3], PrismGeom<JR> &p) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const JR e1 = X[1][i] - X[0][i], e2 = X[2][i] - X[0][i];
+        const JR f1 = X[4][i] - X[3][i], f2 = X[5][i] - X[3][i];
+        const JR h0 = X[3][i] - X[0][i], h1 = X[4][i] - X[1][i], h2 = X[5][i] - X[2][i];
+        p.Ar[i] = JR(0.5) * (e1 + f1);
+        p.Br[i] = JR(0.5) * (f1 - e1);
+        p.As[i] = JR(0.5) * (e2 + f2);
+        p.Bs[i] = JR(0.5) * (f2 - e2);
+        p.C0[i] = JR(0.5) * h0;
+        p.Dr[i] = JR(0.5) * (h1 - h0);
+        p.Ds[i] = JR(0.5) * (h2 - h0);
+    }
+}
+
+// adjugate (transposed cofactors): J^-1 = adj / det, det = J row 0 . adj column 0
+template <typename JR>
+__device__ __forceinline__ JR adjugate(const JR J[3][3], JR A[3][3]) {
+    A[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    A[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    A[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    A[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+    A[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    A[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+    A[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    A[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+    A[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    return J[0][0] * A[0][0] + J[0][1] * A[1][0] + J[0][2] * A[2][0];
+}
+
+// Residual of one element at the Gauss points of its rule (PYR05, PEN06,
+// HEX08), in one sweep: the filter width Delta = V_e^(1/3) is known only
+// after the last point, and nu_t = Delta^2 q(G) with q(G) = c sqrt(B'/G:G),
+// so the subgrid term is accumulated without the Delta^2 factor and added
+// once V_e is complete.  J, its adjugate and determinant are in JR (FP64
+// for flagged elements), the rest in R.
 template <int ET, typename R, bool J64>
 __device__ void element_residual(const Gathered<R, J64> &el, const FieldDev &f, const AsmArgs &args, R r[][3],
                                  float *nut_out, bool &bad) {
     using JR = typename std::conditional<J64, double, R>::type;
     constexpr int nen = kNen[ET], ng = kNg[ET];
     const uint32_t mask = args.mask;
-    // element volume first (filter width)
-    JR V = JR(0);
+    const bool want_q = args.closure == FEA_CLOSURE_VREMAN && ((mask & FEA_TERM_SGS) || nut_out);
+    const R nu = (mask & FEA_TERM_VISC) ? R(f.nu) : R(0);
+    const R cv = R(f.c_vreman);
+    R rs[kMaxNen][3];
 #pragma unroll
+    for (int a = 0; a < nen; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) r[a][i] = rs[a][i] = R(0);
+    PrismGeom<JR> pg;
+    if constexpr (ET == FEA_PEN06) prism_geom<JR>(el.X, pg);
+    JR V = JR(0);
+#pragma unroll 1
     for (int g = 0; g < ng; ++g) {
         JR J[3][3];
-        const JR d = jacobian_at<ET, R, JR>(el.X, g, J);
-        if (!(d > JR(0))) bad = true;
-        V += JR(c_ref.w[ET][g]) * d;
-    }
-    const R delta = cbrt_r(R(V));
-    const R delta2 = delta * delta;
-    const R nu = R(f.nu), cv = R(f.c_vreman);
+        if constexpr (ET == FEA_PEN06) {
+            const JR pr = JR(c_ref.xi[ET][g][0]), ps = JR(c_ref.xi[ET][g][1]), pz = JR(c_ref.xi[ET][g][2]);
 #pragma unroll
-    for (int a = 0; a < nen; ++a) r[a][0] = r[a][1] = r[a][2] = R(0);
-#pragma unroll
-    for (int g = 0; g < ng; ++g) {
-        JR J[3][3], Jd[3][3];
-        jacobian_at<ET, R, JR>(el.X, g, J);
-        const JR detj = inv3(J, Jd);
+            for (int i = 0; i < 3; ++i) {
+                J[i][0] = pg.Ar[i] + pz * pg.Br[i];
+                J[i][1] = pg.As[i] + pz * pg.Bs[i];
+                J[i][2] = pg.C0[i] + pr * pg.Dr[i] + ps * pg.Ds[i];
+            }
+        } else {
+            jacobian_at<ET, R, JR>(el.X, g, J);
+        }
+        JR A[3][3];
+        const JR detj = adjugate(J, A);
+        if (!(detj > JR(0))) bad = true;
+        const JR wdet = JR(c_ref.w[ET][g]) * detj;
+        V += wdet;
+        const R rdet = R(1) / R(detj);
         R Ji[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int j = 0; j < 3; ++j) Ji[i][j] = R(Jd[i][j]);
-        const R W = R(JR(c_ref.w[ET][g]) * detj);
+            for (int j = 0; j < 3; ++j) Ji[i][j] = R(A[i][j]) * rdet;
+        const R W = R(wdet);
         // reference-coordinate gradients and the Gauss-point velocity
         R Gx[3][3] = {}, px[3] = {}, ug[3] = {};
 #pragma unroll
@@ -201,9 +259,9 @@ __device__ void element_residual(const Gathered<R, J64> &el, const FieldDev &f, 
 #pragma unroll
             for (int i = 0; i < 3; ++i) G[i][j] = Gx[i][0] * Ji[0][j] + Gx[i][1] * Ji[1][j] + Gx[i][2] * Ji[2][j];
         }
-        R nut = R(0);
-        if (args.closure == FEA_CLOSURE_VREMAN && ((mask & FEA_TERM_SGS) || nut_out)) nut = vreman(G, delta2, cv);
-        if (nut_out) nut_out[g] = float(nut);
+        const R q = want_q ? vreman(G, R(1), cv) : R(0);
+        if (nut_out) nut_out[g] = float(q);
+        const R qs = (mask & FEA_TERM_SGS) ? q : R(0);
         const R trG = G[0][0] + G[1][1] + G[2][2];
         R f0[3];
 #pragma unroll
@@ -212,29 +270,34 @@ __device__ void element_residual(const Gathered<R, J64> &el, const FieldDev &f, 
             if (mask & FEA_TERM_CONV) c = G[i][0] * ug[0] + G[i][1] * ug[1] + G[i][2] * ug[2] + trG * ug[i];
             f0[i] = W * (c + ((mask & FEA_TERM_PRES) ? gp[i] : R(0)));
         }
-        R visc = R(0);
-        if (mask & FEA_TERM_VISC) visc += nu;
-        if (mask & FEA_TERM_SGS) visc += nut;
-        // S_ik = 2 visc W sum_j eps_ij Ji_kj
-        R eps[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) eps[i][j] = R(0.5) * (G[i][j] + G[j][i]);
-        const R s2 = R(2) * visc * W;
+        // S_ik = 2 W sum_j eps_ij Ji_kj; viscous part nu S, subgrid part q S
         R S[3][3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 3; ++i) {
+            R e0 = R(0.5) * (G[i][0] + G[0][i]), e1 = R(0.5) * (G[i][1] + G[1][i]), e2 = R(0.5) * (G[i][2] + G[2][i]);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) S[i][k] = s2 * (eps[i][0] * Ji[k][0] + eps[i][1] * Ji[k][1] + eps[i][2] * Ji[k][2]);
+            for (int k = 0; k < 3; ++k) S[i][k] = R(2) * W * (e0 * Ji[k][0] + e1 * Ji[k][1] + e2 * Ji[k][2]);
+        }
 #pragma unroll
         for (int a = 0; a < nen; ++a) {
             const R Na = R(c_ref.N[ET][g][a]);
             const R d0 = R(c_ref.dN[ET][g][a][0]), d1 = R(c_ref.dN[ET][g][a][1]), d2 = R(c_ref.dN[ET][g][a][2]);
 #pragma unroll
-            for (int i = 0; i < 3; ++i) r[a][i] -= Na * f0[i] + S[i][0] * d0 + S[i][1] * d1 + S[i][2] * d2;
+            for (int i = 0; i < 3; ++i) {
+                const R t = S[i][0] * d0 + S[i][1] * d1 + S[i][2] * d2;
+                r[a][i] -= Na * f0[i] + nu * t;
+                rs[a][i] -= qs * t;
+            }
         }
     }
+    const R delta = cbrt_r(R(V));
+    const R d2 = delta * delta;
+#pragma unroll
+    for (int a = 0; a < nen; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) r[a][i] += d2 * rs[a][i];
+    if (nut_out)
+        for (int g = 0; g < ng; ++g) nut_out[g] = float(R(nut_out[g]) * d2);
 }
 
 // TET04: affine map, constant gradients; the 4-point rule is exact for the
@@ -368,6 +431,179 @@ cudaError_t launch_assemble_bucket(const BucketDev &b, const FieldDev &f, const 
         case FEA_PYR05: return launch_atomic_t<FEA_PYR05>(b, f, a, prec, threads, s);
         case FEA_PEN06: return launch_atomic_t<FEA_PEN06>(b, f, a, prec, threads, s);
         case FEA_HEX08: return launch_atomic_t<FEA_HEX08>(b, f, a, prec, threads, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// CHUNK scatter: one CTA assembles one chunk of C Morton-consecutive elements.
+//   A. the chunk's L distinct nodes are staged in shared memory: FP32
+//      coordinates relative to the chunk's first node (precomputed from FP64
+//      at upload, so edge vectors keep full FP32 precision) and (u, v, w, p);
+//   B. thread per element: gather from shared memory, element residual,
+//      written to the incidences' positions in the chunk's node-sorted
+//      incidence list (no atomics);
+//   C. thread per local node: sums its contiguous range (FP32, or
+//      compensated two-float sums), converts to FP64 and writes once to the
+//      global RHS:
+//      a plain store when no other chunk touches the node, else one FP64
+//      atomic add per component.
+
+__device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
+    const float t = s + x;
+    const float z = t - s;
+    c += (s - (t - z)) + (x - z);
+    s = t;
+}
+
+template <int ET, bool J64, bool COMP>
+__global__ void __launch_bounds__(256) k_assemble_chunk(BucketDev b, FieldDev f, AsmArgs args) {
+    constexpr int nen = kNen[ET], ng = kNg[ET];
+    extern __shared__ float4 smem4[];
+    const int C = b.chunk_elems;
+    const int64_t k = blockIdx.x;
+    const int64_t e0 = k * (int64_t)C;
+    const int ne = (int)min((int64_t)C, b.count - e0);
+    const int64_t nb = b.chunk_node_off[k];
+    const int L = b.chunk_nodes[k];
+    float4 *sX = smem4;
+    float4 *sU = smem4 + b.max_chunk_nodes;
+    float4 *sR = sU + b.max_chunk_nodes;  // [nen C] residuals in node-sorted incidence order
+    constexpr int np = lconn_pitch(ET);
+    for (int j = threadIdx.x; j < L; j += blockDim.x) {
+        const float4 rec = __ldg(&b.chunk_rec[nb + j]);
+        const int id = __float_as_int(rec.w) & 0x7fffffff;
+        sX[j] = rec;
+        sU[j] = __ldg(&f.up32[id]);
+    }
+    __syncthreads();
+    bool bad = false;
+    float chk = 0.0f;
+    for (int el = threadIdx.x; el < ne; el += blockDim.x) {
+        const int64_t e = e0 + el;
+        Gathered<float, J64> g;
+        int loc[nen];
+        uint16_t lbuf[2 * np];
+        if constexpr (np == 4) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(b.lconn) + e);
+            memcpy(lbuf, &v, 16);
+        } else {
+            const uint4 v0 = __ldg(reinterpret_cast<const uint4 *>(b.lconn) + 2 * e);
+            const uint4 v1 = __ldg(reinterpret_cast<const uint4 *>(b.lconn) + 2 * e + 1);
+            memcpy(lbuf, &v0, 16);
+            memcpy(lbuf + 8, &v1, 16);
+        }
+#pragma unroll
+        for (int a = 0; a < nen; ++a) {
+            loc[a] = lbuf[a];
+            const float4 x = sX[loc[a]];
+            const float4 u = sU[loc[a]];
+            g.U[a][0] = u.x;
+            g.U[a][1] = u.y;
+            g.U[a][2] = u.z;
+            g.P[a] = u.w;
+            if constexpr (J64) {
+                const int64_t id = __float_as_int(x.w) & 0x7fffffff;
+                g.X[a][0] = __ldg(&f.xyz64[id]);
+                g.X[a][1] = __ldg(&f.xyz64[f.n + id]);
+                g.X[a][2] = __ldg(&f.xyz64[2 * f.n + id]);
+            } else {
+                g.X[a][0] = x.x;
+                g.X[a][1] = x.y;
+                g.X[a][2] = x.z;
+            }
+        }
+        float r[kMaxNen][3];
+        float *nut = args.nut ? args.nut + (int64_t)__ldg(&b.orig[e]) * ng : nullptr;
+        if constexpr (ET == FEA_TET04)
+            tet_residual<float, J64>(g, f, args, r, nut, bad);
+        else
+            element_residual<ET, float, J64>(g, f, args, r, nut, bad);
+#pragma unroll
+        for (int a = 0; a < nen; ++a) {
+            sR[lbuf[np + a]] = make_float4(r[a][0], r[a][1], r[a][2], 0.0f);
+            chk += r[a][0] + r[a][1] + r[a][2];
+        }
+    }
+    if (bad) set_err(args.err, ERR_DETJ);
+    if (!isfinite(chk)) set_err(args.err, ERR_NONFINITE);
+    __syncthreads();
+    for (int j = threadIdx.x; j < L; j += blockDim.x) {
+        const uint32_t rg = __ldg(&b.inc_range[nb + j]);
+        const int start = (int)(rg & 0xffffu), cnt = (int)(rg >> 16);
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+        for (int q = 0; q < cnt; ++q) {
+            const float4 v = sR[start + q];
+            if constexpr (COMP) {
+                two_sum_acc(s0, c0, v.x);
+                two_sum_acc(s1, c1, v.y);
+                two_sum_acc(s2, c2, v.z);
+            } else {
+                s0 += v.x;
+                s1 += v.y;
+                s2 += v.z;
+            }
+        }
+        const int bits = __float_as_int(sX[j].w);
+        const int64_t id = bits & 0x7fffffff;
+        double v0 = double(s0), v1 = double(s1), v2 = double(s2);
+        if constexpr (COMP) {
+            v0 += double(c0);
+            v1 += double(c1);
+            v2 += double(c2);
+        }
+        double *r0 = args.rhs + id, *r1 = args.rhs + f.n + id, *r2 = args.rhs + 2 * f.n + id;
+        if (bits < 0) {
+            atomicAdd(r0, v0);
+            atomicAdd(r1, v1);
+            atomicAdd(r2, v2);
+        } else {
+            *r0 = v0;
+            *r1 = v1;
+            *r2 = v2;
+        }
+    }
+}
+
+size_t chunk_smem_bytes(const BucketDev &b) {
+    return sizeof(float4) * (2 * (size_t)b.max_chunk_nodes + (size_t)kNen[b.etype] * b.chunk_elems);
+}
+
+template <int ET, bool J64, bool COMP>
+static cudaError_t launch_chunk_v(const BucketDev &b, const FieldDev &f, const AsmArgs &a, int threads,
+                                  cudaStream_t s) {
+    const size_t smem = chunk_smem_bytes(b);
+    auto kern = k_assemble_chunk<ET, J64, COMP>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<(unsigned)b.n_chunks, threads, smem, s>>>(b, f, a);
+    return cudaGetLastError();
+}
+
+template <int ET>
+static cudaError_t launch_chunk_t(const BucketDev &b, const FieldDev &f, const AsmArgs &a, int threads, int comp,
+                                  cudaStream_t s) {
+    if (b.fp64j)
+        return comp ? launch_chunk_v<ET, true, true>(b, f, a, threads, s)
+                    : launch_chunk_v<ET, true, false>(b, f, a, threads, s);
+    return comp ? launch_chunk_v<ET, false, true>(b, f, a, threads, s)
+                : launch_chunk_v<ET, false, false>(b, f, a, threads, s);
+}
+
+cudaError_t launch_assemble_chunk(const BucketDev &b, const FieldDev &f, const AsmArgs &a, int threads,
+                                  int compensated, cudaStream_t s) {
+    if (b.count == 0) return cudaSuccess;
+    if (!b.lconn || b.n_chunks <= 0) return cudaErrorInvalidValue;
+    if (b.etype == FEA_TET04 && !b.fp64j && !compensated) return launch_tet_pipe(b, f, a, threads, 0, s);
+    if (threads > 256) threads = 256;
+    switch (b.etype) {
+        case FEA_TET04:
+            return launch_chunk_t<FEA_TET04>(b, f, a, threads, compensated, s);
+        case FEA_PYR05: return launch_chunk_t<FEA_PYR05>(b, f, a, threads, compensated, s);
+        case FEA_PEN06: return launch_chunk_t<FEA_PEN06>(b, f, a, threads, compensated, s);
+        case FEA_HEX08: return launch_chunk_t<FEA_HEX08>(b, f, a, threads, compensated, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -50,11 +50,11 @@ class MeshDesc(ctypes.Structure):
 
 class Plan(ctypes.Structure):
     _fields_ = [("scatter", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
-                ("chunk_elems", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("chunk_elems", ctypes.c_int32), ("chunk_acc", ctypes.c_int32)]
 
     def as_dict(self):
         return {"scatter": self.scatter, "threads_per_block": self.threads_per_block,
-                "chunk_elems": self.chunk_elems}
+                "chunk_elems": self.chunk_elems, "chunk_acc": self.chunk_acc}
 
 
 _lib = None
@@ -279,8 +279,8 @@ class DeviceMesh:
         self.ctx.check(self._L().fea_get_plan(self.ctx.handle, self.id, ctypes.byref(p)))
         return p
 
-    def set_plan(self, scatter="atomic", threads_per_block=256, chunk_elems=256):
-        p = Plan(SCATTER[scatter], threads_per_block, chunk_elems, 0)
+    def set_plan(self, scatter="chunk", threads_per_block=256, chunk_elems=512, chunk_acc=0):
+        p = Plan(SCATTER[scatter], threads_per_block, chunk_elems, chunk_acc)
         self.ctx.check(self._L().fea_set_plan(self.ctx.handle, self.id, ctypes.byref(p)))
 
     def autotune(self, prec="mixed", closure="vreman", cache_path: Optional[str] = None):

@@ -169,3 +169,86 @@ def test_upload_errors(ctx):
         dm.assemble(out, mask=99)
     assert ei.value.status == fea.EINVAL
     ctx.sync_status()
+
+
+# ---------------------------------------------------------------------------
+# scatter strategies and launch plans
+
+@pytest.mark.parametrize("chunk_elems,threads,acc", [(512, 256, 0), (256, 128, 1), (96, 64, 1), (1024, 256, 0)])
+def test_chunk_scatter_matches_oracle(ctx, mixed_small, chunk_elems, threads, acc):
+    m, f = mixed_small
+    dm = ctx.upload_mesh(m)
+    dm.set_plan("chunk", threads, chunk_elems, acc)
+    r, _ = gpu_rhs(ctx, m, f, "mixed", scatter="chunk", dm=dm)
+    ref = oracle_rhs(m, f)
+    l2, mx = errors(r, ref)
+    print(f"chunk C={chunk_elems} T={threads} acc={acc}: rel-L2 {l2:.3e} max {mx:.3e}")
+    assert l2 < MIXED_L2 and mx < MIXED_MAX
+
+
+def test_atomic_and_chunk_agree_and_nut_identical(ctx, mixed_small):
+    m, f = mixed_small
+    dm = ctx.upload_mesh(m)
+    ra, nut_a, _ = gpu_rhs(ctx, m, f, "mixed", scatter="atomic", want_nut=True, dm=dm)
+    rc, nut_c, _ = gpu_rhs(ctx, m, f, "mixed", scatter="chunk", want_nut=True, dm=dm)
+    ref = oracle_rhs(m, f)
+    assert errors(ra, ref)[0] < MIXED_L2 and errors(rc, ref)[0] < MIXED_L2
+    # nu_t per Gauss point depends on coordinates only through J: both paths agree to FP32 rounding
+    assert np.allclose(nut_a, nut_c, rtol=1e-4, atol=1e-12)
+
+
+def test_chunk_scatter_is_deterministic_for_exclusive_nodes(ctx, mixed_small):
+    m, f = mixed_small
+    dm = ctx.upload_mesh(m)
+    dm.set_plan("chunk", 256, 1024, 1)
+    a, _ = gpu_rhs(ctx, m, f, "mixed", scatter="chunk", dm=dm)
+    b, _ = gpu_rhs(ctx, m, f, "mixed", scatter="chunk", dm=dm)
+    assert np.abs(a - b).max() <= 1e-15 * np.abs(a).max()
+
+
+def test_plan_validation_and_autotune(ctx, mixed_small):
+    m, f = mixed_small
+    dm = ctx.upload_mesh(m)
+    p = dm.get_plan()
+    assert p.scatter in (1, 2)
+    with pytest.raises(fea.FeaError):
+        dm.set_plan("chunk", 100, 512, 0)
+    with pytest.raises(fea.FeaError):
+        dm.set_plan("chunk", 256, 50, 0)
+    dm.upload_field(f.u, f.p, f.nu, f.c_vreman)
+    best = dm.autotune(prec="mixed", closure="vreman")
+    assert best.scatter in (1, 2) and best.threads_per_block in (128, 256)
+    r, _ = gpu_rhs(ctx, m, f, "mixed", dm=dm)
+    assert errors(r, oracle_rhs(m, f))[0] < MIXED_L2
+
+
+def sampled_parity(ctx, mesh, field, n_sample=3000, seed=0, prec="mixed", plan=None):
+    """RHS at sampled nodes: the oracle assembles only the elements incident to
+    them (their RHS is then complete) on a compacted sub-mesh."""
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(mesh.n_nodes, size=n_sample, replace=False))
+    mark = np.zeros(mesh.n_nodes, bool)
+    mark[pick] = True
+    sub_conn = {t: c[mark[c].any(axis=1)] for t, c in mesh.conn.items()}
+    used = np.unique(np.concatenate([c.ravel() for c in sub_conn.values()]))
+    remap = np.full(mesh.n_nodes, -1, np.int64)
+    remap[used] = np.arange(used.size)
+    om = O.OracleMesh(mesh.xyz[used], {t: remap[c].astype(np.int32) for t, c in sub_conn.items()})
+    ref = O.assemble_rhs(om, field.u[used], field.p[used], field.nu, field.c_vreman, "vreman")[remap[pick]]
+    dm = ctx.upload_mesh(mesh)
+    if plan:
+        dm.set_plan(*plan)
+    dm.upload_field(field.u, field.p, field.nu, field.c_vreman)
+    out = torch.empty((3, dm.n_nodes), dtype=torch.float64, device="cuda")
+    dm.assemble(out, prec=prec, closure="vreman")
+    ctx.sync_status()
+    got = out[:, torch.from_numpy(pick).cuda()].cpu().numpy().T
+    return errors(got, ref)
+
+
+def test_airplane_full_size_sampled_parity(ctx):
+    m = mg.airplane_mesh(170, seed=4)
+    f = mg.inflow_field(m, seed=5)
+    l2, mx = sampled_parity(ctx, m, f, plan=("chunk", 256, 512, 0))
+    print(f"airplane 170^3 sampled mixed: rel-L2 {l2:.3e} max {mx:.3e}")
+    assert l2 < MIXED_L2 and mx < MIXED_MAX
