@@ -167,7 +167,9 @@ def cpu_baseline(mesh, field, target_s: float = 12.0, steps: int = 1):
     t = time.time()
     O.assemble_rhs_omp(om, u, p, field.nu, field.c_vreman, "vreman")
     rate = 200_000 / max(time.time() - t, 1e-6)
-    ne = int(min(conn.shape[0], max(200_000, rate * target_s / max(steps, 1))))
+    want = rate * target_s
+    ne = int(min(conn.shape[0], max(200_000, want / max(steps, 1))))
+    steps = max(steps, int(round(want / ne)))   # whole mesh too small: repeat passes
     om, u, p = sample(ne)
     t = time.time()
     for _ in range(steps):
@@ -320,7 +322,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-axis", type=int, default=170, help="grid nodes per axis of the airplane-like mesh")

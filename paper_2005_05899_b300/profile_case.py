@@ -1,0 +1,60 @@
+"""Run one assembly case for profiling (e.g. under ncu).
+
+    python -m paper_2005_05899_b300.profile_case --mesh airplane --n 100 \
+        --plan chunk --threads 256 --chunk 512 --reps 3
+
+Builds the seeded mesh and field, uploads them, sets the launch plan and runs
+`--reps` mixed-precision Vreman assemblies (or RK3 graph steps with --rk3),
+then checks the device status word.
+"""
+from __future__ import annotations
+
+import argparse
+import sys
+import time
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--mesh", choices=["airplane", "channel", "tgv"], default="airplane")
+    ap.add_argument("--n", type=int, default=100, help="grid nodes per axis (airplane) or cells (tgv)")
+    ap.add_argument("--plan", choices=["chunk", "atomic"], default="chunk")
+    ap.add_argument("--threads", type=int, default=256)
+    ap.add_argument("--chunk", type=int, default=512)
+    ap.add_argument("--acc", type=int, default=0)
+    ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--rk3", action="store_true")
+    a = ap.parse_args(argv)
+    import torch
+
+    from . import fea
+    from . import meshgen as mg
+    if a.mesh == "airplane":
+        m = mg.airplane_mesh(a.n, seed=4)
+        f = mg.inflow_field(m, seed=5)
+    elif a.mesh == "channel":
+        m = mg.channel_mesh()
+        f = mg.channel_field(m)
+    else:
+        m = mg.tgv_mesh(a.n)
+        f = mg.tgv_field(m)
+    ctx = fea.Context(0)
+    dm = ctx.upload_mesh(m)
+    dm.set_plan(a.plan, a.threads, a.chunk, a.acc)
+    dm.upload_field(f.u, f.p, f.nu, f.c_vreman)
+    out = torch.empty((3, dm.n_nodes), dtype=torch.float64, device="cuda")
+    t = time.time()
+    for _ in range(a.reps):
+        if a.rk3:
+            dm.rk_step_graph(1e-4, prec=a.prec)
+        else:
+            dm.assemble(out, prec=a.prec)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    print(f"ok {m.counts()} {a.reps} reps {time.time() - t:.3f}s", flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
