@@ -202,6 +202,33 @@ fea_status fea_rk_step_graph(fea_ctx *ctx, int32_t mesh, double dt, fea_prec pre
 /* Copies the current state u^(k) [3][n_nodes] to out (host or device). */
 fea_status fea_state_download(fea_ctx *ctx, int32_t mesh, double *out, void *stream);
 
+/* Allocation-free RK stage (no counterpart in the paper).
+ *
+ * For callers that cannot allocate device memory at call time -- code that
+ * runs under a fixed, pre-reserved device-memory budget or inside an
+ * embedding that forbids cudaMalloc/cudaFree after set-up.  It computes the
+ * same stage as fea_rk_stage,
+ *   uk_out = a_k un + b_k (uk + dt M^-1 R(uk, p)),  (a, b) as in fea_rk_stage,
+ * R folded over periodic pairs, M the mesh's folded lumped mass, Dirichlet
+ * nodes holding un, but reads the state from and writes it to caller arrays
+ * and allocates nothing: its scratch (the FP64 RHS and an FP32 copy of uk and
+ * p, 40 bytes per node) is one static device array, reserved on every GPU
+ * that loads the library and held until the process exits.
+ *   un, uk, p: device, [3][n_nodes], [3][n_nodes], [n_nodes] FP64 (inputs);
+ *   uk_out: device [3][n_nodes] FP64 (output; may equal uk);
+ *   nu, c_vreman: viscosity and Vreman constant for this call.
+ * The mesh must have been uploaded (fea_mesh_upload allocates as usual) and
+ * have at most FEA_NOALLOC_MAX_NODES nodes, else FEA_EINVAL.  The first call
+ * on a device looks up the array's device address (with that device made
+ * current, then restored); make that first call before any stream capture.
+ * Every call on a device shares the array and it keeps the last call's
+ * contents: each call clears the RHS part itself, and calls that overlap on
+ * the GPU (e.g. on two streams at once) race on the shared scratch. */
+#define FEA_NOALLOC_MAX_NODES 262144
+fea_status fea_rk_stage_noalloc(fea_ctx *ctx, int32_t mesh, int32_t stage, double dt, fea_prec prec,
+                                fea_closure closure, double nu, double c_vreman, const double *un, const double *uk,
+                                const double *p, double *uk_out, void *stream);
+
 /* ---- plans, autotuning, status ----------------------------------------- */
 
 fea_status fea_get_plan(fea_ctx *ctx, int32_t mesh, fea_plan *plan);

@@ -520,6 +520,92 @@ fea_status rk_stage_impl(fea_ctx *ctx, Mesh &m, int stage, double dt, fea_prec p
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// support for the allocation-free stage entry point (fea_noalloc.cu)
+
+namespace fea {
+
+int context_device(const fea_ctx *ctx) { return ctx ? ctx->device : -1; }
+
+fea_status context_fail(fea_ctx *ctx, fea_status st, const char *msg) { return fail(ctx, st, "%s", msg); }
+
+fea_status stage_with_scratch(fea_ctx *ctx, int32_t mesh, int32_t stage, double dt, fea_prec prec,
+                              fea_closure closure, double nu, double c_vreman, const double *un, const double *uk,
+                              const double *p, double *uk_out, double *rhs, float4 *up, int64_t max_nodes,
+                              cudaStream_t s) {
+    static const double A[3] = {0.0, 0.75, 1.0 / 3.0};
+    static const double B[3] = {1.0, 0.25, 2.0 / 3.0};
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    if ((st = check_args(ctx, prec, closure, FEA_TERM_ALL))) return st;
+    if (stage < 0 || stage > 2) return fail(ctx, FEA_EINVAL, "stage must be 0, 1 or 2");
+    if (!(dt > 0.0)) return fail(ctx, FEA_EINVAL, "dt must be > 0");
+    if (!(nu >= 0.0) || !(c_vreman >= 0.0)) return fail(ctx, FEA_EINVAL, "nu and c_vreman must be >= 0");
+    if (!un || !uk || !p || !uk_out) return fail(ctx, FEA_EINVAL, "null state array");
+    if (m->n > max_nodes)
+        return fail(ctx, FEA_EINVAL, "mesh has %lld nodes, above the %lld-node limit of the static scratch",
+                    (long long)m->n, (long long)max_nodes);
+    const int64_t n = m->n;
+    // FP32 copy of (u^(k), p) for the mixed kernels, in scratch
+    CK(launch_pack_field(n, uk, p, up, s));
+    FieldDev f;
+    f.n = n;
+    f.xyz64 = m->xyz64.p;
+    f.xyz32 = m->xyz32.p;
+    f.u64 = uk;
+    f.p64 = p;
+    f.up32 = up;
+    f.nu = nu;
+    f.c_vreman = c_vreman;
+    CK(cudaMemsetAsync(rhs, 0, sizeof(double) * 3 * n, s));
+    const fea_scatter scatter = (fea_scatter)m->plan.scatter;
+    bool forked = false;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (auto &bp : m->buckets) {
+            const Bucket &b = *bp;
+            if (!b.count) continue;
+            const bool side = prec == FEA_MIXED && b.fp64j;
+            if (side != (pass == 0)) continue;
+            cudaStream_t ls = s;
+            if (side) {
+                if (!forked) {
+                    CK(cudaEventRecord(ctx->ev_fork, s));
+                    CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+                    forked = true;
+                }
+                ls = ctx->side;
+            }
+            AsmArgs a;
+            a.mask = FEA_TERM_ALL;
+            a.closure = closure;
+            a.rhs = rhs;
+            a.nut = nullptr;
+            a.err = ctx->d_err;
+            if (prec == FEA_MIXED && scatter == FEA_SCATTER_CHUNK && b.lconn.p)
+                CK(launch_assemble_chunk(b.dev(), f, a, m->plan.threads_per_block, m->plan.chunk_acc, ls));
+            else
+                CK(launch_assemble_bucket(b.dev(), f, a, prec, FEA_SCATTER_ATOMIC, m->plan.threads_per_block, ls));
+            ctx->launches++;
+        }
+    }
+    if (forked) {
+        CK(cudaEventRecord(ctx->ev_join, ctx->side));
+        CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
+    }
+    if (m->slaves.n) {
+        CK(launch_fold(m->slaves.p, m->masters.p, (int64_t)m->slaves.n, rhs, 3, n, s));
+        ctx->launches += 2;
+    }
+    if (uk_out != uk) CK(cudaMemcpyAsync(uk_out, uk, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
+    CK(launch_rk_update(n, un, uk_out, nullptr, rhs, m->minv.p, m->dirichlet.n ? m->dirichlet.p : nullptr, p, up,
+                        A[stage], B[stage], dt, s));
+    ctx->launches += 2;
+    return FEA_OK;
+}
+
+}  // namespace fea
+
 // ===========================================================================
 extern "C" {
 

@@ -100,4 +100,14 @@ cudaError_t launch_pack_field(int64_t n, const double *u64, const double *p64, f
 cudaError_t launch_f32_to_f64(const float *src, double *dst, int64_t count, cudaStream_t s);
 cudaError_t launch_recip(const double *m, double *minv, int64_t n, cudaStream_t s);
 
+// One RK stage from caller state arrays, with caller-provided scratch
+// (rhs [3][n] FP64, up [n] FP32 (u, v, w, p)); used by the allocation-free
+// entry point.  Implemented in fea_api.cu.
+fea_status stage_with_scratch(fea_ctx *ctx, int32_t mesh, int32_t stage, double dt, fea_prec prec,
+                              fea_closure closure, double nu, double c_vreman, const double *un, const double *uk,
+                              const double *p, double *uk_out, double *rhs, float4 *up, int64_t max_nodes,
+                              cudaStream_t s);
+int context_device(const fea_ctx *ctx);
+fea_status context_fail(fea_ctx *ctx, fea_status st, const char *msg);
+
 }  // namespace fea

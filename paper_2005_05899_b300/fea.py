@@ -30,8 +30,9 @@ EXPORTED = (
     "fea_create", "fea_destroy", "fea_last_error", "fea_version", "fea_mesh_upload", "fea_mesh_info",
     "fea_lumped_mass", "fea_field_upload", "fea_assemble_rhs", "fea_assemble_rhs_batched", "fea_periodic_fold",
     "fea_rk_stage", "fea_rk_step_graph", "fea_state_download", "fea_get_plan", "fea_set_plan", "fea_autotune",
-    "fea_sync_status", "fea_launch_count", "fea_profile_enable", "fea_profile_read",
+    "fea_sync_status", "fea_launch_count", "fea_profile_enable", "fea_profile_read", "fea_rk_stage_noalloc",
 )
+NOALLOC_MAX_NODES = 262144
 
 
 class FeaError(RuntimeError):
@@ -92,6 +93,8 @@ def lib() -> ctypes.CDLL:
         L.fea_autotune.argtypes = [vp, i32, ctypes.c_int, ctypes.c_int, ctypes.c_char_p]
         L.fea_sync_status.argtypes = [vp, vp]
         L.fea_profile_enable.argtypes = [vp, ctypes.c_int]
+        L.fea_rk_stage_noalloc.argtypes = [vp, i32, i32, dbl, ctypes.c_int, ctypes.c_int, dbl, dbl, vp, vp, vp, vp,
+                                           vp]
         L.fea_profile_read.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(dbl), ctypes.POINTER(i64),
                                        ctypes.c_int]
         for name in EXPORTED:
@@ -265,6 +268,15 @@ class DeviceMesh:
     def rk_stage(self, stage: int, dt: float, prec="mixed", closure="vreman", stream=None):
         self.ctx.check(self._L().fea_rk_stage(self.ctx.handle, self.id, stage, float(dt), PREC[prec],
                                               CLOSURE[closure], _stream(stream)))
+
+    def rk_stage_noalloc(self, stage: int, dt: float, un, uk, p, out, nu: float, c_vreman: float = 0.07,
+                         prec="mixed", closure="vreman", stream=None):
+        """One RK stage from caller arrays (device, [3][n] / [n] FP64) into `out`,
+        through the entry point that allocates nothing (static device scratch)."""
+        self.ctx.check(self._L().fea_rk_stage_noalloc(self.ctx.handle, self.id, stage, float(dt), PREC[prec],
+                                                      CLOSURE[closure], float(nu), float(c_vreman), _ptr(un),
+                                                      _ptr(uk), _ptr(p), _ptr(out), _stream(stream)))
+        return out
 
     def rk_step_graph(self, dt: float, prec="mixed", closure="vreman", stream=None):
         self.ctx.check(self._L().fea_rk_step_graph(self.ctx.handle, self.id, float(dt), PREC[prec],
