@@ -172,11 +172,15 @@ fea_status fea_field_upload(fea_ctx *ctx, int32_t mesh, const void *u, const voi
 fea_status fea_assemble_rhs(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure closure, uint32_t term_mask,
                             fea_scatter scatter, double *rhs_out, float *nut_out, void *stream);
 
-/* Batched form: one persistent launch over the (mesh, bucket, chunk) work
- * items of n meshes (each with its own field, nu and c_vreman).
- * meshes [n] (host); rhs_out [n] (host array of device pointers, each
- * [3][n_nodes(mesh)]), overwritten.  The same precision/closure/mask apply to
- * all meshes. */
+/* Batched form: one persistent launch over the (mesh, category, chunk) work
+ * items of n meshes (each with its own field, nu and c_vreman); CTAs pull
+ * items from a device work counter, most expensive categories first.  One
+ * zeroing launch for all RHS arrays precedes it.  meshes [n] (host); rhs_out
+ * [n] (host array of device pointers, each [3][n_nodes(mesh)]), overwritten.
+ * The same precision/closure/mask apply to all meshes.  FEA_FP64 (or a mesh
+ * without chunk tables) falls back to per-mesh launches.  The descriptor
+ * tables live in the context: do not overlap batched calls of one context
+ * on different streams. */
 fea_status fea_assemble_rhs_batched(fea_ctx *ctx, const int32_t *meshes, int32_t n, fea_prec prec,
                                     fea_closure closure, uint32_t term_mask, double *const *rhs_out,
                                     void *stream);

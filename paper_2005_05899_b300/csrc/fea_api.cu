@@ -290,6 +290,11 @@ struct fea_ctx {
     std::vector<std::unique_ptr<Mesh>> meshes;
     cudaStream_t capture = nullptr;
     cudaStream_t side = nullptr;      // FP64-Jacobian categories run here, overlapped
+    // batched launch: descriptor tables, work items and the work counter
+    DevBuf<unsigned char> batch_bk, batch_fd, batch_ag, batch_items;
+    DevBuf<double *> batch_rhs;
+    DevBuf<int64_t> batch_len;
+    DevBuf<unsigned long long> batch_counter;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t launches = 0;
 };
@@ -893,17 +898,92 @@ fea_status fea_assemble_rhs_batched(fea_ctx *ctx, const int32_t *meshes, int32_t
     if (!ctx || !meshes || !rhs_out || n <= 0) return fail(ctx, FEA_EINVAL, "bad batch arguments");
     fea_status st = check_args(ctx, prec, closure, mask);
     if (st) return st;
+    bool tables = prec == FEA_MIXED;
     for (int32_t k = 0; k < n; ++k) {
         Mesh *m;
         if ((st = get_mesh(ctx, meshes[k], &m))) return st;
         if (!m->has_field) return fail(ctx, FEA_ESTATE, "no field uploaded for mesh %d", meshes[k]);
         if (!rhs_out[k]) return fail(ctx, FEA_EINVAL, "null rhs_out[%d]", k);
+        for (auto &b : m->buckets)
+            if (b->count && (!b->lconn.p || (b->fp64j && b->etype != FEA_PEN06))) tables = false;
     }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!tables) {  // FP64 path: per-mesh atomic launches
+        for (int32_t k = 0; k < n; ++k) {
+            Mesh *m = ctx->meshes[meshes[k]].get();
+            st = assemble_into(ctx, *m, prec, closure, mask, FEA_SCATTER_ATOMIC, rhs_out[k], nullptr, s);
+            if (st) return st;
+        }
+        return FEA_OK;
+    }
+    // descriptor tables: one entry per (mesh, category); items ordered by
+    // per-element cost (FP64-Jacobian, then HEX08, PYR05, PEN06, TET04)
+    std::vector<BucketDev> bk;
+    std::vector<FieldDev> fd;
+    std::vector<AsmArgs> ag;
+    std::vector<double *> rp((size_t)n);
+    std::vector<int64_t> rl((size_t)n);
+    size_t smem = 0;
     for (int32_t k = 0; k < n; ++k) {
         Mesh *m = ctx->meshes[meshes[k]].get();
-        st = assemble_into(ctx, *m, prec, closure, mask, FEA_SCATTER_AUTO, rhs_out[k], nullptr, (cudaStream_t)stream);
-        if (st) return st;
+        rp[k] = rhs_out[k];
+        rl[k] = 3 * m->n;
+        for (auto &b : m->buckets) {
+            if (!b->count) continue;
+            bk.push_back(b->dev());
+            fd.push_back(m->field());
+            AsmArgs a;
+            a.mask = mask;
+            a.closure = closure;
+            a.rhs = rhs_out[k];
+            a.nut = nullptr;
+            a.err = ctx->d_err;
+            ag.push_back(a);
+            smem = std::max(smem, chunk_smem_bytes(bk.back()));
+        }
     }
+    auto cost = [](const BucketDev &b) { return b.fp64j ? 100 : kNen[b.etype] * kNg[b.etype]; };
+    std::vector<int32_t> order(bk.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int32_t)i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost(bk[x]) > cost(bk[y]); });
+    std::vector<int32_t> items;
+    for (int32_t bi : order)
+        for (int64_t c = 0; c < bk[bi].n_chunks; ++c) {
+            items.push_back(bi);
+            items.push_back((int32_t)c);
+        }
+    const int64_t n_items = (int64_t)items.size() / 2;
+    if (smem > kChunkSmemLimit) return fail(ctx, FEA_EINVAL, "batched chunk needs more than 200 KB of shared memory");
+    auto grow = [&](DevBuf<unsigned char> &d, size_t bytes) -> cudaError_t {
+        return d.n >= bytes ? cudaSuccess : d.alloc(bytes);
+    };
+    CK(grow(ctx->batch_bk, bk.size() * sizeof(BucketDev)));
+    CK(grow(ctx->batch_fd, fd.size() * sizeof(FieldDev)));
+    CK(grow(ctx->batch_ag, ag.size() * sizeof(AsmArgs)));
+    CK(grow(ctx->batch_items, items.size() * sizeof(int32_t)));
+    if (ctx->batch_rhs.n < (size_t)n) CK(ctx->batch_rhs.alloc(n));
+    if (ctx->batch_len.n < (size_t)n) CK(ctx->batch_len.alloc(n));
+    if (!ctx->batch_counter.n) CK(ctx->batch_counter.alloc(1));
+    CK(cudaMemcpyAsync(ctx->batch_bk.p, bk.data(), bk.size() * sizeof(BucketDev), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->batch_fd.p, fd.data(), fd.size() * sizeof(FieldDev), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->batch_ag.p, ag.data(), ag.size() * sizeof(AsmArgs), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->batch_items.p, items.data(), items.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->batch_rhs.p, rp.data(), n * sizeof(double *), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->batch_len.p, rl.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    CK(launch_zero_batch(ctx->batch_rhs.p, ctx->batch_len.p, n, s));
+    ProfRec pr{4, 0, nullptr, nullptr};
+    if (ctx->profiling) {
+        CK(cudaEventCreate(&pr.e0));
+        CK(cudaEventCreate(&pr.e1));
+        CK(cudaEventRecord(pr.e0, s));
+    }
+    CK(launch_assemble_batch(ctx->batch_bk.p, ctx->batch_fd.p, ctx->batch_ag.p, ctx->batch_items.p, n_items,
+                             ctx->batch_counter.p, smem, ctx->sms, s));
+    if (ctx->profiling) {
+        CK(cudaEventRecord(pr.e1, s));
+        ctx->prof.push_back(pr);
+    }
+    ctx->launches += 2;
     return FEA_OK;
 }
 
@@ -1002,7 +1082,7 @@ fea_status fea_set_plan(fea_ctx *ctx, int32_t mesh, const fea_plan *plan) {
         if (plan->chunk_acc != 0 && plan->chunk_acc != 1) return fail(ctx, FEA_EINVAL, "chunk_acc must be 0 or 1");
         if ((st = ensure_chunks(ctx, *m, plan->chunk_elems))) return st;
         for (auto &b : m->buckets)
-            if (b->count && chunk_smem_bytes(b->dev()) > 200 * 1024)
+            if (b->count && chunk_kernel_smem(b->dev(), plan->chunk_acc) > kChunkSmemLimit)
                 return fail(ctx, FEA_EINVAL, "chunk of %d elements needs more than 220 KB of shared memory",
                             plan->chunk_elems);
     }
@@ -1037,7 +1117,7 @@ fea_status fea_autotune(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure c
             if ((st = ensure_chunks(ctx, *m, cand.chunk_elems))) return st;
             bool fits = true;
             for (auto &b : m->buckets)
-                if (b->count && chunk_smem_bytes(b->dev()) > 200 * 1024) fits = false;
+                if (b->count && chunk_kernel_smem(b->dev(), cand.chunk_acc) > kChunkSmemLimit) fits = false;
             if (!fits) continue;
         }
         m->plan = cand;

@@ -85,6 +85,15 @@ cudaError_t launch_assemble_bucket(const BucketDev &b, const FieldDev &f, const 
 cudaError_t launch_assemble_chunk(const BucketDev &b, const FieldDev &f, const AsmArgs &a, int threads,
                                   int compensated, cudaStream_t s);
 size_t chunk_smem_bytes(const BucketDev &b);
+// shared memory of the chunk kernel that launch_assemble_chunk would launch
+size_t chunk_kernel_smem(const BucketDev &b, int compensated);
+constexpr size_t kChunkSmemLimit = 200 * 1024;
+// batched persistent launch over (category, chunk) items of many meshes
+cudaError_t launch_assemble_batch(const void *buckets, const void *fields, const void *args, const void *items,
+                                  int64_t n_items, unsigned long long *counter, size_t smem, int sms,
+                                  cudaStream_t s);
+size_t batch_item_bytes();
+cudaError_t launch_zero_batch(double *const *rhs_dev, const int64_t *len_dev, int n_meshes, cudaStream_t s);
 cudaError_t launch_tet_pipe(const BucketDev &b, const FieldDev &f, const AsmArgs &a, int threads, int sms,
                            cudaStream_t s);
 size_t tet_pipe_smem_bytes(const BucketDev &b);

@@ -14,6 +14,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "fea_internal.h"
 
 namespace fea {
@@ -457,11 +459,10 @@ __device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
 }
 
 template <int ET, bool J64, bool COMP>
-__global__ void __launch_bounds__(256) k_assemble_chunk(BucketDev b, FieldDev f, AsmArgs args) {
+__device__ __forceinline__ void chunk_body(const BucketDev &b, const FieldDev &f, const AsmArgs &args, int64_t k,
+                                           float4 *smem4) {
     constexpr int nen = kNen[ET], ng = kNg[ET];
-    extern __shared__ float4 smem4[];
     const int C = b.chunk_elems;
-    const int64_t k = blockIdx.x;
     const int64_t e0 = k * (int64_t)C;
     const int ne = (int)min((int64_t)C, b.count - e0);
     const int64_t nb = b.chunk_node_off[k];
@@ -565,6 +566,94 @@ __global__ void __launch_bounds__(256) k_assemble_chunk(BucketDev b, FieldDev f,
     }
 }
 
+template <int ET, bool J64, bool COMP>
+__global__ void __launch_bounds__(256) k_assemble_chunk(BucketDev b, FieldDev f, AsmArgs args) {
+    extern __shared__ float4 smem4[];
+    chunk_body<ET, J64, COMP>(b, f, args, blockIdx.x, smem4);
+}
+
+// ---------------------------------------------------------------------------
+// Batched persistent launch: every CTA pulls (category, chunk) work items of
+// many meshes from a device counter, heaviest categories first, and runs the
+// chunk body of the item's element type; per-item descriptors (category,
+// field, RHS) come from device tables built by the host per call.
+
+struct BatchItem {
+    int32_t bucket;   // index into the descriptor tables
+    int32_t chunk;    // chunk index within the bucket
+};
+
+__global__ void __launch_bounds__(256, 2) k_assemble_batch(const BucketDev *__restrict__ bk,
+                                                        const FieldDev *__restrict__ fd,
+                                                        const AsmArgs *__restrict__ ag,
+                                                        const BatchItem *__restrict__ items, int64_t n_items,
+                                                        unsigned long long *counter) {
+    extern __shared__ float4 smem4[];
+    __shared__ long long item_s;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long w = item_s;
+        __syncthreads();
+        if (w >= n_items) return;
+        const BatchItem it = items[w];
+        const BucketDev b = bk[it.bucket];
+        const FieldDev f = fd[it.bucket];
+        const AsmArgs a = ag[it.bucket];
+        switch (b.etype * 2 + b.fp64j) {
+            case 0: chunk_body<FEA_TET04, false, false>(b, f, a, it.chunk, smem4); break;
+            case 2: chunk_body<FEA_PYR05, false, false>(b, f, a, it.chunk, smem4); break;
+            case 4: chunk_body<FEA_PEN06, false, false>(b, f, a, it.chunk, smem4); break;
+            case 5: chunk_body<FEA_PEN06, true, false>(b, f, a, it.chunk, smem4); break;
+            case 6: chunk_body<FEA_HEX08, false, false>(b, f, a, it.chunk, smem4); break;
+            default: break;   // FP64-Jacobian TET04/PYR05/HEX08: not batched (host falls back)
+        }
+        __syncthreads();   // shared memory is reused by the next item
+    }
+}
+
+cudaError_t launch_assemble_batch(const void *buckets, const void *fields, const void *args, const void *items,
+                                  int64_t n_items, unsigned long long *counter, size_t smem, int sms,
+                                  cudaStream_t s) {
+    if (n_items == 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_assemble_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_assemble_batch, 256, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = std::min<int64_t>(n_items, (int64_t)per_sm * sms);
+    k_assemble_batch<<<(unsigned)grid, 256, smem, s>>>(
+        static_cast<const BucketDev *>(buckets), static_cast<const FieldDev *>(fields),
+        static_cast<const AsmArgs *>(args), static_cast<const BatchItem *>(items), n_items, counter);
+    return cudaGetLastError();
+}
+
+size_t batch_item_bytes() { return sizeof(BatchItem); }
+
+// zero the RHS of every mesh of a batch in one launch: blockIdx.y = mesh
+__global__ void k_zero_batch(double *const *rhs, const int64_t *len) {
+    double *r = rhs[blockIdx.y];
+    const int64_t n = len[blockIdx.y];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = 0.0;
+}
+
+cudaError_t launch_zero_batch(double *const *rhs_dev, const int64_t *len_dev, int n_meshes, cudaStream_t s) {
+    if (n_meshes <= 0) return cudaSuccess;
+    k_zero_batch<<<dim3(64, (unsigned)n_meshes), 256, 0, s>>>(rhs_dev, len_dev);
+    return cudaGetLastError();
+}
+
+
+size_t chunk_kernel_smem(const BucketDev &b, int compensated) {
+    if (b.etype == FEA_TET04 && !b.fp64j && !compensated && tet_pipe_smem_bytes(b) <= kChunkSmemLimit)
+        return tet_pipe_smem_bytes(b);
+    return chunk_smem_bytes(b);
+}
+
 size_t chunk_smem_bytes(const BucketDev &b) {
     return sizeof(float4) * (2 * (size_t)b.max_chunk_nodes + (size_t)kNen[b.etype] * b.chunk_elems);
 }
@@ -596,7 +685,8 @@ cudaError_t launch_assemble_chunk(const BucketDev &b, const FieldDev &f, const A
                                   int compensated, cudaStream_t s) {
     if (b.count == 0) return cudaSuccess;
     if (!b.lconn || b.n_chunks <= 0) return cudaErrorInvalidValue;
-    if (b.etype == FEA_TET04 && !b.fp64j && !compensated) return launch_tet_pipe(b, f, a, threads, 0, s);
+    if (b.etype == FEA_TET04 && !b.fp64j && !compensated && tet_pipe_smem_bytes(b) <= kChunkSmemLimit)
+        return launch_tet_pipe(b, f, a, threads, 0, s);
     if (threads > 256) threads = 256;
     switch (b.etype) {
         case FEA_TET04:
