@@ -206,6 +206,38 @@ fea_status fea_rk_step_graph(fea_ctx *ctx, int32_t mesh, double dt, fea_prec pre
 /* Copies the current state u^(k) [3][n_nodes] to out (host or device). */
 fea_status fea_state_download(fea_ctx *ctx, int32_t mesh, double *out, void *stream);
 
+/* ---- learned closure --------------------------------------------------
+ * A small network that stands in for the Vreman closure of section 2.1 (the
+ * paper has no learned model): 6 -> 64 -> 64 -> 64 -> 1, SiLU hidden layers,
+ * softplus output, nu_t = out_scale * softplus(z).  Inputs per Gauss point
+ * (per element for TET04): with S = (G+G^T)/2, O = (G-G^T)/2,
+ *   x_k = sign(I_k) |I_k|^(1/d_k),  I = (tr S^2, tr O^2, tr S^3, tr S O^2,
+ *   tr S^2 O^2),  d = (2, 2, 3, 3, 4),  x_6 = log Delta  (Delta = V_e^(1/3)),
+ * normalised as (x - mean) / std.  Parameter vector theta (FP32, 8,833):
+ *   w1[64][6] b1[64] w2[64][64] b2[64] w3[64][64] b3[64] w4[64] b4[1].
+ * Evaluation uses BF16 weights and activations with FP32 accumulation on
+ * the tensor cores; the FP32 master copy is updated by Adam. */
+
+/* Loads theta, the feature mean and std [6] (host or device) and out_scale;
+ * resets the Adam state.  Errors: FEA_EINVAL (null, std <= 0, scale <= 0). */
+fea_status fea_mlp_load(fea_ctx *ctx, const float *theta, const float *feat_mean, const float *feat_std,
+                        double out_scale, void *stream);
+
+/* Copies the current FP32 parameters to theta_out [8833] (host or device). */
+fea_status fea_mlp_get(fea_ctx *ctx, float *theta_out, void *stream);
+
+/* nu_t for B rows of raw features x [B][6] (device) into nut [B] (device). */
+fea_status fea_mlp_forward(fea_ctx *ctx, const float *x, int64_t B, float *nut, void *stream);
+
+/* One training step on B samples: raw features x [B][6] and targets y [B]
+ * in units of out_scale (device); loss = mean (softplus(z) - y)^2.  The
+ * forward and backward GEMMs run on the tensor cores, then Adam (lr,
+ * beta = 0.9, 0.999, eps = 1e-8) updates theta.  loss_out (optional, host or
+ * device, 1 float) receives the loss before the update; grad_out (optional,
+ * host or device, [8833]) the gradient d loss / d theta. */
+fea_status fea_mlp_train_step(fea_ctx *ctx, const float *x, const float *y, int64_t B, float lr, float *loss_out,
+                              float *grad_out, void *stream);
+
 /* Allocation-free RK stage (no counterpart in the paper).
  *
  * For callers that cannot allocate device memory at call time -- code that

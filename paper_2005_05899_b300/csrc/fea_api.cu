@@ -295,6 +295,12 @@ struct fea_ctx {
     DevBuf<double *> batch_rhs;
     DevBuf<int64_t> batch_len;
     DevBuf<unsigned long long> batch_counter;
+    // learned closure: FP32 master parameters, Adam moments, packed BF16 weights
+    DevBuf<float> mlp_theta, mlp_m1, mlp_m2, mlp_grad, mlp_loss, mlp_norm;
+    DevBuf<unsigned char> mlp_w;
+    int64_t mlp_step = 0;
+    double mlp_scale = 0.0;
+    bool mlp_ready = false;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t launches = 0;
 };
@@ -501,8 +507,10 @@ fea_status assemble_into(fea_ctx *ctx, Mesh &m, fea_prec prec, fea_closure closu
 
 fea_status check_args(fea_ctx *ctx, fea_prec prec, fea_closure closure, uint32_t mask) {
     if (prec != FEA_FP64 && prec != FEA_MIXED) return fail(ctx, FEA_EINVAL, "bad precision %d", (int)prec);
-    if (closure != FEA_CLOSURE_NONE && closure != FEA_CLOSURE_VREMAN)
-        return fail(ctx, FEA_EINVAL, "closure %d not available", (int)closure);
+    if (closure != FEA_CLOSURE_NONE && closure != FEA_CLOSURE_VREMAN && closure != FEA_CLOSURE_MLP)
+        return fail(ctx, FEA_EINVAL, "bad closure %d", (int)closure);
+    if (closure == FEA_CLOSURE_MLP && !ctx->mlp_ready)
+        return fail(ctx, FEA_ESTATE, "MLP closure requested before fea_mlp_load");
     if (mask & ~15u) return fail(ctx, FEA_EINVAL, "bad term mask 0x%x", mask);
     return FEA_OK;
 }
@@ -1145,6 +1153,79 @@ fea_status fea_autotune(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure c
         cudaGraphExecDestroy(m->graph.exec);
         m->graph.exec = nullptr;
     }
+    return FEA_OK;
+}
+
+fea_status fea_mlp_load(fea_ctx *ctx, const float *theta, const float *feat_mean, const float *feat_std,
+                        double out_scale, void *stream) {
+    if (!ctx) return FEA_EINVAL;
+    if (!theta || !feat_mean || !feat_std) return fail(ctx, FEA_EINVAL, "null MLP argument");
+    if (!(out_scale > 0.0)) return fail(ctx, FEA_EINVAL, "out_scale must be > 0");
+    for (int k = 0; k < 6; ++k) {
+        float sd = 0.f;
+        CK(cudaMemcpy(&sd, feat_std + k, sizeof(float), cudaMemcpyDefault));
+        if (!(sd > 0.f)) return fail(ctx, FEA_EINVAL, "feature std must be > 0");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int np = mlp_param_count();
+    if (!ctx->mlp_theta.n) {
+        CK(ctx->mlp_theta.alloc(np));
+        CK(ctx->mlp_m1.alloc(np));
+        CK(ctx->mlp_m2.alloc(np));
+        CK(ctx->mlp_grad.alloc(np));
+        CK(ctx->mlp_loss.alloc(1));
+        CK(ctx->mlp_norm.alloc(12));
+        CK(ctx->mlp_w.alloc(mlp_weights_bytes()));
+    }
+    CK(cudaMemcpyAsync(ctx->mlp_theta.p, theta, sizeof(float) * np, cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(ctx->mlp_norm.p, feat_mean, sizeof(float) * 6, cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(ctx->mlp_norm.p + 6, feat_std, sizeof(float) * 6, cudaMemcpyDefault, s));
+    CK(cudaMemsetAsync(ctx->mlp_m1.p, 0, sizeof(float) * np, s));
+    CK(cudaMemsetAsync(ctx->mlp_m2.p, 0, sizeof(float) * np, s));
+    CK(launch_mlp_pack(ctx->mlp_theta.p, ctx->mlp_norm.p, ctx->mlp_norm.p + 6, (float)out_scale, ctx->mlp_w.p, s));
+    ctx->launches++;
+    ctx->mlp_step = 0;
+    ctx->mlp_scale = out_scale;
+    ctx->mlp_ready = true;
+    return FEA_OK;
+}
+
+fea_status fea_mlp_get(fea_ctx *ctx, float *theta_out, void *stream) {
+    if (!ctx) return FEA_EINVAL;
+    if (!theta_out) return fail(ctx, FEA_EINVAL, "null output");
+    if (!ctx->mlp_ready) return fail(ctx, FEA_ESTATE, "no MLP loaded");
+    CK(cudaMemcpyAsync(theta_out, ctx->mlp_theta.p, sizeof(float) * mlp_param_count(), cudaMemcpyDefault,
+                       (cudaStream_t)stream));
+    return FEA_OK;
+}
+
+fea_status fea_mlp_forward(fea_ctx *ctx, const float *x, int64_t B, float *nut, void *stream) {
+    if (!ctx) return FEA_EINVAL;
+    if (!x || !nut || B < 0) return fail(ctx, FEA_EINVAL, "bad MLP forward arguments");
+    if (!ctx->mlp_ready) return fail(ctx, FEA_ESTATE, "no MLP loaded");
+    CK(launch_mlp_forward(ctx->mlp_w.p, x, B, nut, ctx->sms, (cudaStream_t)stream));
+    ctx->launches++;
+    return FEA_OK;
+}
+
+fea_status fea_mlp_train_step(fea_ctx *ctx, const float *x, const float *y, int64_t B, float lr, float *loss_out,
+                              float *grad_out, void *stream) {
+    if (!ctx) return FEA_EINVAL;
+    if (!x || !y || B <= 0 || !(lr >= 0.f)) return fail(ctx, FEA_EINVAL, "bad MLP training arguments");
+    if (!ctx->mlp_ready) return fail(ctx, FEA_ESTATE, "no MLP loaded");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int np = mlp_param_count();
+    CK(cudaMemsetAsync(ctx->mlp_grad.p, 0, sizeof(float) * np, s));
+    CK(cudaMemsetAsync(ctx->mlp_loss.p, 0, sizeof(float), s));
+    CK(launch_mlp_train(ctx->mlp_w.p, x, y, B, ctx->mlp_grad.p, ctx->mlp_loss.p, s));
+    if (grad_out) CK(cudaMemcpyAsync(grad_out, ctx->mlp_grad.p, sizeof(float) * np, cudaMemcpyDefault, s));
+    if (loss_out) CK(cudaMemcpyAsync(loss_out, ctx->mlp_loss.p, sizeof(float), cudaMemcpyDefault, s));
+    ctx->mlp_step++;
+    CK(launch_adam(ctx->mlp_theta.p, ctx->mlp_grad.p, ctx->mlp_m1.p, ctx->mlp_m2.p, np, lr, 0.9f, 0.999f, 1e-8f,
+                   ctx->mlp_step, s));
+    CK(launch_mlp_pack(ctx->mlp_theta.p, ctx->mlp_norm.p, ctx->mlp_norm.p + 6, (float)ctx->mlp_scale,
+                       ctx->mlp_w.p, s));
+    ctx->launches += 3;
     return FEA_OK;
 }
 

@@ -109,6 +109,17 @@ cudaError_t launch_pack_field(int64_t n, const double *u64, const double *p64, f
 cudaError_t launch_f32_to_f64(const float *src, double *dst, int64_t count, cudaStream_t s);
 cudaError_t launch_recip(const double *m, double *minv, int64_t n, cudaStream_t s);
 
+// MLP closure (fea_mlp.cu)
+size_t mlp_weights_bytes();
+int mlp_param_count();
+cudaError_t launch_mlp_pack(const float *theta, const float *mean, const float *stdv, float out_scale, void *w,
+                            cudaStream_t s);
+cudaError_t launch_mlp_forward(const void *w, const float *x, int64_t B, float *y, int sms, cudaStream_t s);
+cudaError_t launch_mlp_train(const void *w, const float *x, const float *y, int64_t B, float *grad, float *loss,
+                             cudaStream_t s);
+cudaError_t launch_adam(float *theta, const float *grad, float *m1, float *m2, int n, float lr, float b1, float b2,
+                        float eps, int64_t step, cudaStream_t s);
+
 // One RK stage from caller state arrays, with caller-provided scratch
 // (rhs [3][n] FP64, up [n] FP32 (u, v, w, p)); used by the allocation-free
 // entry point.  Implemented in fea_api.cu.

@@ -1,0 +1,237 @@
+// Learned eddy-viscosity closure: a 6 -> 64 -> 64 -> 64 -> 1 MLP (SiLU hidden
+// layers, softplus output) evaluated on BF16 tensor cores with FP32
+// accumulation, warp-cooperatively on tiles of 16 rows.
+//
+// Inputs per row (Gauss point or element): the invariants of S = (G+G^T)/2
+// and O = (G-G^T)/2 of the velocity gradient G_ij = du_i/dx_j,
+//   x_k = sign(I_k) |I_k|^(1/d_k), I = (tr S^2, tr O^2, tr S^3, tr S O^2,
+//   tr S^2 O^2), d = (2, 2, 3, 3, 4), and x_6 = log Delta,
+// normalised as (x - mean) / std; output nu_t = out_scale softplus(z).
+//
+// Tensor-core tiles: mma.sync m16n8k16 (row.col, BF16 in, FP32 accumulate).
+// For lane l: g = l / 4, t = l % 4; an A fragment holds rows (g, g+8) and
+// columns (2t, 2t+1, 2t+8, 2t+9) of a 16 x 16 tile; a C fragment holds rows
+// (g, g+8), columns (2t, 2t+1) of a 16 x 8 tile.  The C fragments of the
+// n-tiles 2k and 2k+1 of one layer are exactly the A fragment of k-step k of
+// the next layer, so the hidden activations never leave registers.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fea {
+
+constexpr int kMlpIn = 6, kMlpH = 64;
+constexpr int kMlpParams = kMlpH * kMlpIn + kMlpH + 2 * (kMlpH * kMlpH + kMlpH) + kMlpH + 1;  // 8,833
+constexpr int kW1Pitch = 24;  // bf16 per row of W1 [64][16 used + pad]: 12 words, conflict-free fragments
+constexpr int kWPitch = 72;   // bf16 per row of W2, W3 [64][64 + pad]: 36 words
+
+// Inference part of the device-resident MLP (copied into shared memory by
+// the kernels that evaluate it).
+struct __align__(16) MlpInfer {
+    uint16_t w1[kMlpH][kW1Pitch];  // bf16 W1[out][in], inputs 6..15 zero
+    uint16_t w2[kMlpH][kWPitch];   // bf16 W2[out][in]
+    uint16_t w3[kMlpH][kWPitch];
+    float b1[kMlpH], b2[kMlpH], b3[kMlpH], w4[kMlpH];
+    float b4;
+    float mean[kMlpIn], istd[kMlpIn];
+    float out_scale;
+};
+
+// Inference part plus the transposed weights used by the backward pass.
+struct __align__(16) MlpWeights {
+    MlpInfer inf;
+    uint16_t w2t[kMlpH][kWPitch];  // bf16 W2^T[in][out]
+    uint16_t w3t[kMlpH][kWPitch];
+};
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float sigmoid_f(float z) { return 1.0f / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float softplus_f(float z) { return z > 20.0f ? z : log1pf(__expf(z)); }
+
+__device__ __forceinline__ float signed_root(float v, int d) {
+    const float a = fabsf(v);
+    float r = d == 2 ? sqrtf(a) : (d == 3 ? cbrtf(a) : sqrtf(sqrtf(a)));
+    return v < 0.0f ? -r : r;
+}
+
+// Raw features of one velocity gradient (row-major G) and filter width.
+__device__ __forceinline__ void mlp_features(const float G[3][3], float delta, float x[kMlpIn]) {
+    float S[3][3], O[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            S[i][j] = 0.5f * (G[i][j] + G[j][i]);
+            O[i][j] = 0.5f * (G[i][j] - G[j][i]);
+        }
+    float S2[3][3], O2[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float a = 0.f, b = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                a += S[i][k] * S[k][j];
+                b += O[i][k] * O[k][j];
+            }
+            S2[i][j] = a;
+            O2[i][j] = b;
+        }
+    float trS2 = 0.f, trO2 = 0.f, trS3 = 0.f, trSO2 = 0.f, trS2O2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        trS2 += S2[i][i];
+        trO2 += O2[i][i];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            trS3 += S2[i][k] * S[k][i];
+            trSO2 += S[i][k] * O2[k][i];
+            trS2O2 += S2[i][k] * O2[k][i];
+        }
+    }
+    x[0] = signed_root(trS2, 2);
+    x[1] = signed_root(trO2, 2);
+    x[2] = signed_root(trS3, 3);
+    x[3] = signed_root(trSO2, 3);
+    x[4] = signed_root(trS2O2, 4);
+    x[5] = logf(delta);
+}
+
+// A fragment of the first layer from a per-warp shared tile of normalised
+// features: feat[row][kW1Pitch] bf16 (columns 6..15 zero); `row0` selects
+// the 16-row half of a 32-row warp tile.
+__device__ __forceinline__ void mlp_load_a1(const uint16_t *feat, int row0, uint32_t a[4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const uint32_t *f32 = reinterpret_cast<const uint32_t *>(feat);
+    constexpr int P = kW1Pitch / 2;  // words per row
+    a[0] = f32[(row0 + g) * P + t];
+    a[1] = f32[(row0 + g + 8) * P + t];
+    a[2] = f32[(row0 + g) * P + 4 + t];
+    a[3] = f32[(row0 + g + 8) * P + 4 + t];
+}
+
+// One hidden layer: C = A W^T + b, then SiLU, returned as the next layer's
+// A fragments.  K = 16 (first layer, W pitch kW1Pitch) or 64.
+template <int KSTEPS, int PITCH>
+__device__ __forceinline__ void mlp_layer(const uint32_t a[KSTEPS][4], const uint16_t (*W)[PITCH], const float *bias,
+                                          uint32_t out[4][4], float *zs /* optional [8][4] pre-activations */) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float c[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.f;
+        const uint32_t *row = reinterpret_cast<const uint32_t *>(W[8 * j + g]);
+#pragma unroll
+        for (int kk = 0; kk < KSTEPS; ++kk) mma_bf16_16816(c[j], a[kk], row[8 * kk + t], row[8 * kk + 4 + t]);
+        const float b0 = bias[8 * j + 2 * t], b1 = bias[8 * j + 2 * t + 1];
+        c[j][0] += b0;
+        c[j][1] += b1;
+        c[j][2] += b0;
+        c[j][3] += b1;
+        if (zs) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) zs[j * 4 + q] = c[j][q];
+        }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        out[kk][0] = pack_bf16x2(silu_f(c[2 * kk][0]), silu_f(c[2 * kk][1]));
+        out[kk][1] = pack_bf16x2(silu_f(c[2 * kk][2]), silu_f(c[2 * kk][3]));
+        out[kk][2] = pack_bf16x2(silu_f(c[2 * kk + 1][0]), silu_f(c[2 * kk + 1][1]));
+        out[kk][3] = pack_bf16x2(silu_f(c[2 * kk + 1][2]), silu_f(c[2 * kk + 1][3]));
+    }
+}
+
+// z of the output layer for rows g (zg) and g+8 (zg8), valid in every lane,
+// from the last hidden layer's A fragments (BF16 activations, FP32 dot).
+__device__ __forceinline__ void mlp_output(const uint32_t h[4][4], const float *w4, float b4, float &zg, float &zg8) {
+    const int lane = threadIdx.x & 31, t = lane & 3;
+    float pg = 0.f, pg8 = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int col = 16 * kk + 8 * half + 2 * t;
+            const __nv_bfloat162 vg = *reinterpret_cast<const __nv_bfloat162 *>(&h[kk][2 * half]);
+            const __nv_bfloat162 vg8 = *reinterpret_cast<const __nv_bfloat162 *>(&h[kk][2 * half + 1]);
+            pg += __low2float(vg) * w4[col] + __high2float(vg) * w4[col + 1];
+            pg8 += __low2float(vg8) * w4[col] + __high2float(vg8) * w4[col + 1];
+        }
+    }
+    pg += __shfl_xor_sync(0xffffffffu, pg, 1);
+    pg += __shfl_xor_sync(0xffffffffu, pg, 2);
+    pg8 += __shfl_xor_sync(0xffffffffu, pg8, 1);
+    pg8 += __shfl_xor_sync(0xffffffffu, pg8, 2);
+    zg = pg + b4;
+    zg8 = pg8 + b4;
+}
+
+// Full forward pass of a 16-row tile given the first layer's A fragment.
+__device__ __forceinline__ void mlp_tile_forward(const MlpInfer &w, const uint32_t a1[4], float &zg, float &zg8) {
+    uint32_t h1[4][4], h2[4][4], h3[4][4];
+    uint32_t a1k[1][4] = {{a1[0], a1[1], a1[2], a1[3]}};
+    mlp_layer<1, kW1Pitch>(a1k, w.w1, w.b1, h1, nullptr);
+    mlp_layer<4, kWPitch>(h1, w.w2, w.b2, h2, nullptr);
+    mlp_layer<4, kWPitch>(h2, w.w3, w.b3, h3, nullptr);
+    mlp_output(h3, w.w4, w.b4, zg, zg8);
+}
+
+// Copies the inference weights into shared memory (all threads of the CTA;
+// ends with a barrier).
+__device__ __forceinline__ void mlp_copy_infer(const MlpInfer *g, MlpInfer *s) {
+    const int4 *src = reinterpret_cast<const int4 *>(g);
+    int4 *dst = reinterpret_cast<int4 *>(s);
+    for (int k = threadIdx.x; k < (int)(sizeof(MlpInfer) / 16); k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+}
+
+// Warp-cooperative nu_t for 32 rows: every lane passes its row's raw
+// features (lanes of inactive rows pass anything finite); returns the lane's
+// nu_t.  scratch: per-warp shared tile of 32 x kW1Pitch bf16.  All 32 lanes
+// of the warp must call this together.
+__device__ __forceinline__ float mlp_warp_nut(const MlpInfer &w, const float x[kMlpIn], uint16_t *scratch) {
+    const int lane = threadIdx.x & 31;
+    uint32_t *row = reinterpret_cast<uint32_t *>(scratch + lane * kW1Pitch);
+    float xn[kMlpIn];
+#pragma unroll
+    for (int k = 0; k < kMlpIn; ++k) xn[k] = (x[k] - w.mean[k]) * w.istd[k];
+    row[0] = pack_bf16x2(xn[0], xn[1]);
+    row[1] = pack_bf16x2(xn[2], xn[3]);
+    row[2] = pack_bf16x2(xn[4], xn[5]);
+#pragma unroll
+    for (int q = 3; q < 8; ++q) row[q] = 0u;
+    __syncwarp();
+    float nut_mine = 0.f;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        uint32_t a1[4];
+        mlp_load_a1(scratch, 16 * half, a1);
+        float zg, zg8;
+        mlp_tile_forward(w, a1, zg, zg8);
+        // row r of this half lives in lanes 4 (r mod 8) + {0..3}
+        const int g = (lane & 15) & 7;   // the group that holds this lane's row
+        const float v_g = __shfl_sync(0xffffffffu, zg, 4 * g);
+        const float v_g8 = __shfl_sync(0xffffffffu, zg8, 4 * g);
+        if ((lane >> 4) == half) nut_mine = ((lane & 15) < 8) ? v_g : v_g8;
+    }
+    __syncwarp();
+    return w.out_scale * softplus_f(nut_mine);
+}
+
+}  // namespace fea

@@ -31,7 +31,9 @@ EXPORTED = (
     "fea_lumped_mass", "fea_field_upload", "fea_assemble_rhs", "fea_assemble_rhs_batched", "fea_periodic_fold",
     "fea_rk_stage", "fea_rk_step_graph", "fea_state_download", "fea_get_plan", "fea_set_plan", "fea_autotune",
     "fea_sync_status", "fea_launch_count", "fea_profile_enable", "fea_profile_read", "fea_rk_stage_noalloc",
+    "fea_mlp_load", "fea_mlp_get", "fea_mlp_forward", "fea_mlp_train_step",
 )
+MLP_NPARAM = 8833
 NOALLOC_MAX_NODES = 262144
 
 
@@ -93,6 +95,10 @@ def lib() -> ctypes.CDLL:
         L.fea_autotune.argtypes = [vp, i32, ctypes.c_int, ctypes.c_int, ctypes.c_char_p]
         L.fea_sync_status.argtypes = [vp, vp]
         L.fea_profile_enable.argtypes = [vp, ctypes.c_int]
+        L.fea_mlp_load.argtypes = [vp, vp, vp, vp, dbl, vp]
+        L.fea_mlp_get.argtypes = [vp, vp, vp]
+        L.fea_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
+        L.fea_mlp_train_step.argtypes = [vp, vp, vp, i64, ctypes.c_float, vp, vp, vp]
         L.fea_rk_stage_noalloc.argtypes = [vp, i32, i32, dbl, ctypes.c_int, ctypes.c_int, dbl, dbl, vp, vp, vp, vp,
                                            vp]
         L.fea_profile_read.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(dbl), ctypes.POINTER(i64),
@@ -166,6 +172,31 @@ class Context:
         self.check(self._lib.fea_profile_read(self.handle, etype, fp64_jac, ctypes.byref(ms), ctypes.byref(n),
                                               1 if reset else 0))
         return ms.value, n.value
+
+    # ---- learned closure ----
+    def mlp_load(self, theta, feat_mean, feat_std, out_scale: float, stream=None):
+        """theta [8833], feat_mean [6], feat_std [6]: float32 numpy (host) or torch tensors."""
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) if not hasattr(a, "data_ptr") else a
+                for a in (theta, feat_mean, feat_std)]
+        self._mlp_keep = arrs
+        self.check(self._lib.fea_mlp_load(self.handle, _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]),
+                                          float(out_scale), _stream(stream)))
+
+    def mlp_get(self) -> np.ndarray:
+        out = np.zeros(MLP_NPARAM, np.float32)
+        self.check(self._lib.fea_mlp_get(self.handle, _ptr(out), _stream(None)))
+        import torch
+        torch.cuda.current_stream().synchronize()
+        return out
+
+    def mlp_forward(self, x, out, stream=None):
+        """x: float32 device tensor [B][6] of raw features; out: float32 device [B]."""
+        self.check(self._lib.fea_mlp_forward(self.handle, _ptr(x), int(x.shape[0]), _ptr(out), _stream(stream)))
+        return out
+
+    def mlp_train_step(self, x, y, lr: float, loss_out=None, grad_out=None, stream=None):
+        self.check(self._lib.fea_mlp_train_step(self.handle, _ptr(x), _ptr(y), int(x.shape[0]), float(lr),
+                                                _ptr(loss_out), _ptr(grad_out), _stream(stream)))
 
     def sync_status(self, stream=None):
         self.check(self._lib.fea_sync_status(self.handle, _stream(stream)))

@@ -1,0 +1,136 @@
+"""GPU MLP closure kernels (BF16 tensor cores) against the FP64 oracle.
+
+Tolerances: the GPU rounds weights W1..W3 and every hidden activation to
+BF16 (8 significant bits, relative 2^-9 per rounding) and accumulates in
+FP32, so the forward pass is compared at rel 2e-2 (+ a floor of 1e-3 of the
+largest value) against the oracle evaluated with the same BF16-rounded
+weights and inputs, and the gradient at 5e-2 relative in the L2 norm.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2005_05899_b300 import fea
+
+pytestmark = pytest.mark.gpu
+
+H, I = 64, 6
+
+
+def bf16_round(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def split(theta):
+    off = 0
+    out = {}
+    for name, n in (("w1", H * I), ("b1", H), ("w2", H * H), ("b2", H), ("w3", H * H), ("b3", H), ("w4", H),
+                    ("b4", 1)):
+        out[name] = theta[off:off + n]
+        off += n
+    return out
+
+
+def gpu_rounded_theta(theta):
+    """theta as the GPU evaluates it: W1..W3 in BF16, the rest FP32."""
+    t = theta.astype(np.float32).copy()
+    p = split(t)
+    for name in ("w1", "w2", "w3"):
+        p[name][:] = bf16_round(p[name])
+    return t.astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = fea.Context(0)
+    yield c
+    c.close()
+
+
+def sample_features(rng, n):
+    G = rng.standard_normal((n, 3, 3)) * rng.uniform(0.1, 3.0, (n, 1, 1))
+    delta = rng.uniform(0.005, 0.05, n)
+    return np.stack([O.mlp_features(G[k], delta[k]) for k in range(n)]).astype(np.float32)
+
+
+def test_forward_matches_oracle(ctx):
+    rng = np.random.default_rng(0)
+    theta = (0.3 * rng.standard_normal(fea.MLP_NPARAM)).astype(np.float32)
+    x = sample_features(rng, 3000)
+    mean = x.mean(axis=0).astype(np.float32)
+    std = (x.std(axis=0) + 1e-3).astype(np.float32)
+    scale = 2e-4
+    ctx.mlp_load(theta, mean, std, scale)
+    xt = torch.tensor(x, device="cuda")
+    out = torch.empty(x.shape[0], dtype=torch.float32, device="cuda")
+    ctx.mlp_forward(xt, out)
+    ctx.sync_status()
+    got = out.cpu().numpy().astype(np.float64)
+    # oracle on the GPU's BF16 weights and BF16 normalised inputs
+    xn = bf16_round((x - mean) / std).astype(np.float64)
+    mlp = O.MLPParams(gpu_rounded_theta(theta), np.zeros(6), np.ones(6), scale)
+    ref = O.mlp_forward(mlp, xn)
+    assert np.all(np.abs(got - ref) <= 2e-2 * np.abs(ref) + 1e-3 * np.abs(ref).max())
+    assert np.corrcoef(got, ref)[0, 1] > 0.999
+
+
+def test_gradient_matches_oracle_and_adam_step(ctx):
+    rng = np.random.default_rng(1)
+    theta = (0.3 * rng.standard_normal(fea.MLP_NPARAM)).astype(np.float32)
+    B = 4099                       # ragged: not a multiple of the 64-row CTA tile
+    x = sample_features(rng, B)
+    mean = x.mean(axis=0).astype(np.float32)
+    std = (x.std(axis=0) + 1e-3).astype(np.float32)
+    y = rng.uniform(0.0, 2.0, B).astype(np.float32)
+    ctx.mlp_load(theta, mean, std, 1.0)
+    xt = torch.tensor(x, device="cuda")
+    yt = torch.tensor(y, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    grad = torch.zeros(fea.MLP_NPARAM, dtype=torch.float32, device="cuda")
+    lr = 1e-3
+    ctx.mlp_train_step(xt, yt, lr, loss_out=loss, grad_out=grad)
+    ctx.sync_status()
+    g = grad.cpu().numpy().astype(np.float64)
+    xn = bf16_round((x - mean) / std).astype(np.float64)
+    ref_loss, ref_g = O.mlp_loss_grad(gpu_rounded_theta(theta), xn, y.astype(np.float64))
+    assert abs(loss.item() - ref_loss) <= 2e-2 * ref_loss
+    assert np.linalg.norm(g - ref_g) <= 5e-2 * np.linalg.norm(ref_g)
+    for name_range in ((0, H * I), (H * I + H, H * I + H + H * H)):   # w1 and w2 blocks separately
+        a, b = name_range
+        assert np.linalg.norm(g[a:b] - ref_g[a:b]) <= 5e-2 * np.linalg.norm(ref_g[a:b])
+    # Adam on the GPU gradient, against the oracle's Adam
+    th = theta.astype(np.float64).copy()
+    m1 = np.zeros_like(th)
+    m2 = np.zeros_like(th)
+    O.adam_step(th, g, m1, m2, lr, 0.9, 0.999, 1e-8, 1)
+    new = ctx.mlp_get().astype(np.float64)
+    assert np.abs(new - th).max() <= 1e-6
+
+
+def test_training_reduces_loss(ctx):
+    rng = np.random.default_rng(2)
+    B = 16384
+    x = sample_features(rng, B)
+    mean = x.mean(axis=0).astype(np.float32)
+    std = (x.std(axis=0) + 1e-3).astype(np.float32)
+    # smooth synthetic target in out_scale units
+    xn = (x - mean) / std
+    y = np.log1p(np.exp(0.8 * xn[:, 0] - 0.5 * xn[:, 1] + 0.3 * xn[:, 5])).astype(np.float32)
+    theta = (0.1 * rng.standard_normal(fea.MLP_NPARAM)).astype(np.float32)
+    ctx.mlp_load(theta, mean, std, 1.0)
+    xt = torch.tensor(x, device="cuda")
+    yt = torch.tensor(y, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    first = None
+    for step in range(300):
+        ctx.mlp_train_step(xt, yt, 3e-3, loss_out=loss)
+        if step == 0:
+            torch.cuda.synchronize()
+            first = loss.item()
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    assert loss.item() < 0.1 * first, (first, loss.item())
