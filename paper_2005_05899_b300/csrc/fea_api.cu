@@ -478,6 +478,7 @@ fea_status assemble_into(fea_ctx *ctx, Mesh &m, fea_prec prec, fea_closure closu
             a.rhs = rhs;
             a.nut = nut ? nut + type_nut_offset(m, b.etype) : nullptr;
             a.err = ctx->d_err;
+            a.mlp = closure == FEA_CLOSURE_MLP ? ctx->mlp_w.p : nullptr;
             cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
             if (ctx->profiling) CK(cudaStreamIsCapturing(s, &cap));
             ProfRec pr{b.etype, b.fp64j, nullptr, nullptr};
@@ -595,6 +596,7 @@ fea_status stage_with_scratch(fea_ctx *ctx, int32_t mesh, int32_t stage, double 
             a.rhs = rhs;
             a.nut = nullptr;
             a.err = ctx->d_err;
+            a.mlp = closure == FEA_CLOSURE_MLP ? ctx->mlp_w.p : nullptr;
             if (prec == FEA_MIXED && scatter == FEA_SCATTER_CHUNK && b.lconn.p)
                 CK(launch_assemble_chunk(b.dev(), f, a, m->plan.threads_per_block, m->plan.chunk_acc, ls));
             else
@@ -946,6 +948,7 @@ fea_status fea_assemble_rhs_batched(fea_ctx *ctx, const int32_t *meshes, int32_t
             a.rhs = rhs_out[k];
             a.nut = nullptr;
             a.err = ctx->d_err;
+            a.mlp = closure == FEA_CLOSURE_MLP ? ctx->mlp_w.p : nullptr;
             ag.push_back(a);
             smem = std::max(smem, chunk_smem_bytes(bk.back()));
         }
@@ -986,7 +989,7 @@ fea_status fea_assemble_rhs_batched(fea_ctx *ctx, const int32_t *meshes, int32_t
         CK(cudaEventRecord(pr.e0, s));
     }
     CK(launch_assemble_batch(ctx->batch_bk.p, ctx->batch_fd.p, ctx->batch_ag.p, ctx->batch_items.p, n_items,
-                             ctx->batch_counter.p, smem, ctx->sms, s));
+                             ctx->batch_counter.p, smem, ctx->sms, closure == FEA_CLOSURE_MLP, s));
     if (ctx->profiling) {
         CK(cudaEventRecord(pr.e1, s));
         ctx->prof.push_back(pr);

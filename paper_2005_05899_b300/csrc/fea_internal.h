@@ -76,6 +76,7 @@ struct AsmArgs {
     double *rhs;          // [3][n]
     float *nut;           // optional: type block of nu_t output (already offset)
     unsigned *err;        // device error word
+    const void *mlp;      // MLP closure weights (device MlpInfer) when closure == FEA_CLOSURE_MLP
 };
 
 // launchers (fea_kernels.cu); all return cudaGetLastError() of the launch
@@ -85,12 +86,13 @@ cudaError_t launch_assemble_bucket(const BucketDev &b, const FieldDev &f, const 
 cudaError_t launch_assemble_chunk(const BucketDev &b, const FieldDev &f, const AsmArgs &a, int threads,
                                   int compensated, cudaStream_t s);
 size_t chunk_smem_bytes(const BucketDev &b);
+size_t mlp_smem_bytes(int threads);   // shared memory a CTA needs for the fused MLP
 // shared memory of the chunk kernel that launch_assemble_chunk would launch
 size_t chunk_kernel_smem(const BucketDev &b, int compensated);
 constexpr size_t kChunkSmemLimit = 200 * 1024;
 // batched persistent launch over (category, chunk) items of many meshes
 cudaError_t launch_assemble_batch(const void *buckets, const void *fields, const void *args, const void *items,
-                                  int64_t n_items, unsigned long long *counter, size_t smem, int sms,
+                                  int64_t n_items, unsigned long long *counter, size_t smem, int sms, bool mlp,
                                   cudaStream_t s);
 size_t batch_item_bytes();
 cudaError_t launch_zero_batch(double *const *rhs_dev, const int64_t *len_dev, int n_meshes, cudaStream_t s);

@@ -17,6 +17,7 @@
 #include <algorithm>
 
 #include "fea_internal.h"
+#include "fea_mlp.cuh"
 
 namespace fea {
 
@@ -195,13 +196,36 @@ __device__ __forceinline__ JR adjugate(const JR J[3][3], JR A[3][3]) {
 // so the subgrid term is accumulated without the Delta^2 factor and added
 // once V_e is complete.  J, its adjugate and determinant are in JR (FP64
 // for flagged elements), the rest in R.
-template <int ET, typename R, bool J64>
+// MLP closure in an element kernel: weights and the warp's feature tile
+struct MlpUse {
+    const MlpInfer *w;
+    uint16_t *scratch;   // this warp's [32][kW1Pitch] bf16 tile
+};
+
+template <typename R>
+__device__ __forceinline__ float mlp_nut_of(const R G[3][3], R delta, const MlpUse &mu) {
+    float Gf[3][3], x[kMlpIn];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Gf[i][j] = float(G[i][j]);
+    mlp_features(Gf, float(delta), x);
+#pragma unroll
+    for (int k = 0; k < kMlpIn; ++k)
+        if (!isfinite(x[k])) x[k] = mu.w->mean[k];   // inactive lanes may carry junk
+    return mlp_warp_nut(*mu.w, x, mu.scratch);
+}
+
+template <int ET, typename R, typename JR>
+__device__ __forceinline__ JR prism_or_generic_jacobian(const JR X[][3], const PrismGeom<JR> &pg, int g, JR J[3][3]);
+
+template <int ET, typename R, bool J64, bool MLP = false>
 __device__ void element_residual(const Gathered<R, J64> &el, const FieldDev &f, const AsmArgs &args, R r[][3],
-                                 float *nut_out, bool &bad) {
+                                 float *nut_out, bool &bad, const MlpUse &mu = MlpUse{nullptr, nullptr}) {
     using JR = typename std::conditional<J64, double, R>::type;
     constexpr int nen = kNen[ET], ng = kNg[ET];
     const uint32_t mask = args.mask;
-    const bool want_q = args.closure == FEA_CLOSURE_VREMAN && ((mask & FEA_TERM_SGS) || nut_out);
+    const bool want_q = !MLP && args.closure == FEA_CLOSURE_VREMAN && ((mask & FEA_TERM_SGS) || nut_out);
     const R nu = (mask & FEA_TERM_VISC) ? R(f.nu) : R(0);
     const R cv = R(f.c_vreman);
     R rs[kMaxNen][3];
@@ -211,21 +235,22 @@ __device__ void element_residual(const Gathered<R, J64> &el, const FieldDev &f, 
         for (int i = 0; i < 3; ++i) r[a][i] = rs[a][i] = R(0);
     PrismGeom<JR> pg;
     if constexpr (ET == FEA_PEN06) prism_geom<JR>(el.X, pg);
+    // the MLP needs Delta at every Gauss point: element volume first
+    R mlp_delta = R(0);
+    if constexpr (MLP) {
+        JR V0 = JR(0);
+#pragma unroll 1
+        for (int g = 0; g < ng; ++g) {
+            JR J[3][3];
+            V0 += JR(c_ref.w[ET][g]) * prism_or_generic_jacobian<ET, R, JR>(el.X, pg, g, J);
+        }
+        mlp_delta = cbrt_r(R(V0));
+    }
     JR V = JR(0);
 #pragma unroll 1
     for (int g = 0; g < ng; ++g) {
         JR J[3][3];
-        if constexpr (ET == FEA_PEN06) {
-            const JR pr = JR(c_ref.xi[ET][g][0]), ps = JR(c_ref.xi[ET][g][1]), pz = JR(c_ref.xi[ET][g][2]);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                J[i][0] = pg.Ar[i] + pz * pg.Br[i];
-                J[i][1] = pg.As[i] + pz * pg.Bs[i];
-                J[i][2] = pg.C0[i] + pr * pg.Dr[i] + ps * pg.Ds[i];
-            }
-        } else {
-            jacobian_at<ET, R, JR>(el.X, g, J);
-        }
+        prism_or_generic_jacobian<ET, R, JR>(el.X, pg, g, J);
         JR A[3][3];
         const JR detj = adjugate(J, A);
         if (!(detj > JR(0))) bad = true;
@@ -261,8 +286,16 @@ __device__ void element_residual(const Gathered<R, J64> &el, const FieldDev &f, 
 #pragma unroll
             for (int i = 0; i < 3; ++i) G[i][j] = Gx[i][0] * Ji[0][j] + Gx[i][1] * Ji[1][j] + Gx[i][2] * Ji[2][j];
         }
-        const R q = want_q ? vreman(G, R(1), cv) : R(0);
-        if (nut_out) nut_out[g] = float(q);
+        R q = want_q ? vreman(G, R(1), cv) : R(0);
+        R visc_g = nu;
+        if constexpr (MLP) {
+            const R nt = R(mlp_nut_of(G, mlp_delta, mu));
+            if (nut_out) nut_out[g] = float(nt);
+            if (mask & FEA_TERM_SGS) visc_g += nt;
+            q = R(0);
+        } else {
+            if (nut_out) nut_out[g] = float(q);
+        }
         const R qs = (mask & FEA_TERM_SGS) ? q : R(0);
         const R trG = G[0][0] + G[1][1] + G[2][2];
         R f0[3];
@@ -287,27 +320,45 @@ __device__ void element_residual(const Gathered<R, J64> &el, const FieldDev &f, 
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 const R t = S[i][0] * d0 + S[i][1] * d1 + S[i][2] * d2;
-                r[a][i] -= Na * f0[i] + nu * t;
+                r[a][i] -= Na * f0[i] + visc_g * t;
                 rs[a][i] -= qs * t;
             }
         }
     }
-    const R delta = cbrt_r(R(V));
-    const R d2 = delta * delta;
+    if constexpr (!MLP) {
+        const R delta = cbrt_r(R(V));
+        const R d2 = delta * delta;
 #pragma unroll
-    for (int a = 0; a < nen; ++a)
+        for (int a = 0; a < nen; ++a)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) r[a][i] += d2 * rs[a][i];
-    if (nut_out)
-        for (int g = 0; g < ng; ++g) nut_out[g] = float(R(nut_out[g]) * d2);
+            for (int i = 0; i < 3; ++i) r[a][i] += d2 * rs[a][i];
+        if (nut_out)
+            for (int g = 0; g < ng; ++g) nut_out[g] = float(R(nut_out[g]) * d2);
+    }
+}
+
+template <int ET, typename R, typename JR>
+__device__ __forceinline__ JR prism_or_generic_jacobian(const JR X[][3], const PrismGeom<JR> &pg, int g, JR J[3][3]) {
+    if constexpr (ET == FEA_PEN06) {
+        const JR pr = JR(c_ref.xi[ET][g][0]), ps = JR(c_ref.xi[ET][g][1]), pz = JR(c_ref.xi[ET][g][2]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            J[i][0] = pg.Ar[i] + pz * pg.Br[i];
+            J[i][1] = pg.As[i] + pz * pg.Bs[i];
+            J[i][2] = pg.C0[i] + pr * pg.Dr[i] + ps * pg.Ds[i];
+        }
+        return det3(J);
+    } else {
+        return jacobian_at<ET, R, JR>(X, g, J);
+    }
 }
 
 // TET04: affine map, constant gradients; the 4-point rule is exact for the
 // degree-2 integrands, so the Gauss sums take their closed forms:
 //   sum_g W N_a N_b = V (1 + delta_ab) / 20,  sum_g W N_a = V / 4.
-template <typename R, bool J64>
+template <typename R, bool J64, bool MLP = false>
 __device__ void tet_residual(const Gathered<R, J64> &el, const FieldDev &f, const AsmArgs &args, R r[][3],
-                             float *nut_out, bool &bad) {
+                             float *nut_out, bool &bad, const MlpUse &mu = MlpUse{nullptr, nullptr}) {
     using JR = typename std::conditional<J64, double, R>::type;
     const uint32_t mask = args.mask;
     JR J[3][3];
@@ -342,7 +393,9 @@ __device__ void tet_residual(const Gathered<R, J64> &el, const FieldDev &f, cons
         }
     }
     R nut = R(0);
-    if (args.closure == FEA_CLOSURE_VREMAN && ((mask & FEA_TERM_SGS) || nut_out)) {
+    if constexpr (MLP) {
+        nut = R(mlp_nut_of(G, cbrt_r(V), mu));
+    } else if (args.closure == FEA_CLOSURE_VREMAN && ((mask & FEA_TERM_SGS) || nut_out)) {
         const R delta = cbrt_r(V);
         nut = vreman(G, delta * delta, R(f.c_vreman));
     }
@@ -382,11 +435,17 @@ __device__ void tet_residual(const Gathered<R, J64> &el, const FieldDev &f, cons
 // ---------------------------------------------------------------------------
 // ATOMIC scatter kernel: thread per element, FP64 atomic adds into rhs [3][n]
 
-template <int ET, typename R, bool J64>
+template <int ET, typename R, bool J64, bool MLP = false>
 __global__ void __launch_bounds__(256) k_assemble_atomic(BucketDev b, FieldDev f, AsmArgs args) {
     constexpr int nen = kNen[ET], ng = kNg[ET];
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= b.count) return;
+    const int64_t e_raw = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // with the MLP the whole warp evaluates the network together: idle lanes
+    // repeat the last element and store nothing
+    if (!MLP && e_raw >= b.count) return;
+    const bool active = e_raw < b.count;
+    const int64_t e = active ? e_raw : b.count - 1;
+    __shared__ __align__(16) uint16_t mlp_tiles[MLP ? 8 : 1][MLP ? 32 * kW1Pitch : 8];
+    MlpUse mu{static_cast<const MlpInfer *>(args.mlp), MLP ? mlp_tiles[threadIdx.x >> 5] : nullptr};
     int idx[nen];
 #pragma unroll
     for (int a = 0; a < nen; ++a) idx[a] = __ldg(&b.conn[(int64_t)a * b.count + e]);
@@ -394,11 +453,13 @@ __global__ void __launch_bounds__(256) k_assemble_atomic(BucketDev b, FieldDev f
     gather<ET, R, J64>(f, idx, el);
     R r[kMaxNen][3];
     bool bad = false;
-    float *nut = args.nut ? args.nut + (int64_t)__ldg(&b.orig[e]) * ng : nullptr;
+    float nut_tmp[ng];
+    float *nut = args.nut ? (active ? args.nut + (int64_t)__ldg(&b.orig[e]) * ng : nut_tmp) : nullptr;
     if constexpr (ET == FEA_TET04)
-        tet_residual<R, J64>(el, f, args, r, nut, bad);
+        tet_residual<R, J64, MLP>(el, f, args, r, nut, bad, mu);
     else
-        element_residual<ET, R, J64>(el, f, args, r, nut, bad);
+        element_residual<ET, R, J64, MLP>(el, f, args, r, nut, bad, mu);
+    if (!active) return;
     R chk = R(0);
 #pragma unroll
     for (int a = 0; a < nen; ++a) chk += r[a][0] + r[a][1] + r[a][2];
@@ -414,7 +475,14 @@ template <int ET>
 static cudaError_t launch_atomic_t(const BucketDev &b, const FieldDev &f, const AsmArgs &a, fea_prec prec,
                                    int threads, cudaStream_t s) {
     const unsigned blocks = (unsigned)((b.count + threads - 1) / threads);
-    if (prec == FEA_FP64)
+    if (a.closure == FEA_CLOSURE_MLP) {
+        if (prec == FEA_FP64)
+            k_assemble_atomic<ET, double, false, true><<<blocks, threads, 0, s>>>(b, f, a);
+        else if (b.fp64j)
+            k_assemble_atomic<ET, float, true, true><<<blocks, threads, 0, s>>>(b, f, a);
+        else
+            k_assemble_atomic<ET, float, false, true><<<blocks, threads, 0, s>>>(b, f, a);
+    } else if (prec == FEA_FP64)
         k_assemble_atomic<ET, double, false><<<blocks, threads, 0, s>>>(b, f, a);
     else if (b.fp64j)
         k_assemble_atomic<ET, float, true><<<blocks, threads, 0, s>>>(b, f, a);
@@ -451,6 +519,11 @@ cudaError_t launch_assemble_bucket(const BucketDev &b, const FieldDev &f, const 
 //      a plain store when no other chunk touches the node, else one FP64
 //      atomic add per component.
 
+__host__ __device__ __forceinline__ size_t chunk_smem_bytes_dev(const BucketDev &b) {
+    const int nen = b.etype == FEA_TET04 ? 4 : (b.etype == FEA_PYR05 ? 5 : (b.etype == FEA_PEN06 ? 6 : 8));
+    return sizeof(float4) * (2 * (size_t)b.max_chunk_nodes + (size_t)nen * b.chunk_elems);
+}
+
 __device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
     const float t = s + x;
     const float z = t - s;
@@ -458,9 +531,9 @@ __device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
     s = t;
 }
 
-template <int ET, bool J64, bool COMP>
+template <int ET, bool J64, bool COMP, bool MLP = false>
 __device__ __forceinline__ void chunk_body(const BucketDev &b, const FieldDev &f, const AsmArgs &args, int64_t k,
-                                           float4 *smem4) {
+                                           float4 *smem4, const MlpUse &mu = MlpUse{nullptr, nullptr}) {
     constexpr int nen = kNen[ET], ng = kNg[ET];
     const int C = b.chunk_elems;
     const int64_t e0 = k * (int64_t)C;
@@ -480,7 +553,13 @@ __device__ __forceinline__ void chunk_body(const BucketDev &b, const FieldDev &f
     __syncthreads();
     bool bad = false;
     float chk = 0.0f;
-    for (int el = threadIdx.x; el < ne; el += blockDim.x) {
+    // warp-uniform trip count: with the MLP every lane of a warp joins the
+    // network evaluation; lanes past the chunk's end repeat its last element
+    for (int base = 0; base < ne; base += blockDim.x) {
+        const int el_raw = base + threadIdx.x;
+        if (!MLP && el_raw >= ne) break;
+        const bool active = el_raw < ne;
+        const int el = active ? el_raw : ne - 1;
         const int64_t e = e0 + el;
         Gathered<float, J64> g;
         int loc[nen];
@@ -515,11 +594,13 @@ __device__ __forceinline__ void chunk_body(const BucketDev &b, const FieldDev &f
             }
         }
         float r[kMaxNen][3];
-        float *nut = args.nut ? args.nut + (int64_t)__ldg(&b.orig[e]) * ng : nullptr;
+        float nut_tmp[ng];
+        float *nut = args.nut ? (active ? args.nut + (int64_t)__ldg(&b.orig[e]) * ng : nut_tmp) : nullptr;
         if constexpr (ET == FEA_TET04)
-            tet_residual<float, J64>(g, f, args, r, nut, bad);
+            tet_residual<float, J64, MLP>(g, f, args, r, nut, bad, mu);
         else
-            element_residual<ET, float, J64>(g, f, args, r, nut, bad);
+            element_residual<ET, float, J64, MLP>(g, f, args, r, nut, bad, mu);
+        if (!active) continue;
 #pragma unroll
         for (int a = 0; a < nen; ++a) {
             sR[lbuf[np + a]] = make_float4(r[a][0], r[a][1], r[a][2], 0.0f);
@@ -566,10 +647,19 @@ __device__ __forceinline__ void chunk_body(const BucketDev &b, const FieldDev &f
     }
 }
 
-template <int ET, bool J64, bool COMP>
+template <int ET, bool J64, bool COMP, bool MLP = false>
 __global__ void __launch_bounds__(256) k_assemble_chunk(BucketDev b, FieldDev f, AsmArgs args) {
     extern __shared__ float4 smem4[];
-    chunk_body<ET, J64, COMP>(b, f, args, blockIdx.x, smem4);
+    MlpUse mu{nullptr, nullptr};
+    if constexpr (MLP) {
+        // weights and per-warp feature tiles after the chunk's buffers
+        unsigned char *tail = reinterpret_cast<unsigned char *>(smem4) + chunk_smem_bytes_dev(b);
+        MlpInfer *w = reinterpret_cast<MlpInfer *>(tail);
+        mlp_copy_infer(static_cast<const MlpInfer *>(args.mlp), w);
+        mu.w = w;
+        mu.scratch = reinterpret_cast<uint16_t *>(tail + sizeof(MlpInfer)) + (threadIdx.x >> 5) * 32 * kW1Pitch;
+    }
+    chunk_body<ET, J64, COMP, MLP>(b, f, args, blockIdx.x, smem4, mu);
 }
 
 // ---------------------------------------------------------------------------
@@ -583,13 +673,22 @@ struct BatchItem {
     int32_t chunk;    // chunk index within the bucket
 };
 
+template <bool MLP>
 __global__ void __launch_bounds__(256, 2) k_assemble_batch(const BucketDev *__restrict__ bk,
                                                         const FieldDev *__restrict__ fd,
                                                         const AsmArgs *__restrict__ ag,
                                                         const BatchItem *__restrict__ items, int64_t n_items,
-                                                        unsigned long long *counter) {
+                                                        unsigned long long *counter, size_t chunk_bytes) {
     extern __shared__ float4 smem4[];
     __shared__ long long item_s;
+    MlpUse mu{nullptr, nullptr};
+    if constexpr (MLP) {
+        unsigned char *tail = reinterpret_cast<unsigned char *>(smem4) + chunk_bytes;
+        MlpInfer *w = reinterpret_cast<MlpInfer *>(tail);
+        mlp_copy_infer(static_cast<const MlpInfer *>(ag[0].mlp), w);
+        mu.w = w;
+        mu.scratch = reinterpret_cast<uint16_t *>(tail + sizeof(MlpInfer)) + (threadIdx.x >> 5) * 32 * kW1Pitch;
+    }
     for (;;) {
         if (threadIdx.x == 0) item_s = (long long)atomicAdd(counter, 1ull);
         __syncthreads();
@@ -601,11 +700,11 @@ __global__ void __launch_bounds__(256, 2) k_assemble_batch(const BucketDev *__re
         const FieldDev f = fd[it.bucket];
         const AsmArgs a = ag[it.bucket];
         switch (b.etype * 2 + b.fp64j) {
-            case 0: chunk_body<FEA_TET04, false, false>(b, f, a, it.chunk, smem4); break;
-            case 2: chunk_body<FEA_PYR05, false, false>(b, f, a, it.chunk, smem4); break;
-            case 4: chunk_body<FEA_PEN06, false, false>(b, f, a, it.chunk, smem4); break;
-            case 5: chunk_body<FEA_PEN06, true, false>(b, f, a, it.chunk, smem4); break;
-            case 6: chunk_body<FEA_HEX08, false, false>(b, f, a, it.chunk, smem4); break;
+            case 0: chunk_body<FEA_TET04, false, false, MLP>(b, f, a, it.chunk, smem4, mu); break;
+            case 2: chunk_body<FEA_PYR05, false, false, MLP>(b, f, a, it.chunk, smem4, mu); break;
+            case 4: chunk_body<FEA_PEN06, false, false, MLP>(b, f, a, it.chunk, smem4, mu); break;
+            case 5: chunk_body<FEA_PEN06, true, false, MLP>(b, f, a, it.chunk, smem4, mu); break;
+            case 6: chunk_body<FEA_HEX08, false, false, MLP>(b, f, a, it.chunk, smem4, mu); break;
             default: break;   // FP64-Jacobian TET04/PYR05/HEX08: not batched (host falls back)
         }
         __syncthreads();   // shared memory is reused by the next item
@@ -613,21 +712,24 @@ __global__ void __launch_bounds__(256, 2) k_assemble_batch(const BucketDev *__re
 }
 
 cudaError_t launch_assemble_batch(const void *buckets, const void *fields, const void *args, const void *items,
-                                  int64_t n_items, unsigned long long *counter, size_t smem, int sms,
+                                  int64_t n_items, unsigned long long *counter, size_t smem, int sms, bool mlp,
                                   cudaStream_t s) {
     if (n_items == 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_assemble_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t chunk_bytes = smem;
+    if (mlp) smem += mlp_smem_bytes(256);
+    auto kern = mlp ? k_assemble_batch<true> : k_assemble_batch<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_assemble_batch, 256, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(n_items, (int64_t)per_sm * sms);
-    k_assemble_batch<<<(unsigned)grid, 256, smem, s>>>(
-        static_cast<const BucketDev *>(buckets), static_cast<const FieldDev *>(fields),
-        static_cast<const AsmArgs *>(args), static_cast<const BatchItem *>(items), n_items, counter);
+    kern<<<(unsigned)grid, 256, smem, s>>>(static_cast<const BucketDev *>(buckets),
+                                           static_cast<const FieldDev *>(fields), static_cast<const AsmArgs *>(args),
+                                           static_cast<const BatchItem *>(items), n_items, counter, chunk_bytes);
     return cudaGetLastError();
 }
 
@@ -654,15 +756,16 @@ size_t chunk_kernel_smem(const BucketDev &b, int compensated) {
     return chunk_smem_bytes(b);
 }
 
-size_t chunk_smem_bytes(const BucketDev &b) {
-    return sizeof(float4) * (2 * (size_t)b.max_chunk_nodes + (size_t)kNen[b.etype] * b.chunk_elems);
-}
+size_t chunk_smem_bytes(const BucketDev &b) { return chunk_smem_bytes_dev(b); }
+
+size_t mlp_smem_bytes(int threads) { return sizeof(MlpInfer) + (size_t)(threads / 32) * 32 * kW1Pitch * 2; }
 
 template <int ET, bool J64, bool COMP>
 static cudaError_t launch_chunk_v(const BucketDev &b, const FieldDev &f, const AsmArgs &a, int threads,
                                   cudaStream_t s) {
-    const size_t smem = chunk_smem_bytes(b);
-    auto kern = k_assemble_chunk<ET, J64, COMP>;
+    const bool mlp = a.closure == FEA_CLOSURE_MLP;
+    const size_t smem = chunk_smem_bytes(b) + (mlp ? mlp_smem_bytes(threads) : 0);
+    auto kern = mlp ? k_assemble_chunk<ET, J64, COMP, true> : k_assemble_chunk<ET, J64, COMP, false>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -685,7 +788,8 @@ cudaError_t launch_assemble_chunk(const BucketDev &b, const FieldDev &f, const A
                                   int compensated, cudaStream_t s) {
     if (b.count == 0) return cudaSuccess;
     if (!b.lconn || b.n_chunks <= 0) return cudaErrorInvalidValue;
-    if (b.etype == FEA_TET04 && !b.fp64j && !compensated && tet_pipe_smem_bytes(b) <= kChunkSmemLimit)
+    if (b.etype == FEA_TET04 && !b.fp64j && !compensated && a.closure != FEA_CLOSURE_MLP &&
+        tet_pipe_smem_bytes(b) <= kChunkSmemLimit)
         return launch_tet_pipe(b, f, a, threads, 0, s);
     if (threads > 256) threads = 256;
     switch (b.etype) {

@@ -134,3 +134,68 @@ def test_training_reduces_loss(ctx):
     torch.cuda.synchronize()
     ctx.sync_status()
     assert loss.item() < 0.1 * first, (first, loss.item())
+
+
+# ---------------------------------------------------------------------------
+# the MLP closure fused into the assembly kernels
+
+from paper_2005_05899_b300 import meshgen as mg  # noqa: E402
+
+
+def closure_model(rng, mesh, field):
+    """An MLP whose nu_t is of the size of Vreman's on this field."""
+    theta = (0.2 * rng.standard_normal(fea.MLP_NPARAM)).astype(np.float32)
+    om = O.OracleMesh.of(mesh)
+    _, nut = O.assemble_rhs(om, field.u, field.p, field.nu, field.c_vreman, "vreman", want_nut=True)
+    scale = float(np.mean(np.concatenate([v.ravel() for v in nut.values()]))) + 1e-8
+    x = sample_features(rng, 2000)
+    mean = x.mean(axis=0).astype(np.float32)
+    std = (x.std(axis=0) + 1e-3).astype(np.float32)
+    return theta, mean, std, scale
+
+
+@pytest.mark.parametrize("prec,scatter", [("mixed", "chunk"), ("mixed", "atomic"), ("fp64", "atomic")])
+def test_assembly_with_mlp_closure_matches_oracle(ctx, prec, scatter):
+    rng = np.random.default_rng(5)
+    m = mg.channel_mesh(nx=10, ny=12, nz=8, seed=21, n_layers=2, split_frac=0.3)
+    f = mg.channel_field(m, seed=5, nu=1e-3)
+    theta, mean, std, scale = closure_model(rng, m, f)
+    ctx.mlp_load(theta, mean, std, scale)
+    dm = ctx.upload_mesh(m)
+    dm.upload_field(f.u, f.p, f.nu, f.c_vreman)
+    out = torch.empty((3, dm.n_nodes), dtype=torch.float64, device="cuda")
+    nut = torch.empty(dm.n_gauss_total, dtype=torch.float32, device="cuda")
+    dm.assemble(out, prec=prec, closure="mlp", scatter=scatter, nut_out=nut)
+    ctx.sync_status()
+    got = out.cpu().numpy().T
+    mlp = O.MLPParams(gpu_rounded_theta(theta), mean.astype(np.float64), std.astype(np.float64), scale)
+    om = O.OracleMesh.of(m)
+    ref, nref = O.assemble_rhs(om, f.u, f.p, f.nu, f.c_vreman, "mlp", mlp=mlp, want_nut=True)
+    ref_sgs = O.assemble_rhs(om, f.u, f.p, f.nu, f.c_vreman, "mlp", mask=O.TERM_SGS, mlp=mlp)
+    nr = np.concatenate([nref[t].ravel() for t in range(4) if t in nref])
+    ng = nut.cpu().numpy()
+    assert np.all(np.abs(ng - nr) <= 3e-2 * np.abs(nr) + 2e-3 * np.abs(nr).max())
+    err = np.linalg.norm(got - ref)
+    assert err <= 3e-2 * np.linalg.norm(ref_sgs) + 2e-5 * np.linalg.norm(ref), (err, np.linalg.norm(ref_sgs))
+
+
+def test_batched_assembly_with_mlp_closure(ctx):
+    rng = np.random.default_rng(6)
+    batch = mg.batch_meshes(count=4, seed=3, e_min=2e3, e_max=2e4)
+    theta, mean, std, scale = closure_model(rng, *batch[0])
+    ctx.mlp_load(theta, mean, std, scale)
+    dms, outs = [], []
+    for m, f in batch:
+        dm = ctx.upload_mesh(m)
+        dm.upload_field(f.u, f.p, f.nu, f.c_vreman)
+        dms.append(dm)
+        outs.append(torch.empty((3, dm.n_nodes), dtype=torch.float64, device="cuda"))
+    ctx.assemble_batched(dms, outs, prec="mixed", closure="mlp")
+    ctx.sync_status()
+    single = torch.empty_like(outs[0])
+    for dm, o in zip(dms, outs):
+        single = torch.empty_like(o)
+        dm.assemble(single, prec="mixed", closure="mlp", scatter="chunk")
+        ctx.sync_status()
+        a, b = o.cpu().numpy(), single.cpu().numpy()
+        assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
