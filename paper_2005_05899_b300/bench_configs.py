@@ -1,7 +1,9 @@
-"""Secondary measurements: the channel mesh (mixed types) and the batch of
-64 uneven meshes (one persistent launch vs one launch sequence per mesh).
+"""Secondary measurements: the channel mesh (mixed types), the batch of
+64 uneven meshes (one persistent launch vs one launch sequence per mesh) and
+the learned closure (trained on filtered fine Taylor-Green runs, then fused
+into the assembly of an 8M-element mixed channel mesh against Vreman).
 
-    python -m paper_2005_05899_b300.bench_configs [--channel] [--batch] [--reps 20]
+    python -m paper_2005_05899_b300.bench_configs [--channel] [--batch] [--closure] [--reps 20]
 
 Prints one JSON line per measurement (CUDA-event times on the current stream,
 after warm-up; inputs are larger than L2 for the channel and the batch).
@@ -87,18 +89,93 @@ def batch(reps: int, count: int = 64):
                       "elements": E, "generate_s": gen_s, **res}), flush=True)
 
 
+def _time_assemble(dm, out, reps: int, **kw) -> float:
+    import torch
+    for _ in range(3):
+        dm.assemble(out, **kw)
+    e0, e1 = _events()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        dm.assemble(out, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def closure(reps: int, n_f: int = 256, steps: int = 8000, dims=(269, 134, 135)):
+    """Learned closure: GPU training on box-filtered n_f^3 Taylor-Green runs,
+    a-priori errors on a held-out time, then the network fused at every Gauss
+    point of a mixed channel mesh against the Vreman path: time per assembly,
+    and relative L2 differences of nu_t and of the RHS (whole and subgrid part
+    alone), plus the mixed-precision error of the learned path against its own
+    FP64 assembly."""
+    import numpy as np
+    import torch
+    from . import closure_data as cd
+    from . import fea
+    from . import meshgen as mg
+    ctx = fea.Context(0)
+    t = time.time()
+    res = cd.run(n_f=n_f, ratios=(4, 8), t_train=(3.0, 4.0, 5.0, 7.0, 8.0), t_test=(6.0,), steps=steps,
+                 log=None, ctx=ctx)
+    res.pop("model")
+    train_total_s = time.time() - t
+    m = mg.channel_mesh(*dims)
+    f = mg.channel_field(m, nu=1.0 / 5600.0)
+    dm = ctx.upload_mesh(m)
+    dm.upload_field(f.u, f.p, f.nu, f.c_vreman)
+    E = m.n_elem_total
+    plans = {}
+    ms = {}
+    N = dm.n_nodes
+    rhs = {c: torch.empty((3, N), dtype=torch.float64, device="cuda") for c in ("vreman", "mlp")}
+    sgs = {c: torch.empty((3, N), dtype=torch.float64, device="cuda") for c in ("vreman", "mlp")}
+    nut = {c: torch.empty(dm.n_gauss_total, dtype=torch.float32, device="cuda") for c in ("vreman", "mlp")}
+    for c in ("vreman", "mlp"):
+        plans[c] = dm.autotune(prec="mixed", closure=c).as_dict()
+        ms[c] = _time_assemble(dm, rhs[c], reps, prec="mixed", closure=c)
+        dm.assemble(rhs[c], prec="mixed", closure=c, nut_out=nut[c])
+        dm.assemble(sgs[c], prec="mixed", closure=c, mask=fea.TERM_SGS)
+    ref64 = torch.empty((3, N), dtype=torch.float64, device="cuda")
+    dm.assemble(ref64, prec="fp64", closure="mlp", scatter="atomic")
+    ctx.sync_status()
+
+    def rel(a, b):
+        return float(torch.linalg.norm((a - b).double()) / torch.linalg.norm(b.double()))
+
+    nv, nm = nut["vreman"], nut["mlp"]
+    out = {"workload": f"learned closure: trained on box-filtered {n_f}^3 Taylor-Green runs, fused into "
+                       f"channel {dims[0]}x{dims[1]}x{dims[2]} mixed ({E:,} elements)",
+           "counts": m.counts(), "elements": E, "gauss_points": int(dm.n_gauss_total),
+           "training": res, "train_total_s": train_total_s,
+           "assemble_ms": ms, "melem_s": {c: E / v / 1e3 for c, v in ms.items()},
+           "mlp_over_vreman_time": ms["mlp"] / ms["vreman"], "plans": plans,
+           "nut_rel_l2_mlp_vs_vreman": rel(nm, nv),
+           "nut_mean": {"vreman": float(nv.double().mean()), "mlp": float(nm.double().mean())},
+           "rhs_rel_l2_mlp_vs_vreman": rel(rhs["mlp"], rhs["vreman"]),
+           "sgs_rel_l2_mlp_vs_vreman": rel(sgs["mlp"], sgs["vreman"]),
+           "mlp_mixed_vs_fp64_rel_l2": rel(rhs["mlp"], ref64)}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--channel", action="store_true")
     ap.add_argument("--batch", action="store_true")
+    ap.add_argument("--closure", action="store_true")
+    ap.add_argument("--n-f", type=int, default=256, help="fine Taylor-Green grid of the closure's training runs")
     ap.add_argument("--reps", type=int, default=20)
     a = ap.parse_args(argv)
-    if not (a.channel or a.batch):
+    if not (a.channel or a.batch or a.closure):
         a.channel = a.batch = True
     if a.channel:
         channel(a.reps)
     if a.batch:
         batch(a.reps)
+    if a.closure:
+        closure(a.reps, n_f=a.n_f)
     return 0
 
 

@@ -297,10 +297,15 @@ def apriori_errors(ctx: fea.Context, cs: CoarseSet, nu: float = 1.0 / 1600.0, c_
 
 
 def run(n_f: int = 96, ratios=(4, 8), t_train=(3.0, 4.0, 5.0, 7.0, 8.0), t_test=(6.0,), steps: int = 2000,
-        save: str = "", log=print) -> Dict:
-    """Fine run, filtering, GPU training and the a-priori comparison on held-out times."""
+        save: str = "", log=print, ctx: fea.Context = None) -> Dict:
+    """Fine run, filtering, GPU training and the a-priori comparison on held-out times.
+
+    Returns a JSON-able dict plus the key "model" (the TrainedClosure, left
+    loaded in the context when one is passed in)."""
     import time
-    ctx = fea.Context(0)
+    own = ctx is None
+    if own:
+        ctx = fea.Context(0)
     t0 = time.time()
     data = generate(ctx, n_f=n_f, ratios=ratios, t_snap=sorted(set(t_train) | set(t_test)), log=log)
     t_gen = time.time() - t0
@@ -318,7 +323,9 @@ def run(n_f: int = 96, ratios=(4, 8), t_train=(3.0, 4.0, 5.0, 7.0, 8.0), t_test=
         e = apriori_errors(ctx, c)
         e["n_c"] = c.n_c
         res["test"].append(e)
-    ctx.close()
+    res["model"] = model
+    if own:
+        ctx.close()
     return res
 
 
@@ -330,4 +337,6 @@ if __name__ == "__main__":
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--save", default="")
     a = ap.parse_args()
-    print(json.dumps(run(n_f=a.n_f, steps=a.steps, save=a.save)), flush=True)
+    r = run(n_f=a.n_f, steps=a.steps, save=a.save)
+    r.pop("model")
+    print(json.dumps(r), flush=True)

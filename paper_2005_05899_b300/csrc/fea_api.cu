@@ -478,7 +478,7 @@ fea_status assemble_into(fea_ctx *ctx, Mesh &m, fea_prec prec, fea_closure closu
             a.rhs = rhs;
             a.nut = nut ? nut + type_nut_offset(m, b.etype) : nullptr;
             a.err = ctx->d_err;
-            a.mlp = closure == FEA_CLOSURE_MLP ? ctx->mlp_w.p : nullptr;
+            a.mlp = closure == FEA_CLOSURE_MLP ? mlp_fast_ptr(ctx->mlp_w.p) : nullptr;
             cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
             if (ctx->profiling) CK(cudaStreamIsCapturing(s, &cap));
             ProfRec pr{b.etype, b.fp64j, nullptr, nullptr};
@@ -596,7 +596,7 @@ fea_status stage_with_scratch(fea_ctx *ctx, int32_t mesh, int32_t stage, double 
             a.rhs = rhs;
             a.nut = nullptr;
             a.err = ctx->d_err;
-            a.mlp = closure == FEA_CLOSURE_MLP ? ctx->mlp_w.p : nullptr;
+            a.mlp = closure == FEA_CLOSURE_MLP ? mlp_fast_ptr(ctx->mlp_w.p) : nullptr;
             if (prec == FEA_MIXED && scatter == FEA_SCATTER_CHUNK && b.lconn.p)
                 CK(launch_assemble_chunk(b.dev(), f, a, m->plan.threads_per_block, m->plan.chunk_acc, ls));
             else
@@ -948,7 +948,7 @@ fea_status fea_assemble_rhs_batched(fea_ctx *ctx, const int32_t *meshes, int32_t
             a.rhs = rhs_out[k];
             a.nut = nullptr;
             a.err = ctx->d_err;
-            a.mlp = closure == FEA_CLOSURE_MLP ? ctx->mlp_w.p : nullptr;
+            a.mlp = closure == FEA_CLOSURE_MLP ? mlp_fast_ptr(ctx->mlp_w.p) : nullptr;
             ag.push_back(a);
             smem = std::max(smem, chunk_smem_bytes(bk.back()));
         }
@@ -965,6 +965,8 @@ fea_status fea_assemble_rhs_batched(fea_ctx *ctx, const int32_t *meshes, int32_t
         }
     const int64_t n_items = (int64_t)items.size() / 2;
     if (smem > kChunkSmemLimit) return fail(ctx, FEA_EINVAL, "batched chunk needs more than 200 KB of shared memory");
+    if (closure == FEA_CLOSURE_MLP && smem + mlp_smem_bytes(256, kMaxNg) > kMaxBlockSmem)
+        return fail(ctx, FEA_EINVAL, "batched chunk with the MLP closure needs more than 227 KB of shared memory");
     auto grow = [&](DevBuf<unsigned char> &d, size_t bytes) -> cudaError_t {
         return d.n >= bytes ? cudaSuccess : d.alloc(bytes);
     };
@@ -1128,7 +1130,11 @@ fea_status fea_autotune(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure c
             if ((st = ensure_chunks(ctx, *m, cand.chunk_elems))) return st;
             bool fits = true;
             for (auto &b : m->buckets)
-                if (b->count && chunk_kernel_smem(b->dev(), cand.chunk_acc) > kChunkSmemLimit) fits = false;
+                if (b->count && (chunk_kernel_smem(b->dev(), cand.chunk_acc) > kChunkSmemLimit ||
+                                 (closure == FEA_CLOSURE_MLP &&
+                                  chunk_launch_smem(b->dev(), cand.threads_per_block, cand.chunk_acc, true) >
+                                      kMaxBlockSmem)))
+                    fits = false;
             if (!fits) continue;
         }
         m->plan = cand;

@@ -76,7 +76,7 @@ struct AsmArgs {
     double *rhs;          // [3][n]
     float *nut;           // optional: type block of nu_t output (already offset)
     unsigned *err;        // device error word
-    const void *mlp;      // MLP closure weights (device MlpInfer) when closure == FEA_CLOSURE_MLP
+    const void *mlp;      // MLP closure weights (device MlpFast) when closure == FEA_CLOSURE_MLP
 };
 
 // launchers (fea_kernels.cu); all return cudaGetLastError() of the launch
@@ -86,7 +86,11 @@ cudaError_t launch_assemble_bucket(const BucketDev &b, const FieldDev &f, const 
 cudaError_t launch_assemble_chunk(const BucketDev &b, const FieldDev &f, const AsmArgs &a, int threads,
                                   int compensated, cudaStream_t s);
 size_t chunk_smem_bytes(const BucketDev &b);
-size_t mlp_smem_bytes(int threads);   // shared memory a CTA needs for the fused MLP
+// shared memory a CTA needs for the fused MLP: weights plus per-warp scratch
+size_t mlp_smem_bytes(int threads, int rows_per_elem);
+// shared memory of a chunk launch with this many threads, with or without the MLP
+size_t chunk_launch_smem(const BucketDev &b, int threads, int compensated, bool mlp);
+constexpr size_t kMaxBlockSmem = 227 * 1024;   // opt-in dynamic shared memory per CTA
 // shared memory of the chunk kernel that launch_assemble_chunk would launch
 size_t chunk_kernel_smem(const BucketDev &b, int compensated);
 constexpr size_t kChunkSmemLimit = 200 * 1024;
@@ -113,6 +117,7 @@ cudaError_t launch_recip(const double *m, double *minv, int64_t n, cudaStream_t 
 
 // MLP closure (fea_mlp.cu)
 size_t mlp_weights_bytes();
+const void *mlp_fast_ptr(const void *w);   // inference layout inside the weights block
 int mlp_param_count();
 cudaError_t launch_mlp_pack(const float *theta, const float *mean, const float *stdv, float out_scale, void *w,
                             cudaStream_t s);

@@ -196,24 +196,17 @@ __device__ __forceinline__ JR adjugate(const JR J[3][3], JR A[3][3]) {
 // so the subgrid term is accumulated without the Delta^2 factor and added
 // once V_e is complete.  J, its adjugate and determinant are in JR (FP64
 // for flagged elements), the rest in R.
-// MLP closure in an element kernel: weights and the warp's feature tile
+// MLP closure in an element kernel: the weights in shared memory and this
+// warp's scratch (mlp_warp_scratch_bytes of the element's row count).
 struct MlpUse {
-    const MlpInfer *w;
-    uint16_t *scratch;   // this warp's [32][kW1Pitch] bf16 tile
+    const MlpFast *w;
+    unsigned char *scratch;
 };
 
-template <typename R>
-__device__ __forceinline__ float mlp_nut_of(const R G[3][3], R delta, const MlpUse &mu) {
-    float Gf[3][3], x[kMlpIn];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) Gf[i][j] = float(G[i][j]);
-    mlp_features(Gf, float(delta), x);
-#pragma unroll
-    for (int k = 0; k < kMlpIn; ++k)
-        if (!isfinite(x[k])) x[k] = mu.w->mean[k];   // inactive lanes may carry junk
-    return mlp_warp_nut(*mu.w, x, mu.scratch);
+// rows of the network per element: one per Gauss point, one for TET04
+// (constant gradient, so every Gauss point has the same nu_t)
+__host__ __device__ constexpr int mlp_rows_per_elem(int et) {
+    return et == FEA_TET04 ? 1 : (et == FEA_PYR05 ? 8 : (et == FEA_PEN06 ? 6 : 8));
 }
 
 template <int ET, typename R, typename JR>
@@ -235,17 +228,14 @@ __device__ void element_residual(const Gathered<R, J64> &el, const FieldDev &f, 
         for (int i = 0; i < 3; ++i) r[a][i] = rs[a][i] = R(0);
     PrismGeom<JR> pg;
     if constexpr (ET == FEA_PEN06) prism_geom<JR>(el.X, pg);
-    // the MLP needs Delta at every Gauss point: element volume first
-    R mlp_delta = R(0);
-    if constexpr (MLP) {
-        JR V0 = JR(0);
-#pragma unroll 1
-        for (int g = 0; g < ng; ++g) {
-            JR J[3][3];
-            V0 += JR(c_ref.w[ET][g]) * prism_or_generic_jacobian<ET, R, JR>(el.X, pg, g, J);
-        }
-        mlp_delta = cbrt_r(R(V0));
-    }
+    // MLP: phase 1 (this loop) stores each Gauss point's features and its
+    // matrix S in the warp's scratch and assembles everything but the
+    // subgrid term; phase 2 runs the network over the warp's 32 x ng rows;
+    // phase 3 adds the subgrid term with the per-point nu_t.
+    const int lane = threadIdx.x & 31;
+    uint32_t *featw = reinterpret_cast<uint32_t *>(mu.scratch);
+    float *Stile = reinterpret_cast<float *>(mu.scratch + mlp_feat_bytes(ng));
+    float *ntile = Stile + ng * 9 * 32;
     JR V = JR(0);
 #pragma unroll 1
     for (int g = 0; g < ng; ++g) {
@@ -287,12 +277,20 @@ __device__ void element_residual(const Gathered<R, J64> &el, const FieldDev &f, 
             for (int i = 0; i < 3; ++i) G[i][j] = Gx[i][0] * Ji[0][j] + Gx[i][1] * Ji[1][j] + Gx[i][2] * Ji[2][j];
         }
         R q = want_q ? vreman(G, R(1), cv) : R(0);
-        R visc_g = nu;
+        const R visc_g = nu;
         if constexpr (MLP) {
-            const R nt = R(mlp_nut_of(G, mlp_delta, mu));
-            if (nut_out) nut_out[g] = float(nt);
-            if (mask & FEA_TERM_SGS) visc_g += nt;
-            q = R(0);
+            float Gf[3][3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) Gf[i][j] = float(G[i][j]);
+            uint32_t wds[3];
+            mlp_gp_words(Gf, *mu.w, wds);
+            uint32_t *row = featw + (g * 32 + lane) * 4;
+            row[0] = wds[0];
+            row[1] = wds[1];
+            row[2] = wds[2];
+            row[3] = 0u;
         } else {
             if (nut_out) nut_out[g] = float(q);
         }
@@ -313,6 +311,12 @@ __device__ void element_residual(const Gathered<R, J64> &el, const FieldDev &f, 
 #pragma unroll
             for (int k = 0; k < 3; ++k) S[i][k] = R(2) * W * (e0 * Ji[k][0] + e1 * Ji[k][1] + e2 * Ji[k][2]);
         }
+        if constexpr (MLP) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) Stile[(g * 9 + 3 * i + k) * 32 + lane] = float(S[i][k]);
+        }
 #pragma unroll
         for (int a = 0; a < nen; ++a) {
             const R Na = R(c_ref.N[ET][g][a]);
@@ -321,11 +325,40 @@ __device__ void element_residual(const Gathered<R, J64> &el, const FieldDev &f, 
             for (int i = 0; i < 3; ++i) {
                 const R t = S[i][0] * d0 + S[i][1] * d1 + S[i][2] * d2;
                 r[a][i] -= Na * f0[i] + visc_g * t;
-                rs[a][i] -= qs * t;
+                if constexpr (!MLP) rs[a][i] -= qs * t;
             }
         }
     }
-    if constexpr (!MLP) {
+    if constexpr (MLP) {
+        // Delta = V^(1/3) completes every row (column 5)
+        const uint16_t db = mlp_delta_bits(float(cbrt_r(R(V))), *mu.w);
+#pragma unroll 1
+        for (int g = 0; g < ng; ++g) reinterpret_cast<uint16_t *>(featw + (g * 32 + lane) * 4)[5] = db;
+        __syncwarp();
+#pragma unroll 1
+        for (int g = 0; g < ng; ++g) mlp_rows32(*mu.w, reinterpret_cast<const uint16_t *>(featw), ntile, g);
+        __syncwarp();
+#pragma unroll 1
+        for (int g = 0; g < ng; ++g) {
+            const R nt = R(ntile[g * 32 + lane]);
+            if (nut_out) nut_out[g] = float(nt);
+            if (mask & FEA_TERM_SGS) {
+                R Sg[3][3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) Sg[i][k] = R(Stile[(g * 9 + 3 * i + k) * 32 + lane]);
+#pragma unroll
+                for (int a = 0; a < nen; ++a) {
+                    const R d0 = R(c_ref.dN[ET][g][a][0]), d1 = R(c_ref.dN[ET][g][a][1]),
+                            d2 = R(c_ref.dN[ET][g][a][2]);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) r[a][i] -= nt * (Sg[i][0] * d0 + Sg[i][1] * d1 + Sg[i][2] * d2);
+                }
+            }
+        }
+        __syncwarp();   // the scratch is rewritten for the warp's next elements
+    } else {
         const R delta = cbrt_r(R(V));
         const R d2 = delta * delta;
 #pragma unroll
@@ -394,7 +427,26 @@ __device__ void tet_residual(const Gathered<R, J64> &el, const FieldDev &f, cons
     }
     R nut = R(0);
     if constexpr (MLP) {
-        nut = R(mlp_nut_of(G, cbrt_r(V), mu));
+        // one row per element (lane) through the warp's 32-row tile
+        const int lane = threadIdx.x & 31;
+        float Gf[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Gf[i][j] = float(G[i][j]);
+        uint32_t *row = reinterpret_cast<uint32_t *>(mu.scratch) + lane * 4;
+        float *ntile = reinterpret_cast<float *>(mu.scratch + mlp_feat_bytes(1) + mlp_s_bytes(1));
+        uint32_t wds[3];
+        mlp_gp_words(Gf, *mu.w, wds);
+        row[0] = wds[0];
+        row[1] = wds[1];
+        row[2] = (wds[2] & 0xffffu) | ((uint32_t)mlp_delta_bits(float(cbrt_r(V)), *mu.w) << 16);
+        row[3] = 0u;
+        __syncwarp();
+        mlp_rows32(*mu.w, reinterpret_cast<const uint16_t *>(mu.scratch), ntile, 0);
+        __syncwarp();
+        nut = R(ntile[lane]);
+        __syncwarp();
     } else if (args.closure == FEA_CLOSURE_VREMAN && ((mask & FEA_TERM_SGS) || nut_out)) {
         const R delta = cbrt_r(V);
         nut = vreman(G, delta * delta, R(f.c_vreman));
@@ -444,8 +496,16 @@ __global__ void __launch_bounds__(256) k_assemble_atomic(BucketDev b, FieldDev f
     if (!MLP && e_raw >= b.count) return;
     const bool active = e_raw < b.count;
     const int64_t e = active ? e_raw : b.count - 1;
-    __shared__ __align__(16) uint16_t mlp_tiles[MLP ? 8 : 1][MLP ? 32 * kW1Pitch : 8];
-    MlpUse mu{static_cast<const MlpInfer *>(args.mlp), MLP ? mlp_tiles[threadIdx.x >> 5] : nullptr};
+    MlpUse mu{nullptr, nullptr};
+    if constexpr (MLP) {
+        // weights, then one scratch block per warp (no thread has returned)
+        extern __shared__ float4 smem4[];
+        unsigned char *base = reinterpret_cast<unsigned char *>(smem4);
+        MlpFast *w = reinterpret_cast<MlpFast *>(base);
+        mlp_copy_fast(static_cast<const MlpFast *>(args.mlp), w);
+        mu.w = w;
+        mu.scratch = base + sizeof(MlpFast) + (threadIdx.x >> 5) * mlp_warp_scratch_bytes(mlp_rows_per_elem(ET));
+    }
     int idx[nen];
 #pragma unroll
     for (int a = 0; a < nen; ++a) idx[a] = __ldg(&b.conn[(int64_t)a * b.count + e]);
@@ -476,12 +536,13 @@ static cudaError_t launch_atomic_t(const BucketDev &b, const FieldDev &f, const 
                                    int threads, cudaStream_t s) {
     const unsigned blocks = (unsigned)((b.count + threads - 1) / threads);
     if (a.closure == FEA_CLOSURE_MLP) {
-        if (prec == FEA_FP64)
-            k_assemble_atomic<ET, double, false, true><<<blocks, threads, 0, s>>>(b, f, a);
-        else if (b.fp64j)
-            k_assemble_atomic<ET, float, true, true><<<blocks, threads, 0, s>>>(b, f, a);
-        else
-            k_assemble_atomic<ET, float, false, true><<<blocks, threads, 0, s>>>(b, f, a);
+        const size_t smem = mlp_smem_bytes(threads, mlp_rows_per_elem(ET));
+        auto kern = prec == FEA_FP64 ? k_assemble_atomic<ET, double, false, true>
+                                     : (b.fp64j ? k_assemble_atomic<ET, float, true, true>
+                                                : k_assemble_atomic<ET, float, false, true>);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<blocks, threads, smem, s>>>(b, f, a);
     } else if (prec == FEA_FP64)
         k_assemble_atomic<ET, double, false><<<blocks, threads, 0, s>>>(b, f, a);
     else if (b.fp64j)
@@ -652,12 +713,12 @@ __global__ void __launch_bounds__(256) k_assemble_chunk(BucketDev b, FieldDev f,
     extern __shared__ float4 smem4[];
     MlpUse mu{nullptr, nullptr};
     if constexpr (MLP) {
-        // weights and per-warp feature tiles after the chunk's buffers
+        // weights and per-warp scratch after the chunk's buffers
         unsigned char *tail = reinterpret_cast<unsigned char *>(smem4) + chunk_smem_bytes_dev(b);
-        MlpInfer *w = reinterpret_cast<MlpInfer *>(tail);
-        mlp_copy_infer(static_cast<const MlpInfer *>(args.mlp), w);
+        MlpFast *w = reinterpret_cast<MlpFast *>(tail);
+        mlp_copy_fast(static_cast<const MlpFast *>(args.mlp), w);
         mu.w = w;
-        mu.scratch = reinterpret_cast<uint16_t *>(tail + sizeof(MlpInfer)) + (threadIdx.x >> 5) * 32 * kW1Pitch;
+        mu.scratch = tail + sizeof(MlpFast) + (threadIdx.x >> 5) * mlp_warp_scratch_bytes(mlp_rows_per_elem(ET));
     }
     chunk_body<ET, J64, COMP, MLP>(b, f, args, blockIdx.x, smem4, mu);
 }
@@ -683,11 +744,12 @@ __global__ void __launch_bounds__(256, 2) k_assemble_batch(const BucketDev *__re
     __shared__ long long item_s;
     MlpUse mu{nullptr, nullptr};
     if constexpr (MLP) {
+        // element types vary per item: scratch for the largest row count
         unsigned char *tail = reinterpret_cast<unsigned char *>(smem4) + chunk_bytes;
-        MlpInfer *w = reinterpret_cast<MlpInfer *>(tail);
-        mlp_copy_infer(static_cast<const MlpInfer *>(ag[0].mlp), w);
+        MlpFast *w = reinterpret_cast<MlpFast *>(tail);
+        mlp_copy_fast(static_cast<const MlpFast *>(ag[0].mlp), w);
         mu.w = w;
-        mu.scratch = reinterpret_cast<uint16_t *>(tail + sizeof(MlpInfer)) + (threadIdx.x >> 5) * 32 * kW1Pitch;
+        mu.scratch = tail + sizeof(MlpFast) + (threadIdx.x >> 5) * mlp_warp_scratch_bytes(kMaxNg);
     }
     for (;;) {
         if (threadIdx.x == 0) item_s = (long long)atomicAdd(counter, 1ull);
@@ -716,7 +778,8 @@ cudaError_t launch_assemble_batch(const void *buckets, const void *fields, const
                                   cudaStream_t s) {
     if (n_items == 0) return cudaSuccess;
     const size_t chunk_bytes = smem;
-    if (mlp) smem += mlp_smem_bytes(256);
+    if (mlp) smem += mlp_smem_bytes(256, kMaxNg);
+    if (smem > kMaxBlockSmem) return cudaErrorInvalidConfiguration;
     auto kern = mlp ? k_assemble_batch<true> : k_assemble_batch<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -758,13 +821,21 @@ size_t chunk_kernel_smem(const BucketDev &b, int compensated) {
 
 size_t chunk_smem_bytes(const BucketDev &b) { return chunk_smem_bytes_dev(b); }
 
-size_t mlp_smem_bytes(int threads) { return sizeof(MlpInfer) + (size_t)(threads / 32) * 32 * kW1Pitch * 2; }
+size_t mlp_smem_bytes(int threads, int rows_per_elem) {
+    return sizeof(MlpFast) + (size_t)(threads / 32) * mlp_warp_scratch_bytes(rows_per_elem);
+}
+
+size_t chunk_launch_smem(const BucketDev &b, int threads, int compensated, bool mlp) {
+    if (!mlp) return chunk_kernel_smem(b, compensated);
+    return chunk_smem_bytes(b) + mlp_smem_bytes(threads, mlp_rows_per_elem(b.etype));
+}
 
 template <int ET, bool J64, bool COMP>
 static cudaError_t launch_chunk_v(const BucketDev &b, const FieldDev &f, const AsmArgs &a, int threads,
                                   cudaStream_t s) {
     const bool mlp = a.closure == FEA_CLOSURE_MLP;
-    const size_t smem = chunk_smem_bytes(b) + (mlp ? mlp_smem_bytes(threads) : 0);
+    const size_t smem = chunk_smem_bytes(b) + (mlp ? mlp_smem_bytes(threads, mlp_rows_per_elem(ET)) : 0);
+    if (smem > kMaxBlockSmem) return cudaErrorInvalidConfiguration;
     auto kern = mlp ? k_assemble_chunk<ET, J64, COMP, true> : k_assemble_chunk<ET, J64, COMP, false>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

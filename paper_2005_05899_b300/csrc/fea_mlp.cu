@@ -26,12 +26,59 @@ __device__ __forceinline__ uint16_t to_bf16_bits(float v) {
     return *reinterpret_cast<uint16_t *>(&b);
 }
 
+__device__ __forceinline__ uint16_t f16_bits(float v) {
+    __half h = __float2half_rn(v);
+    return *reinterpret_cast<uint16_t *>(&h);
+}
+
+// the BF16 rounding of v, stored as FP16 (exact unless it underflows FP16's
+// normal range, where FP16 subnormals keep it to 2^-24)
+__device__ __forceinline__ uint16_t bf16_as_f16_bits(float v) {
+    return f16_bits(__uint_as_float((uint32_t)to_bf16_bits(v) << 16));
+}
+
 __device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
 
-__global__ void k_mlp_pack(const float *theta, const float *mean, const float *stdv, float out_scale, MlpWeights *w) {
+__global__ void k_mlp_pack(const float *theta, const float *mean, const float *stdv, float out_scale, MlpWeights *w,
+                           MlpFast *fw) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nth = gridDim.x * blockDim.x;
+    // inference layout: the BF16 values of the hidden weights, halved (exact),
+    // in FP16 containers (exact); hidden biases halved
+    for (int k = tid; k < kMlpH * 8; k += nth) {
+        const int o = k / 8, i = k % 8;
+        fw->w1[o][i] = bf16_as_f16_bits(i < kMlpIn ? 0.5f * theta[OFF_W1 + o * kMlpIn + i] : 0.f);
+    }
+    for (int k = tid; k < kMlpH * kWPitch; k += nth) {
+        const int o = k / kWPitch, i = k % kWPitch;
+        const bool in = i < kMlpH;
+        fw->w2[o][i] = bf16_as_f16_bits(in ? 0.5f * theta[OFF_W2 + o * kMlpH + i] : 0.f);
+        fw->w3[o][i] = bf16_as_f16_bits(in ? 0.5f * theta[OFF_W3 + o * kMlpH + i] : 0.f);
+    }
+    for (int k = tid; k < 8 * kWPitch; k += nth) {
+        const int o = k / kWPitch, i = k % kWPitch;
+        uint16_t v = 0;
+        if (i < kMlpH && o < 2) {
+            const float x = theta[OFF_W4 + i];
+            const float hi = __uint_as_float((uint32_t)to_bf16_bits(x) << 16);
+            v = f16_bits(o == 0 ? hi : x - hi);
+        }
+        fw->w4[o][i] = v;
+    }
+    for (int k = tid; k < kMlpH; k += nth) {
+        fw->b1[k] = 0.5f * theta[OFF_B1 + k];
+        fw->b2[k] = 0.5f * theta[OFF_B2 + k];
+        fw->b3[k] = 0.5f * theta[OFF_B3 + k];
+    }
+    if (tid == 0) {
+        fw->b4 = theta[OFF_B4];
+        for (int k = 0; k < kMlpIn; ++k) {
+            fw->mean[k] = mean[k];
+            fw->istd[k] = 1.0f / stdv[k];
+        }
+        fw->out_scale = out_scale;
+    }
     for (int k = tid; k < kMlpH * kW1Pitch; k += nth) {
         const int o = k / kW1Pitch, i = k % kW1Pitch;
         w->inf.w1[o][i] = to_bf16_bits(i < kMlpIn ? theta[OFF_W1 + o * kMlpIn + i] : 0.f);
@@ -67,22 +114,36 @@ __device__ __forceinline__ void copy_weights_to_smem(const MlpWeights *g, MlpWei
     __syncthreads();
 }
 
-// batched forward: raw features x [B][6] -> nu_t y [B]
-__global__ void __launch_bounds__(256) k_mlp_forward(const MlpInfer *wg, const float *x, int64_t B, float *y) {
+// batched forward: raw features x [B][6] -> nu_t y [B]; each warp takes 32
+// rows at a time through a [32][8] bf16 feature tile and a [32] nu_t tile
+constexpr int kFwdTileBytes = 32 * 16 + 32 * 4;
+
+__global__ void __launch_bounds__(256) k_mlp_forward(const MlpFast *wg, const float *x, int64_t B, float *y) {
     extern __shared__ __align__(16) unsigned char smem[];
-    MlpInfer *w = reinterpret_cast<MlpInfer *>(smem);
-    uint16_t *scratch = reinterpret_cast<uint16_t *>(smem + sizeof(MlpInfer));
-    mlp_copy_infer(wg, w);
+    MlpFast *w = reinterpret_cast<MlpFast *>(smem);
+    mlp_copy_fast(wg, w);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint16_t *mine = scratch + warp * 32 * kW1Pitch;
+    unsigned char *mine = smem + sizeof(MlpFast) + warp * kFwdTileBytes;
+    uint32_t *feat = reinterpret_cast<uint32_t *>(mine);
+    float *nut = reinterpret_cast<float *>(mine + 32 * 16);
     const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32; base < B; base += warps_total * 32) {
         const int64_t r = base + lane;
-        float xr[kMlpIn];
+        float xn[kMlpIn];
 #pragma unroll
-        for (int k = 0; k < kMlpIn; ++k) xr[k] = r < B ? x[r * kMlpIn + k] : w->mean[k];
-        const float nut = mlp_warp_nut(*w, xr, mine);
-        if (r < B) y[r] = nut;
+        for (int k = 0; k < kMlpIn; ++k) {
+            const float v = r < B ? (x[r * kMlpIn + k] - w->mean[k]) * w->istd[k] : 0.0f;
+            xn[k] = isfinite(v) ? fminf(fmaxf(v, -kFeatClamp), kFeatClamp) : 0.0f;
+        }
+        feat[lane * 4 + 0] = pack_f16x2(xn[0], xn[1]);
+        feat[lane * 4 + 1] = pack_f16x2(xn[2], xn[3]);
+        feat[lane * 4 + 2] = pack_f16x2(xn[4], xn[5]);
+        feat[lane * 4 + 3] = 0u;
+        __syncwarp();
+        mlp_rows32(*w, reinterpret_cast<const uint16_t *>(feat), nut, 0);
+        __syncwarp();
+        if (r < B) y[r] = nut[lane];
+        __syncwarp();
     }
 }
 
@@ -350,23 +411,29 @@ __global__ void k_adam(float *theta, const float *grad, float *m1, float *m2, in
 
 }  // namespace
 
-size_t mlp_weights_bytes() { return sizeof(MlpWeights); }
+// One device block holds the training layout (MlpWeights) followed by the
+// inference layout (MlpFast).
+constexpr size_t kFastOffset = (sizeof(MlpWeights) + 255) & ~size_t(255);
+
+size_t mlp_weights_bytes() { return kFastOffset + sizeof(MlpFast); }
 int mlp_param_count() { return kMlpParams; }
+const void *mlp_fast_ptr(const void *w) { return static_cast<const unsigned char *>(w) + kFastOffset; }
 
 cudaError_t launch_mlp_pack(const float *theta, const float *mean, const float *stdv, float out_scale, void *w,
                             cudaStream_t s) {
-    k_mlp_pack<<<16, 256, 0, s>>>(theta, mean, stdv, out_scale, static_cast<MlpWeights *>(w));
+    k_mlp_pack<<<16, 256, 0, s>>>(theta, mean, stdv, out_scale, static_cast<MlpWeights *>(w),
+                                  reinterpret_cast<MlpFast *>(static_cast<unsigned char *>(w) + kFastOffset));
     return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_forward(const void *w, const float *x, int64_t B, float *y, int sms, cudaStream_t s) {
     if (B <= 0) return cudaSuccess;
-    const size_t smem = sizeof(MlpInfer) + 8 * 32 * kW1Pitch * sizeof(uint16_t);
+    const size_t smem = sizeof(MlpFast) + 8 * kFwdTileBytes;
     cudaError_t e = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t want = (B + 255) / 256;
     const int grid = (int)std::min<int64_t>(want, (int64_t)sms * 4);
-    k_mlp_forward<<<grid, 256, smem, s>>>(&static_cast<const MlpWeights *>(w)->inf, x, B, y);
+    k_mlp_forward<<<grid, 256, smem, s>>>(static_cast<const MlpFast *>(mlp_fast_ptr(w)), x, B, y);
     return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -201,37 +202,243 @@ __device__ __forceinline__ void mlp_copy_infer(const MlpInfer *g, MlpInfer *s) {
     __syncthreads();
 }
 
-// Warp-cooperative nu_t for 32 rows: every lane passes its row's raw
-// features (lanes of inactive rows pass anything finite); returns the lane's
-// nu_t.  scratch: per-warp shared tile of 32 x kW1Pitch bf16.  All 32 lanes
-// of the warp must call this together.
-__device__ __forceinline__ float mlp_warp_nut(const MlpInfer &w, const float x[kMlpIn], uint16_t *scratch) {
-    const int lane = threadIdx.x & 31;
-    uint32_t *row = reinterpret_cast<uint32_t *>(scratch + lane * kW1Pitch);
-    float xn[kMlpIn];
+// ---------------------------------------------------------------------------
+// Inference layout of the same network for the fused closure and the batched
+// forward.  The weights keep their BF16 values (the precision the network is
+// trained with) but are stored as FP16, which holds every such value exactly,
+// and the activations travel as FP16: the packed SiLU below loses about
+// |z| 2^-12 to cancellation where z << 0, eight times less than in BF16.
+// The hidden layers' weights and biases are stored halved, so a layer's
+// accumulator holds h = z/2 and SiLU(z) = h (1 + tanh h) costs one packed
+// tanh and one packed FMA per two activations.  The output weights are split
+// into two FP16 rows, hi = bf16(w4) and lo = w4 - hi, so the output layer is
+// one more tensor-core tile whose columns 0 and 1 add up to the FP32 dot.
+// Normalised features are clamped to +-64 (far outside any training data)
+// so that no FP16 value overflows.
+struct __align__(16) MlpFast {
+    uint16_t w1[kMlpH][8];         // f16 W1/2 [out][in], inputs 6, 7 zero
+    uint16_t w2[kMlpH][kWPitch];   // f16 W2/2 [out][in]
+    uint16_t w3[kMlpH][kWPitch];   // f16 W3/2
+    uint16_t w4[8][kWPitch];       // rows 0, 1: hi and lo parts of w4; rows 2..7 zero
+    float b1[kMlpH], b2[kMlpH], b3[kMlpH];   // halved
+    float b4;
+    float mean[kMlpIn], istd[kMlpIn];
+    float out_scale;
+};
+constexpr float kFeatClamp = 64.0f;
+
+// Per-warp scratch of the fused closure for ng Gauss points per element, 32
+// elements (one per lane): normalised feature rows [ng*32][8] f16 (row
+// g*32 + lane), the per-point matrices S [ng][9][32] f32 the subgrid term
+// needs once nu_t is known, and nu_t [ng*32] f32.
+__host__ __device__ constexpr size_t mlp_feat_bytes(int ng) { return (size_t)ng * 32 * 16; }
+__host__ __device__ constexpr size_t mlp_s_bytes(int ng) { return (size_t)ng * 9 * 32 * 4; }
+__host__ __device__ constexpr size_t mlp_warp_scratch_bytes(int ng) {
+    return mlp_feat_bytes(ng) + mlp_s_bytes(ng) + (size_t)ng * 32 * 4;
+}
+
+__device__ __forceinline__ void mlp_copy_fast(const MlpFast *g, MlpFast *s) {
+    const int4 *src = reinterpret_cast<const int4 *>(g);
+    int4 *dst = reinterpret_cast<int4 *>(s);
+    for (int k = threadIdx.x; k < (int)(sizeof(MlpFast) / 16); k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void *p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+__device__ __forceinline__ uint32_t pack_f16x2(float lo, float hi) {
+    __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void mma_f16_16816(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mma_f16_1688(float c[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(b0));
+}
+
+// SiLU of two halved pre-activations, packed FP16: h (1 + tanh h), h = z/2.
+__device__ __forceinline__ uint32_t silu_half_f16x2(float hlo, float hhi) {
+    const uint32_t h = pack_f16x2(hlo, hhi);
+    uint32_t th, out;
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(th) : "r"(h));
+    asm("fma.rn.f16x2 %0, %1, %2, %1;" : "=r"(out) : "r"(h), "r"(th));
+    return out;
+}
+
+__device__ __forceinline__ void fast_bias(float c[8][4], const float *b) {
+    const int t = threadIdx.x & 3;
 #pragma unroll
-    for (int k = 0; k < kMlpIn; ++k) xn[k] = (x[k] - w.mean[k]) * w.istd[k];
-    row[0] = pack_bf16x2(xn[0], xn[1]);
-    row[1] = pack_bf16x2(xn[2], xn[3]);
-    row[2] = pack_bf16x2(xn[4], xn[5]);
-#pragma unroll
-    for (int q = 3; q < 8; ++q) row[q] = 0u;
-    __syncwarp();
-    float nut_mine = 0.f;
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        uint32_t a1[4];
-        mlp_load_a1(scratch, 16 * half, a1);
-        float zg, zg8;
-        mlp_tile_forward(w, a1, zg, zg8);
-        // row r of this half lives in lanes 4 (r mod 8) + {0..3}
-        const int g = (lane & 15) & 7;   // the group that holds this lane's row
-        const float v_g = __shfl_sync(0xffffffffu, zg, 4 * g);
-        const float v_g8 = __shfl_sync(0xffffffffu, zg8, 4 * g);
-        if ((lane >> 4) == half) nut_mine = ((lane & 15) < 8) ? v_g : v_g8;
+    for (int j = 0; j < 8; ++j) {
+        const float2 v = *reinterpret_cast<const float2 *>(b + 8 * j + 2 * t);
+        c[j][0] = c[j][2] = v.x;
+        c[j][1] = c[j][3] = v.y;
     }
-    __syncwarp();
-    return w.out_scale * softplus_f(nut_mine);
+}
+
+// C fragments of 8 n-tiles -> SiLU -> A fragments of the next layer's 4 k-steps
+__device__ __forceinline__ void fast_silu(const float c[8][4], uint32_t h[4][4]) {
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        h[kk][0] = silu_half_f16x2(c[2 * kk][0], c[2 * kk][1]);
+        h[kk][1] = silu_half_f16x2(c[2 * kk][2], c[2 * kk][3]);
+        h[kk][2] = silu_half_f16x2(c[2 * kk + 1][0], c[2 * kk + 1][1]);
+        h[kk][3] = silu_half_f16x2(c[2 * kk + 1][2], c[2 * kk + 1][3]);
+    }
+}
+
+// One 64 -> 64 hidden layer for two 16-row tiles; B fragments by ldmatrix
+// (matrix q of a load: n-tile 2jp + q/2, k half q%2).
+__device__ __forceinline__ void fast_layer64(const uint32_t hin[2][4][4], const uint16_t (*W)[kWPitch],
+                                             const float *bias, uint32_t hout[2][4][4]) {
+    const int lane = threadIdx.x & 31, mat = lane >> 3, rr = lane & 7;
+    float c[2][8][4];
+    fast_bias(c[0], bias);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) c[1][j][q] = c[0][j][q];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+        for (int jp = 0; jp < 4; ++jp) {
+            uint32_t b[4];
+            ldsm_x4(b, &W[16 * jp + 8 * (mat >> 1) + rr][16 * kk + 8 * (mat & 1)]);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                mma_f16_16816(c[mt][2 * jp], hin[mt][kk], b[0], b[1]);
+                mma_f16_16816(c[mt][2 * jp + 1], hin[mt][kk], b[2], b[3]);
+            }
+        }
+    }
+    fast_silu(c[0], hout[0]);
+    fast_silu(c[1], hout[1]);
+}
+
+// Warp-cooperative nu_t of the 32 rows [32 blk, 32 blk + 32) of a feature
+// tile feat[rows][8] (f16, normalised, columns 6 and 7 zero); writes
+// nut[32 blk + r].  All 32 lanes call it together.
+__device__ __forceinline__ void mlp_rows32(const MlpFast &w, const uint16_t *feat, float *nut, int blk) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, mat = lane >> 3, rr = lane & 7;
+    const uint32_t *f32 = reinterpret_cast<const uint32_t *>(feat) + (size_t)blk * 32 * 4;
+    uint32_t h1[2][4][4];
+    {
+        float c[2][8][4];
+        fast_bias(c[0], w.b1);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) c[1][j][q] = c[0][j][q];
+        uint32_t b[8];
+        ldsm_x4(b, &w.w1[8 * mat + rr][0]);
+        ldsm_x4(b + 4, &w.w1[32 + 8 * mat + rr][0]);
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const uint32_t a0 = f32[(16 * mt + g) * 4 + t], a1 = f32[(16 * mt + g + 8) * 4 + t];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) mma_f16_1688(c[mt][j], a0, a1, b[j]);
+        }
+        fast_silu(c[0], h1[0]);
+        fast_silu(c[1], h1[1]);
+    }
+    uint32_t h2[2][4][4];
+    fast_layer64(h1, w.w2, w.b2, h2);
+    fast_layer64(h2, w.w3, w.b3, h1);
+    float c4[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        uint32_t b[4];
+        ldsm_x4(b, &w.w4[rr][16 * (2 * q + (mat >> 1)) + 8 * (mat & 1)]);
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            mma_f16_16816(c4[mt], h1[mt][2 * q], b[0], b[1]);
+            mma_f16_16816(c4[mt], h1[mt][2 * q + 1], b[2], b[3]);
+        }
+    }
+    if (t == 0) {
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const float zg = c4[mt][0] + c4[mt][1] + w.b4, zg8 = c4[mt][2] + c4[mt][3] + w.b4;
+            nut[32 * blk + 16 * mt + g] = w.out_scale * softplus_f(zg);
+            nut[32 * blk + 16 * mt + g + 8] = w.out_scale * softplus_f(zg8);
+        }
+    }
+}
+
+// The five invariant features of G (signed roots; log Delta is the sixth),
+// normalised and clamped, as f16 words: word 0 = (x0, x1), word 1 =
+// (x2, x3), word 2 = (x4, 0).  Non-finite values (degenerate elements, idle
+// lanes) become the mean.
+__device__ __forceinline__ void mlp_gp_words(const float G[3][3], const MlpFast &w, uint32_t words[3]) {
+    float S[3][3], O[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            S[i][j] = 0.5f * (G[i][j] + G[j][i]);
+            O[i][j] = 0.5f * (G[i][j] - G[j][i]);
+        }
+    float S2[3][3], O2[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float a = 0.f, b = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                a += S[i][k] * S[k][j];
+                b += O[i][k] * O[k][j];
+            }
+            S2[i][j] = a;
+            O2[i][j] = b;
+        }
+    float I[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        I[0] += S2[i][i];
+        I[1] += O2[i][i];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            I[2] += S2[i][k] * S[k][i];
+            I[3] += S[i][k] * O2[k][i];
+            I[4] += S2[i][k] * O2[k][i];
+        }
+    }
+    float xn[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const float a = fabsf(I[k]);
+        // roots of degree 2, 2, 3, 3, 4; the features are rounded to FP16 next,
+        // so the fast exp2/log2 power is ample for the cube root
+        float r = (k < 2) ? sqrtf(a) : (k < 4 ? __powf(a, 1.0f / 3.0f) : sqrtf(sqrtf(a)));
+        r = I[k] < 0.0f ? -r : r;
+        const float v = (r - w.mean[k]) * w.istd[k];
+        xn[k] = isfinite(v) ? fminf(fmaxf(v, -kFeatClamp), kFeatClamp) : 0.0f;
+    }
+    words[0] = pack_f16x2(xn[0], xn[1]);
+    words[1] = pack_f16x2(xn[2], xn[3]);
+    words[2] = pack_f16x2(xn[4], 0.0f);
+}
+
+// f16 bits of the normalised (clamped) log-Delta feature
+__device__ __forceinline__ uint16_t mlp_delta_bits(float delta, const MlpFast &w) {
+    float v = (__logf(delta) - w.mean[5]) * w.istd[5];
+    v = isfinite(v) ? fminf(fmaxf(v, -kFeatClamp), kFeatClamp) : 0.0f;
+    return (uint16_t)(pack_f16x2(v, 0.0f) & 0xffffu);
 }
 
 }  // namespace fea

@@ -4,8 +4,9 @@
         --plan chunk --threads 256 --chunk 512 --reps 3
 
 Builds the seeded mesh and field, uploads them, sets the launch plan and runs
-`--reps` mixed-precision Vreman assemblies (or RK3 graph steps with --rk3),
-then checks the device status word.
+`--reps` mixed-precision assemblies (or RK3 graph steps with --rk3) with the
+Vreman closure, or with `--closure mlp` a seeded random network scaled to
+Vreman's mean eddy viscosity, then checks the device status word.
 """
 from __future__ import annotations
 
@@ -25,6 +26,7 @@ def main(argv=None) -> int:
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--rk3", action="store_true")
+    ap.add_argument("--closure", choices=["vreman", "mlp"], default="vreman")
     a = ap.parse_args(argv)
     import torch
 
@@ -44,12 +46,20 @@ def main(argv=None) -> int:
     dm.set_plan(a.plan, a.threads, a.chunk, a.acc)
     dm.upload_field(f.u, f.p, f.nu, f.c_vreman)
     out = torch.empty((3, dm.n_nodes), dtype=torch.float64, device="cuda")
+    if a.closure == "mlp":
+        import numpy as np
+        nut = torch.empty(dm.n_gauss_total, dtype=torch.float32, device="cuda")
+        dm.assemble(out, prec=a.prec, closure="vreman", nut_out=nut)
+        rng = np.random.default_rng(11)
+        theta = (0.2 * rng.standard_normal(fea.MLP_NPARAM)).astype(np.float32)
+        mean = np.array([1.0, 1.0, 0.5, -0.5, 1.0, -3.0], np.float32)
+        ctx.mlp_load(theta, mean, np.ones(6, np.float32), float(nut.double().mean()) + 1e-12)
     t = time.time()
     for _ in range(a.reps):
         if a.rk3:
-            dm.rk_step_graph(1e-4, prec=a.prec)
+            dm.rk_step_graph(1e-4, prec=a.prec, closure=a.closure)
         else:
-            dm.assemble(out, prec=a.prec)
+            dm.assemble(out, prec=a.prec, closure=a.closure)
     torch.cuda.synchronize()
     ctx.sync_status()
     print(f"ok {m.counts()} {a.reps} reps {time.time() - t:.3f}s", flush=True)
