@@ -215,13 +215,32 @@ fea_status fea_state_download(fea_ctx *ctx, int32_t mesh, double *out, void *str
  *   tr S^2 O^2),  d = (2, 2, 3, 3, 4),  x_6 = log Delta  (Delta = V_e^(1/3)),
  * normalised as (x - mean) / std.  Parameter vector theta (FP32, 8,833):
  *   w1[64][6] b1[64] w2[64][64] b2[64] w3[64][64] b3[64] w4[64] b4[1].
- * Evaluation uses BF16 weights and activations with FP32 accumulation on
- * the tensor cores; the FP32 master copy is updated by Adam. */
+ * Training evaluates BF16 weights and activations with FP32 accumulation on
+ * the tensor cores and updates the FP32 master copy by Adam.  Inference
+ * (fea_mlp_forward and the fused closure) uses the same BF16 weight values
+ * with FP16 activations and FP32 accumulation; normalised features are
+ * clamped to +-64.  With an envelope set (fea_mlp_set_envelope), a Gauss
+ * point whose features or element size lie outside it takes Vreman's nu_t
+ * instead (section 2.1), so the plain closure is the network's fallback. */
 
 /* Loads theta, the feature mean and std [6] (host or device) and out_scale;
  * resets the Adam state.  Errors: FEA_EINVAL (null, std <= 0, scale <= 0). */
 fea_status fea_mlp_load(fea_ctx *ctx, const float *theta, const float *feat_mean, const float *feat_std,
                         double out_scale, void *stream);
+
+/* Training envelope of the fused closure: raw-feature bounds lo [6], hi [6]
+ * (host).  A Gauss point uses the network only if each of its five
+ * invariant features and its element's log Delta lie in [lo_k, hi_k];
+ * otherwise it uses Vreman's nu_t (c_vreman of the mesh's field), and the
+ * point is counted (fea_mlp_fallback_read).  lo = hi = NULL removes the
+ * envelope; fea_mlp_load also removes it.  Synchronises the stream.
+ * Errors: FEA_ESTATE (no network loaded), FEA_EINVAL (one bound NULL, NaN). */
+fea_status fea_mlp_set_envelope(fea_ctx *ctx, const float *lo, const float *hi, void *stream);
+
+/* Number of Gauss-point evaluations of the MLP closure that fell back to
+ * Vreman since the network was loaded or the last reset (reset != 0 zeroes
+ * the count after reading).  Synchronises the device. */
+fea_status fea_mlp_fallback_read(fea_ctx *ctx, int64_t *points, int reset);
 
 /* Copies the current FP32 parameters to theta_out [8833] (host or device). */
 fea_status fea_mlp_get(fea_ctx *ctx, float *theta_out, void *stream);

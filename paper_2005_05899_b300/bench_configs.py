@@ -117,26 +117,44 @@ def closure(reps: int, n_f: int = 256, steps: int = 8000, dims=(269, 134, 135)):
     from . import meshgen as mg
     ctx = fea.Context(0)
     t = time.time()
-    res = cd.run(n_f=n_f, ratios=(4, 8), t_train=(3.0, 4.0, 5.0, 7.0, 8.0), t_test=(6.0,), steps=steps,
+    res = cd.run(n_f=n_f, ratios=(2, 4, 8), t_train=(3.0, 4.0, 5.0, 7.0, 8.0), t_test=(6.0,), steps=steps,
                  log=None, ctx=ctx)
-    res.pop("model")
+    model = res.pop("model")
     train_total_s = time.time() - t
     m = mg.channel_mesh(*dims)
     f = mg.channel_field(m, nu=1.0 / 5600.0)
     dm = ctx.upload_mesh(m)
     dm.upload_field(f.u, f.p, f.nu, f.c_vreman)
     E = m.n_elem_total
-    plans = {}
-    ms = {}
-    N = dm.n_nodes
-    rhs = {c: torch.empty((3, N), dtype=torch.float64, device="cuda") for c in ("vreman", "mlp")}
-    sgs = {c: torch.empty((3, N), dtype=torch.float64, device="cuda") for c in ("vreman", "mlp")}
-    nut = {c: torch.empty(dm.n_gauss_total, dtype=torch.float32, device="cuda") for c in ("vreman", "mlp")}
-    for c in ("vreman", "mlp"):
-        plans[c] = dm.autotune(prec="mixed", closure=c).as_dict()
-        ms[c] = _time_assemble(dm, rhs[c], reps, prec="mixed", closure=c)
-        dm.assemble(rhs[c], prec="mixed", closure=c, nut_out=nut[c])
-        dm.assemble(sgs[c], prec="mixed", closure=c, mask=fea.TERM_SGS)
+    N, NG = dm.n_nodes, dm.n_gauss_total
+    kinds = ("vreman", "mlp", "mlp_raw")   # mlp: with the training envelope; mlp_raw: without
+
+    def closure_of(k):
+        return "vreman" if k == "vreman" else "mlp"
+
+    def envelope_for(k):
+        if k == "mlp_raw":
+            ctx.mlp_set_envelope(None, None)
+        elif k == "mlp":
+            ctx.mlp_set_envelope(model.env_lo, model.env_hi)
+
+    rhs = {k: torch.empty((3, N), dtype=torch.float64, device="cuda") for k in kinds}
+    sgs = {k: torch.empty((3, N), dtype=torch.float64, device="cuda") for k in kinds}
+    nut = {k: torch.empty(NG, dtype=torch.float32, device="cuda") for k in kinds}
+    plans, ms, fallback = {}, {}, {}
+    for k in kinds:
+        envelope_for(k)
+        plans[k] = dm.autotune(prec="mixed", closure=closure_of(k)).as_dict()
+        ms[k] = _time_assemble(dm, rhs[k], reps, prec="mixed", closure=closure_of(k))
+        ctx.sync_status()
+        if k != "vreman":
+            ctx.mlp_fallback_read(reset=True)
+        dm.assemble(rhs[k], prec="mixed", closure=closure_of(k), nut_out=nut[k])
+        ctx.sync_status()
+        if k != "vreman":
+            fallback[k] = ctx.mlp_fallback_read(reset=True) / NG
+        dm.assemble(sgs[k], prec="mixed", closure=closure_of(k), mask=fea.TERM_SGS)
+    envelope_for("mlp")
     ref64 = torch.empty((3, N), dtype=torch.float64, device="cuda")
     dm.assemble(ref64, prec="fp64", closure="mlp", scatter="atomic")
     ctx.sync_status()
@@ -144,17 +162,18 @@ def closure(reps: int, n_f: int = 256, steps: int = 8000, dims=(269, 134, 135)):
     def rel(a, b):
         return float(torch.linalg.norm((a - b).double()) / torch.linalg.norm(b.double()))
 
-    nv, nm = nut["vreman"], nut["mlp"]
+    nv = nut["vreman"]
     out = {"workload": f"learned closure: trained on box-filtered {n_f}^3 Taylor-Green runs, fused into "
                        f"channel {dims[0]}x{dims[1]}x{dims[2]} mixed ({E:,} elements)",
-           "counts": m.counts(), "elements": E, "gauss_points": int(dm.n_gauss_total),
+           "counts": m.counts(), "elements": E, "gauss_points": int(NG),
            "training": res, "train_total_s": train_total_s,
-           "assemble_ms": ms, "melem_s": {c: E / v / 1e3 for c, v in ms.items()},
+           "assemble_ms": ms, "melem_s": {k: E / v / 1e3 for k, v in ms.items()},
            "mlp_over_vreman_time": ms["mlp"] / ms["vreman"], "plans": plans,
-           "nut_rel_l2_mlp_vs_vreman": rel(nm, nv),
-           "nut_mean": {"vreman": float(nv.double().mean()), "mlp": float(nm.double().mean())},
-           "rhs_rel_l2_mlp_vs_vreman": rel(rhs["mlp"], rhs["vreman"]),
-           "sgs_rel_l2_mlp_vs_vreman": rel(sgs["mlp"], sgs["vreman"]),
+           "fallback_frac": fallback,
+           "nut_mean": {k: float(nut[k].double().mean()) for k in kinds},
+           "nut_rel_l2_vs_vreman": {k: rel(nut[k], nv) for k in kinds if k != "vreman"},
+           "rhs_rel_l2_vs_vreman": {k: rel(rhs[k], rhs["vreman"]) for k in kinds if k != "vreman"},
+           "sgs_rel_l2_vs_vreman": {k: rel(sgs[k], sgs["vreman"]) for k in kinds if k != "vreman"},
            "mlp_mixed_vs_fp64_rel_l2": rel(rhs["mlp"], ref64)}
     print(json.dumps(out), flush=True)
     ctx.close()

@@ -13,7 +13,8 @@ learned model, so this module defines the data pipeline:
    momentum without the pressure gradient, then projection).
 2. **Box filter** of the fine nodal velocity to a coarse grid of n_f / r
    cells per direction (trapezoidal top-hat of width r fine cells, periodic),
-   for r in `ratios` (two filter widths give the network Delta variation).
+   for r in `ratios` (several filter widths give the network the range of
+   Delta it is later applied to).
 3. **Samples per coarse TET04 element**: the FE gradient G of the filtered
    velocity, Delta = V_e^(1/3), the subgrid stress tau = bar(u u) - bar(u)
    bar(u) averaged over the element's vertices, and the least-squares eddy
@@ -141,8 +142,8 @@ class CoarseSet:
     u_nodes: np.ndarray       # (N, 3) filtered velocity at the coarse mesh's stored nodes
     feats: np.ndarray         # (E, 6) raw features per element
     target: np.ndarray        # (E,) nu_t*
-    tau_d: np.ndarray         # (E, 3, 3) deviatoric subgrid stress per element
-    grad_n: np.ndarray        # (E, 4, 3) shape-function gradients
+    tau_d: np.ndarray         # (E, 3, 3) deviatoric subgrid stress per element (None: training only)
+    grad_n: np.ndarray        # (E, 4, 3) shape-function gradients (None: training only)
     vol: np.ndarray           # (E,)
 
 
@@ -161,7 +162,10 @@ def _features(G: torch.Tensor, delta: torch.Tensor) -> torch.Tensor:
     return torch.stack(cols, dim=1)
 
 
-def coarse_samples(snap: Snapshot, r: int) -> CoarseSet:
+def coarse_samples(snap: Snapshot, r: int, keep_stress: bool = True) -> CoarseSet:
+    """Filtered coarse field, features and targets at filter ratio r; the
+    per-element stresses and gradients are kept for the a-priori comparison
+    only when keep_stress."""
     n_f = snap.u.shape[-1]
     n_c = n_f // r
     ub = _box(snap.u, r)[:, ::r, ::r, ::r].contiguous()                  # [3, n_c^3]
@@ -192,14 +196,17 @@ def coarse_samples(snap: Snapshot, r: int) -> CoarseSet:
     target = torch.clamp(-(td * S).sum((1, 2)) / (2.0 * ss + 1e-300), min=0.0)
     feats = _features(G, vol.abs() ** (1.0 / 3.0))
     return CoarseSet(n_c=n_c, mesh=mesh, u_nodes=u_nodes.cpu().numpy(), feats=feats.cpu().numpy(),
-                     target=target.cpu().numpy(), tau_d=td.cpu().numpy(), grad_n=gN.cpu().numpy(),
-                     vol=vol.cpu().numpy())
+                     target=target.cpu().numpy(), tau_d=td.cpu().numpy() if keep_stress else None,
+                     grad_n=gN.cpu().numpy() if keep_stress else None, vol=vol.cpu().numpy())
 
 
-def generate(ctx: fea.Context, n_f: int = 96, ratios=(4, 8), t_snap=(3.0, 4.0, 5.0, 6.0, 7.0, 8.0), log=None):
-    """Fine run + filtered samples: {t: [CoarseSet per ratio]}."""
+def generate(ctx: fea.Context, n_f: int = 96, ratios=(4, 8), t_snap=(3.0, 4.0, 5.0, 6.0, 7.0, 8.0), log=None,
+             t_stress=None):
+    """Fine run + filtered samples: {t: [CoarseSet per ratio]}; stresses kept
+    at the times in t_stress (all when None)."""
     snaps = fine_tgv_run(ctx, n_f, t_snap, log=log)
-    return {s.t: [coarse_samples(s, r) for r in ratios] for s in snaps}
+    return {s.t: [coarse_samples(s, r, keep_stress=t_stress is None or s.t in t_stress) for r in ratios]
+            for s in snaps}
 
 
 @dataclasses.dataclass
@@ -210,20 +217,34 @@ class TrainedClosure:
     scale: float
     losses: List[float]       # batch losses every 100 steps (units of scale^2)
     fit_mse: float = float("nan")      # full training set, same units
+    n_samples: int = 0
+    env_lo: np.ndarray = None          # training envelope (raw features), set in the context
+    env_hi: np.ndarray = None
     target_var: float = float("nan")   # variance of the normalised target (the best constant's MSE)
 
 
 def train(ctx: fea.Context, sets: Sequence[CoarseSet], steps: int = 2000, batch: int = 65536, lr: float = 2e-3,
-          seed: int = 0) -> TrainedClosure:
-    """Fits the network to nu_t* on the GPU (the library's training step)."""
-    x = np.concatenate([c.feats for c in sets]).astype(np.float32)
-    y = np.concatenate([c.target for c in sets])
+          seed: int = 0, max_per_set: int = 2_000_000, envelope_q: float = 1e-4) -> TrainedClosure:
+    """Fits the network to nu_t* on the GPU (the library's training step).
+    Each set contributes at most max_per_set seeded random samples, so fine
+    filter widths (many coarse elements) do not swamp the coarse ones.  The
+    per-feature [q, 1 - q] quantiles of the training features become the
+    closure's envelope (Vreman outside it)."""
+    rng = np.random.default_rng(seed)
+    xs, ys = [], []
+    for c in sets:
+        take = np.arange(c.target.size)
+        if take.size > max_per_set:
+            take = np.sort(rng.choice(take.size, max_per_set, replace=False))
+        xs.append(c.feats[take])
+        ys.append(c.target[take])
+    x = np.concatenate(xs).astype(np.float32)
+    y = np.concatenate(ys)
     keep = np.all(np.isfinite(x), axis=1) & np.isfinite(y)
     x, y = x[keep], y[keep]
     mean = x.mean(axis=0)
     std = x.std(axis=0) + 1e-6
     scale = float(np.mean(y)) + 1e-12
-    rng = np.random.default_rng(seed)
     theta = np.zeros(fea.MLP_NPARAM, np.float32)
     off = 0
     for n_out, n_in in ((64, 6), (64, 64), (64, 64), (1, 64)):
@@ -253,8 +274,11 @@ def train(ctx: fea.Context, sets: Sequence[CoarseSet], steps: int = 2000, batch:
     ys = yt.double()
     mse = float(((pred.double() / scale - ys) ** 2).mean())
     var = float(ys.var(unbiased=False))
+    lo = np.quantile(x, envelope_q, axis=0).astype(np.float32)
+    hi = np.quantile(x, 1.0 - envelope_q, axis=0).astype(np.float32)
+    ctx.mlp_set_envelope(lo, hi)
     return TrainedClosure(theta=ctx.mlp_get(), mean=mean, std=std, scale=scale, losses=losses,
-                          fit_mse=mse, target_var=var)
+                          fit_mse=mse, target_var=var, n_samples=n, env_lo=lo, env_hi=hi)
 
 
 def apriori_errors(ctx: fea.Context, cs: CoarseSet, nu: float = 1.0 / 1600.0, c_vreman: float = 0.07) -> Dict:
@@ -283,9 +307,13 @@ def apriori_errors(ctx: fea.Context, cs: CoarseSet, nu: float = 1.0 / 1600.0, c_
     nut = torch.empty(dm.n_gauss_total, dtype=torch.float32, device="cuda")
     tgt = cs.target
     for name in ("vreman", "mlp"):
+        if name == "mlp":
+            ctx.mlp_fallback_read(reset=True)
         dm.assemble(R, prec="mixed", closure=name, mask=fea.TERM_SGS, nut_out=nut)
         dm.fold(R)
         ctx.sync_status()
+        if name == "mlp":
+            out["fallback_frac"] = ctx.mlp_fallback_read(reset=True) / dm.n_gauss_total
         r = R.cpu().numpy()[:, masters]
         nt = nut.cpu().numpy().reshape(-1, 4)[:, 0]
         diss = float((u_m * r).sum())
@@ -307,7 +335,8 @@ def run(n_f: int = 96, ratios=(4, 8), t_train=(3.0, 4.0, 5.0, 7.0, 8.0), t_test=
     if own:
         ctx = fea.Context(0)
     t0 = time.time()
-    data = generate(ctx, n_f=n_f, ratios=ratios, t_snap=sorted(set(t_train) | set(t_test)), log=log)
+    data = generate(ctx, n_f=n_f, ratios=ratios, t_snap=sorted(set(t_train) | set(t_test)), log=log,
+                    t_stress=set(t_test))
     t_gen = time.time() - t0
     train_sets = [c for t in t_train for c in data[t]]
     test_sets = [c for t in t_test for c in data[t]]
@@ -315,8 +344,9 @@ def run(n_f: int = 96, ratios=(4, 8), t_train=(3.0, 4.0, 5.0, 7.0, 8.0), t_test=
     model = train(ctx, train_sets, steps=steps)
     t_train_s = time.time() - t0
     if save:
-        np.savez(save, theta=model.theta, mean=model.mean, std=model.std, scale=model.scale)
-    res = {"n_f": n_f, "ratios": list(ratios), "samples_train": int(sum(c.target.size for c in train_sets)),
+        np.savez(save, theta=model.theta, mean=model.mean, std=model.std, scale=model.scale, env_lo=model.env_lo,
+                 env_hi=model.env_hi)
+    res = {"n_f": n_f, "ratios": list(ratios), "samples_train": int(model.n_samples),
            "generate_s": t_gen, "train_s": t_train_s, "loss_first": model.losses[0], "loss_last": model.losses[-1],
            "fit_mse": model.fit_mse, "target_var": model.target_var, "test": []}
     for c in test_sets:

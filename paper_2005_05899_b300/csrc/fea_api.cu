@@ -298,6 +298,7 @@ struct fea_ctx {
     // learned closure: FP32 master parameters, Adam moments, packed BF16 weights
     DevBuf<float> mlp_theta, mlp_m1, mlp_m2, mlp_grad, mlp_loss, mlp_norm;
     DevBuf<unsigned char> mlp_w;
+    DevBuf<unsigned long long> mlp_fb;   // Gauss points that fell back to Vreman
     int64_t mlp_step = 0;
     double mlp_scale = 0.0;
     bool mlp_ready = false;
@@ -479,6 +480,7 @@ fea_status assemble_into(fea_ctx *ctx, Mesh &m, fea_prec prec, fea_closure closu
             a.nut = nut ? nut + type_nut_offset(m, b.etype) : nullptr;
             a.err = ctx->d_err;
             a.mlp = closure == FEA_CLOSURE_MLP ? mlp_fast_ptr(ctx->mlp_w.p) : nullptr;
+            a.mlp_fb = closure == FEA_CLOSURE_MLP ? ctx->mlp_fb.p : nullptr;
             cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
             if (ctx->profiling) CK(cudaStreamIsCapturing(s, &cap));
             ProfRec pr{b.etype, b.fp64j, nullptr, nullptr};
@@ -597,6 +599,7 @@ fea_status stage_with_scratch(fea_ctx *ctx, int32_t mesh, int32_t stage, double 
             a.nut = nullptr;
             a.err = ctx->d_err;
             a.mlp = closure == FEA_CLOSURE_MLP ? mlp_fast_ptr(ctx->mlp_w.p) : nullptr;
+            a.mlp_fb = closure == FEA_CLOSURE_MLP ? ctx->mlp_fb.p : nullptr;
             if (prec == FEA_MIXED && scatter == FEA_SCATTER_CHUNK && b.lconn.p)
                 CK(launch_assemble_chunk(b.dev(), f, a, m->plan.threads_per_block, m->plan.chunk_acc, ls));
             else
@@ -949,6 +952,7 @@ fea_status fea_assemble_rhs_batched(fea_ctx *ctx, const int32_t *meshes, int32_t
             a.nut = nullptr;
             a.err = ctx->d_err;
             a.mlp = closure == FEA_CLOSURE_MLP ? mlp_fast_ptr(ctx->mlp_w.p) : nullptr;
+            a.mlp_fb = closure == FEA_CLOSURE_MLP ? ctx->mlp_fb.p : nullptr;
             ag.push_back(a);
             smem = std::max(smem, chunk_smem_bytes(bk.back()));
         }
@@ -1183,12 +1187,19 @@ fea_status fea_mlp_load(fea_ctx *ctx, const float *theta, const float *feat_mean
         CK(ctx->mlp_m2.alloc(np));
         CK(ctx->mlp_grad.alloc(np));
         CK(ctx->mlp_loss.alloc(1));
-        CK(ctx->mlp_norm.alloc(12));
+        CK(ctx->mlp_norm.alloc(24));   // mean[6], std[6], envelope lo[6], hi[6]
         CK(ctx->mlp_w.alloc(mlp_weights_bytes()));
+        CK(ctx->mlp_fb.alloc(1));
+        CK(cudaMemsetAsync(ctx->mlp_fb.p, 0, sizeof(unsigned long long), s));
     }
     CK(cudaMemcpyAsync(ctx->mlp_theta.p, theta, sizeof(float) * np, cudaMemcpyDefault, s));
     CK(cudaMemcpyAsync(ctx->mlp_norm.p, feat_mean, sizeof(float) * 6, cudaMemcpyDefault, s));
     CK(cudaMemcpyAsync(ctx->mlp_norm.p + 6, feat_std, sizeof(float) * 6, cudaMemcpyDefault, s));
+    // a new network starts without an envelope
+    static const float open_env[12] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY, -INFINITY, -INFINITY,
+                                       INFINITY,  INFINITY,  INFINITY,  INFINITY,  INFINITY,  INFINITY};
+    CK(cudaMemcpyAsync(ctx->mlp_norm.p + 12, open_env, sizeof(open_env), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));   // open_env and the caller's arrays are read before returning
     CK(cudaMemsetAsync(ctx->mlp_m1.p, 0, sizeof(float) * np, s));
     CK(cudaMemsetAsync(ctx->mlp_m2.p, 0, sizeof(float) * np, s));
     CK(launch_mlp_pack(ctx->mlp_theta.p, ctx->mlp_norm.p, ctx->mlp_norm.p + 6, (float)out_scale, ctx->mlp_w.p, s));
@@ -1196,6 +1207,36 @@ fea_status fea_mlp_load(fea_ctx *ctx, const float *theta, const float *feat_mean
     ctx->mlp_step = 0;
     ctx->mlp_scale = out_scale;
     ctx->mlp_ready = true;
+    return FEA_OK;
+}
+
+fea_status fea_mlp_set_envelope(fea_ctx *ctx, const float *lo, const float *hi, void *stream) {
+    if (!ctx) return FEA_EINVAL;
+    if (!ctx->mlp_ready) return fail(ctx, FEA_ESTATE, "no MLP loaded");
+    if ((lo == nullptr) != (hi == nullptr)) return fail(ctx, FEA_EINVAL, "envelope needs both bounds or neither");
+    float env[12];
+    for (int k = 0; k < 6; ++k) {
+        env[k] = lo ? lo[k] : -INFINITY;
+        env[6 + k] = hi ? hi[k] : INFINITY;
+        if (env[k] != env[k] || env[6 + k] != env[6 + k]) return fail(ctx, FEA_EINVAL, "NaN envelope bound");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(ctx->mlp_norm.p + 12, env, sizeof(env), cudaMemcpyHostToDevice, s));
+    CK(launch_mlp_pack(ctx->mlp_theta.p, ctx->mlp_norm.p, ctx->mlp_norm.p + 6, (float)ctx->mlp_scale, ctx->mlp_w.p, s));
+    ctx->launches++;
+    CK(cudaStreamSynchronize(s));   // env is a host stack array
+    return FEA_OK;
+}
+
+fea_status fea_mlp_fallback_read(fea_ctx *ctx, int64_t *points, int reset) {
+    if (!ctx || !points) return ctx ? fail(ctx, FEA_EINVAL, "null output") : FEA_EINVAL;
+    if (!ctx->mlp_ready) return fail(ctx, FEA_ESTATE, "no MLP loaded");
+    unsigned long long v = 0;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(&v, ctx->mlp_fb.p, sizeof(v), cudaMemcpyDeviceToHost));
+    if (reset) CK(cudaMemset(ctx->mlp_fb.p, 0, sizeof(v)));
+    *points = (int64_t)v;
     return FEA_OK;
 }
 

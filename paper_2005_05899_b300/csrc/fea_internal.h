@@ -77,6 +77,7 @@ struct AsmArgs {
     float *nut;           // optional: type block of nu_t output (already offset)
     unsigned *err;        // device error word
     const void *mlp;      // MLP closure weights (device MlpFast) when closure == FEA_CLOSURE_MLP
+    unsigned long long *mlp_fb = nullptr;   // count of Gauss points that fell back to Vreman (MLP only)
 };
 
 // launchers (fea_kernels.cu); all return cudaGetLastError() of the launch

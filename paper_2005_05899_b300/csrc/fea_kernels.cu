@@ -212,9 +212,11 @@ __host__ __device__ constexpr int mlp_rows_per_elem(int et) {
 template <int ET, typename R, typename JR>
 __device__ __forceinline__ JR prism_or_generic_jacobian(const JR X[][3], const PrismGeom<JR> &pg, int g, JR J[3][3]);
 
+// Returns the number of Gauss points whose nu_t fell back from the MLP to
+// Vreman (outside the training envelope); 0 without the MLP.
 template <int ET, typename R, bool J64, bool MLP = false>
-__device__ void element_residual(const Gathered<R, J64> &el, const FieldDev &f, const AsmArgs &args, R r[][3],
-                                 float *nut_out, bool &bad, const MlpUse &mu = MlpUse{nullptr, nullptr}) {
+__device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, const AsmArgs &args, R r[][3],
+                                float *nut_out, bool &bad, const MlpUse &mu = MlpUse{nullptr, nullptr}) {
     using JR = typename std::conditional<J64, double, R>::type;
     constexpr int nen = kNen[ET], ng = kNg[ET];
     const uint32_t mask = args.mask;
@@ -236,6 +238,8 @@ __device__ void element_residual(const Gathered<R, J64> &el, const FieldDev &f, 
     uint32_t *featw = reinterpret_cast<uint32_t *>(mu.scratch);
     float *Stile = reinterpret_cast<float *>(mu.scratch + mlp_feat_bytes(ng));
     float *ntile = Stile + ng * 9 * 32;
+    float *qtile = ntile + ng * 32;
+    uint32_t inside_mask = 0;   // bit g: point g inside the training envelope
     JR V = JR(0);
 #pragma unroll 1
     for (int g = 0; g < ng; ++g) {
@@ -285,12 +289,15 @@ __device__ void element_residual(const Gathered<R, J64> &el, const FieldDev &f, 
 #pragma unroll
                 for (int j = 0; j < 3; ++j) Gf[i][j] = float(G[i][j]);
             uint32_t wds[3];
-            mlp_gp_words(Gf, *mu.w, wds);
+            const bool inside = mlp_gp_words(Gf, *mu.w, wds);
             uint32_t *row = featw + (g * 32 + lane) * 4;
             row[0] = wds[0];
             row[1] = wds[1];
             row[2] = wds[2];
             row[3] = 0u;
+            inside_mask |= (uint32_t)inside << g;
+            // with an envelope, Vreman's q = nu_t / Delta^2 for the fallback
+            if (mu.w->env_on) qtile[g * 32 + lane] = float(vreman(G, R(1), cv));
         } else {
             if (nut_out) nut_out[g] = float(q);
         }
@@ -329,9 +336,14 @@ __device__ void element_residual(const Gathered<R, J64> &el, const FieldDev &f, 
             }
         }
     }
+    int fallbacks = 0;
     if constexpr (MLP) {
         // Delta = V^(1/3) completes every row (column 5)
-        const uint16_t db = mlp_delta_bits(float(cbrt_r(R(V))), *mu.w);
+        const R delta = cbrt_r(R(V));
+        const R d2 = delta * delta;
+        bool delta_inside;
+        const uint16_t db = mlp_delta_bits(float(delta), *mu.w, &delta_inside);
+        if (!delta_inside) inside_mask = 0;
 #pragma unroll 1
         for (int g = 0; g < ng; ++g) reinterpret_cast<uint16_t *>(featw + (g * 32 + lane) * 4)[5] = db;
         __syncwarp();
@@ -340,7 +352,9 @@ __device__ void element_residual(const Gathered<R, J64> &el, const FieldDev &f, 
         __syncwarp();
 #pragma unroll 1
         for (int g = 0; g < ng; ++g) {
-            const R nt = R(ntile[g * 32 + lane]);
+            const bool use = (inside_mask >> g) & 1u;
+            fallbacks += !use;
+            const R nt = use ? R(ntile[g * 32 + lane]) : R(qtile[g * 32 + lane]) * d2;
             if (nut_out) nut_out[g] = float(nt);
             if (mask & FEA_TERM_SGS) {
                 R Sg[3][3];
@@ -368,6 +382,7 @@ __device__ void element_residual(const Gathered<R, J64> &el, const FieldDev &f, 
         if (nut_out)
             for (int g = 0; g < ng; ++g) nut_out[g] = float(R(nut_out[g]) * d2);
     }
+    return fallbacks;
 }
 
 template <int ET, typename R, typename JR>
@@ -390,8 +405,8 @@ __device__ __forceinline__ JR prism_or_generic_jacobian(const JR X[][3], const P
 // degree-2 integrands, so the Gauss sums take their closed forms:
 //   sum_g W N_a N_b = V (1 + delta_ab) / 20,  sum_g W N_a = V / 4.
 template <typename R, bool J64, bool MLP = false>
-__device__ void tet_residual(const Gathered<R, J64> &el, const FieldDev &f, const AsmArgs &args, R r[][3],
-                             float *nut_out, bool &bad, const MlpUse &mu = MlpUse{nullptr, nullptr}) {
+__device__ int tet_residual(const Gathered<R, J64> &el, const FieldDev &f, const AsmArgs &args, R r[][3],
+                            float *nut_out, bool &bad, const MlpUse &mu = MlpUse{nullptr, nullptr}) {
     using JR = typename std::conditional<J64, double, R>::type;
     const uint32_t mask = args.mask;
     JR J[3][3];
@@ -426,6 +441,7 @@ __device__ void tet_residual(const Gathered<R, J64> &el, const FieldDev &f, cons
         }
     }
     R nut = R(0);
+    int fallbacks = 0;
     if constexpr (MLP) {
         // one row per element (lane) through the warp's 32-row tile
         const int lane = threadIdx.x & 31;
@@ -437,15 +453,22 @@ __device__ void tet_residual(const Gathered<R, J64> &el, const FieldDev &f, cons
         uint32_t *row = reinterpret_cast<uint32_t *>(mu.scratch) + lane * 4;
         float *ntile = reinterpret_cast<float *>(mu.scratch + mlp_feat_bytes(1) + mlp_s_bytes(1));
         uint32_t wds[3];
-        mlp_gp_words(Gf, *mu.w, wds);
+        const bool inside = mlp_gp_words(Gf, *mu.w, wds);
+        bool delta_inside;
         row[0] = wds[0];
         row[1] = wds[1];
-        row[2] = (wds[2] & 0xffffu) | ((uint32_t)mlp_delta_bits(float(cbrt_r(V)), *mu.w) << 16);
+        row[2] = (wds[2] & 0xffffu) | ((uint32_t)mlp_delta_bits(float(cbrt_r(V)), *mu.w, &delta_inside) << 16);
         row[3] = 0u;
         __syncwarp();
         mlp_rows32(*mu.w, reinterpret_cast<const uint16_t *>(mu.scratch), ntile, 0);
         __syncwarp();
-        nut = R(ntile[lane]);
+        if (inside && delta_inside) {
+            nut = R(ntile[lane]);
+        } else {
+            const R delta = cbrt_r(V);
+            nut = vreman(G, delta * delta, R(f.c_vreman));
+            fallbacks = 4;   // all four Gauss points
+        }
         __syncwarp();
     } else if (args.closure == FEA_CLOSURE_VREMAN && ((mask & FEA_TERM_SGS) || nut_out)) {
         const R delta = cbrt_r(V);
@@ -482,6 +505,14 @@ __device__ void tet_residual(const Gathered<R, J64> &el, const FieldDev &f, cons
             r[a][i] = -v;
         }
     }
+    return fallbacks;
+}
+
+// warp-aggregated count of MLP fallbacks (all 32 lanes call it together)
+__device__ __forceinline__ void count_fallbacks(unsigned long long *counter, int n) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if (counter && (threadIdx.x & 31) == 0 && n) atomicAdd(counter, (unsigned long long)n);
 }
 
 // ---------------------------------------------------------------------------
@@ -515,10 +546,12 @@ __global__ void __launch_bounds__(256) k_assemble_atomic(BucketDev b, FieldDev f
     bool bad = false;
     float nut_tmp[ng];
     float *nut = args.nut ? (active ? args.nut + (int64_t)__ldg(&b.orig[e]) * ng : nut_tmp) : nullptr;
+    int fb;
     if constexpr (ET == FEA_TET04)
-        tet_residual<R, J64, MLP>(el, f, args, r, nut, bad, mu);
+        fb = tet_residual<R, J64, MLP>(el, f, args, r, nut, bad, mu);
     else
-        element_residual<ET, R, J64, MLP>(el, f, args, r, nut, bad, mu);
+        fb = element_residual<ET, R, J64, MLP>(el, f, args, r, nut, bad, mu);
+    if constexpr (MLP) count_fallbacks(args.mlp_fb, active ? fb : 0);
     if (!active) return;
     R chk = R(0);
 #pragma unroll
@@ -614,6 +647,7 @@ __device__ __forceinline__ void chunk_body(const BucketDev &b, const FieldDev &f
     __syncthreads();
     bool bad = false;
     float chk = 0.0f;
+    int fallbacks = 0;
     // warp-uniform trip count: with the MLP every lane of a warp joins the
     // network evaluation; lanes past the chunk's end repeat its last element
     for (int base = 0; base < ne; base += blockDim.x) {
@@ -657,10 +691,12 @@ __device__ __forceinline__ void chunk_body(const BucketDev &b, const FieldDev &f
         float r[kMaxNen][3];
         float nut_tmp[ng];
         float *nut = args.nut ? (active ? args.nut + (int64_t)__ldg(&b.orig[e]) * ng : nut_tmp) : nullptr;
+        int fb;
         if constexpr (ET == FEA_TET04)
-            tet_residual<float, J64, MLP>(g, f, args, r, nut, bad, mu);
+            fb = tet_residual<float, J64, MLP>(g, f, args, r, nut, bad, mu);
         else
-            element_residual<ET, float, J64, MLP>(g, f, args, r, nut, bad, mu);
+            fb = element_residual<ET, float, J64, MLP>(g, f, args, r, nut, bad, mu);
+        if (active) fallbacks += fb;
         if (!active) continue;
 #pragma unroll
         for (int a = 0; a < nen; ++a) {
@@ -668,6 +704,7 @@ __device__ __forceinline__ void chunk_body(const BucketDev &b, const FieldDev &f
             chk += r[a][0] + r[a][1] + r[a][2];
         }
     }
+    if constexpr (MLP) count_fallbacks(args.mlp_fb, fallbacks);
     if (bad) set_err(args.err, ERR_DETJ);
     if (!isfinite(chk)) set_err(args.err, ERR_NONFINITE);
     __syncthreads();

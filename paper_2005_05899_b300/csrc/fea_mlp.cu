@@ -76,7 +76,13 @@ __global__ void k_mlp_pack(const float *theta, const float *mean, const float *s
         for (int k = 0; k < kMlpIn; ++k) {
             fw->mean[k] = mean[k];
             fw->istd[k] = 1.0f / stdv[k];
+            // envelope bounds follow std in the norm block: lo[6], hi[6] (raw units)
+            fw->env_lo[k] = (stdv[kMlpIn + k] - mean[k]) / stdv[k];
+            fw->env_hi[k] = (stdv[2 * kMlpIn + k] - mean[k]) / stdv[k];
         }
+        int on = 0;
+        for (int k = 0; k < kMlpIn; ++k) on |= isfinite(fw->env_lo[k]) || isfinite(fw->env_hi[k]);
+        fw->env_on = on;
         fw->out_scale = out_scale;
     }
     for (int k = tid; k < kMlpH * kW1Pitch; k += nth) {

@@ -223,7 +223,9 @@ struct __align__(16) MlpFast {
     float b1[kMlpH], b2[kMlpH], b3[kMlpH];   // halved
     float b4;
     float mean[kMlpIn], istd[kMlpIn];
+    float env_lo[kMlpIn], env_hi[kMlpIn];   // training envelope, normalised units (+-inf: none)
     float out_scale;
+    int env_on;                              // any finite envelope bound
 };
 constexpr float kFeatClamp = 64.0f;
 
@@ -233,8 +235,10 @@ constexpr float kFeatClamp = 64.0f;
 // needs once nu_t is known, and nu_t [ng*32] f32.
 __host__ __device__ constexpr size_t mlp_feat_bytes(int ng) { return (size_t)ng * 32 * 16; }
 __host__ __device__ constexpr size_t mlp_s_bytes(int ng) { return (size_t)ng * 9 * 32 * 4; }
+// after them: nu_t [ng*32] f32 and Vreman's q = nu_t / Delta^2 [ng*32] f32
+// (negative where the point is inside the training envelope)
 __host__ __device__ constexpr size_t mlp_warp_scratch_bytes(int ng) {
-    return mlp_feat_bytes(ng) + mlp_s_bytes(ng) + (size_t)ng * 32 * 4;
+    return mlp_feat_bytes(ng) + mlp_s_bytes(ng) + (size_t)ng * 32 * 4 * 2;
 }
 
 __device__ __forceinline__ void mlp_copy_fast(const MlpFast *g, MlpFast *s) {
@@ -382,8 +386,9 @@ __device__ __forceinline__ void mlp_rows32(const MlpFast &w, const uint16_t *fea
 // The five invariant features of G (signed roots; log Delta is the sixth),
 // normalised and clamped, as f16 words: word 0 = (x0, x1), word 1 =
 // (x2, x3), word 2 = (x4, 0).  Non-finite values (degenerate elements, idle
-// lanes) become the mean.
-__device__ __forceinline__ void mlp_gp_words(const float G[3][3], const MlpFast &w, uint32_t words[3]) {
+// lanes) become the mean.  Returns whether the five lie inside the training
+// envelope (the caller falls back to Vreman's nu_t where they do not).
+__device__ __forceinline__ bool mlp_gp_words(const float G[3][3], const MlpFast &w, uint32_t words[3]) {
     float S[3][3], O[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -419,6 +424,7 @@ __device__ __forceinline__ void mlp_gp_words(const float G[3][3], const MlpFast 
         }
     }
     float xn[5];
+    bool inside = true;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         const float a = fabsf(I[k]);
@@ -427,16 +433,20 @@ __device__ __forceinline__ void mlp_gp_words(const float G[3][3], const MlpFast 
         float r = (k < 2) ? sqrtf(a) : (k < 4 ? __powf(a, 1.0f / 3.0f) : sqrtf(sqrtf(a)));
         r = I[k] < 0.0f ? -r : r;
         const float v = (r - w.mean[k]) * w.istd[k];
+        inside = inside && v >= w.env_lo[k] && v <= w.env_hi[k];   // false for NaN
         xn[k] = isfinite(v) ? fminf(fmaxf(v, -kFeatClamp), kFeatClamp) : 0.0f;
     }
     words[0] = pack_f16x2(xn[0], xn[1]);
     words[1] = pack_f16x2(xn[2], xn[3]);
     words[2] = pack_f16x2(xn[4], 0.0f);
+    return inside;
 }
 
-// f16 bits of the normalised (clamped) log-Delta feature
-__device__ __forceinline__ uint16_t mlp_delta_bits(float delta, const MlpFast &w) {
+// f16 bits of the normalised (clamped) log-Delta feature; *inside: within
+// the training envelope
+__device__ __forceinline__ uint16_t mlp_delta_bits(float delta, const MlpFast &w, bool *inside) {
     float v = (__logf(delta) - w.mean[5]) * w.istd[5];
+    *inside = v >= w.env_lo[5] && v <= w.env_hi[5];
     v = isfinite(v) ? fminf(fmaxf(v, -kFeatClamp), kFeatClamp) : 0.0f;
     return (uint16_t)(pack_f16x2(v, 0.0f) & 0xffffu);
 }

@@ -31,7 +31,8 @@ EXPORTED = (
     "fea_lumped_mass", "fea_field_upload", "fea_assemble_rhs", "fea_assemble_rhs_batched", "fea_periodic_fold",
     "fea_rk_stage", "fea_rk_step_graph", "fea_state_download", "fea_get_plan", "fea_set_plan", "fea_autotune",
     "fea_sync_status", "fea_launch_count", "fea_profile_enable", "fea_profile_read", "fea_rk_stage_noalloc",
-    "fea_mlp_load", "fea_mlp_get", "fea_mlp_forward", "fea_mlp_train_step",
+    "fea_mlp_load", "fea_mlp_get", "fea_mlp_forward", "fea_mlp_train_step", "fea_mlp_set_envelope",
+    "fea_mlp_fallback_read",
 )
 MLP_NPARAM = 8833
 NOALLOC_MAX_NODES = 262144
@@ -99,6 +100,8 @@ def lib() -> ctypes.CDLL:
         L.fea_mlp_get.argtypes = [vp, vp, vp]
         L.fea_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
         L.fea_mlp_train_step.argtypes = [vp, vp, vp, i64, ctypes.c_float, vp, vp, vp]
+        L.fea_mlp_set_envelope.argtypes = [vp, vp, vp, vp]
+        L.fea_mlp_fallback_read.argtypes = [vp, ctypes.POINTER(i64), ctypes.c_int]
         L.fea_rk_stage_noalloc.argtypes = [vp, i32, i32, dbl, ctypes.c_int, ctypes.c_int, dbl, dbl, vp, vp, vp, vp,
                                            vp]
         L.fea_profile_read.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(dbl), ctypes.POINTER(i64),
@@ -181,6 +184,24 @@ class Context:
         self._mlp_keep = arrs
         self.check(self._lib.fea_mlp_load(self.handle, _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]),
                                           float(out_scale), _stream(stream)))
+
+    def mlp_set_envelope(self, lo=None, hi=None, stream=None):
+        """Raw-feature bounds lo [6], hi [6] (None, None: no envelope); outside
+        them the fused closure uses Vreman's nu_t."""
+        if (lo is None) != (hi is None):
+            raise ValueError("give both bounds or neither")
+        if lo is None:
+            self.check(self._lib.fea_mlp_set_envelope(self.handle, None, None, _stream(stream)))
+            return
+        a = np.ascontiguousarray(lo, dtype=np.float32)
+        b = np.ascontiguousarray(hi, dtype=np.float32)
+        self.check(self._lib.fea_mlp_set_envelope(self.handle, _ptr(a), _ptr(b), _stream(stream)))
+
+    def mlp_fallback_read(self, reset: bool = False) -> int:
+        """Gauss-point evaluations that fell back to Vreman since load / last reset."""
+        n = ctypes.c_int64()
+        self.check(self._lib.fea_mlp_fallback_read(self.handle, ctypes.byref(n), 1 if reset else 0))
+        return n.value
 
     def mlp_get(self) -> np.ndarray:
         out = np.zeros(MLP_NPARAM, np.float32)

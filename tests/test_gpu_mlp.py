@@ -207,3 +207,75 @@ def test_batched_assembly_with_mlp_closure(ctx):
         ctx.sync_status()
         a, b = o.cpu().numpy(), single.cpu().numpy()
         assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
+
+
+# ---------------------------------------------------------------------------
+# Vreman as the network's fallback outside the training envelope
+
+def oracle_gp_features(mesh, field):
+    """Raw features of every Gauss point, per element type (E, ng, 6), from
+    the oracle's geometry and feature functions."""
+    out = {}
+    for t, conn in mesh.conn.items():
+        ng = O.NGAUSS[t]
+        F = np.zeros((conn.shape[0], ng, 6))
+        for e in range(conn.shape[0]):
+            _, d, W, _ = O.element_geometry(t, mesh.xyz[conn[e]])
+            U = field.u[conn[e]]
+            delta = W.sum() ** (1.0 / 3.0)
+            for g in range(ng):
+                F[e, g] = O.mlp_features(U.T @ d[g], delta)
+        out[t] = F
+    return out
+
+
+def test_mlp_envelope_falls_back_to_vreman(ctx):
+    rng = np.random.default_rng(8)
+    m = mg.channel_mesh(nx=10, ny=12, nz=8, seed=21, n_layers=2, split_frac=0.3)
+    f = mg.channel_field(m, seed=5, nu=1e-3)
+    theta, mean, std, scale = closure_model(rng, m, f)
+    ctx.mlp_load(theta, mean, std, scale)
+    dm = ctx.upload_mesh(m)
+    dm.upload_field(f.u, f.p, f.nu, f.c_vreman)
+    N, NG = dm.n_nodes, dm.n_gauss_total
+
+    def run(closure):
+        out = torch.empty((3, N), dtype=torch.float64, device="cuda")
+        nut = torch.empty(NG, dtype=torch.float32, device="cuda")
+        dm.assemble(out, prec="mixed", closure=closure, scatter="chunk", nut_out=nut)
+        ctx.sync_status()
+        return out.cpu().numpy(), nut.cpu().numpy()
+
+    r_mlp, n_mlp = run("mlp")
+    r_vre, n_vre = run("vreman")
+    ctx.mlp_fallback_read(reset=True)
+    # an envelope that holds everything changes nothing and counts nothing
+    ctx.mlp_set_envelope(np.full(6, -1e30), np.full(6, 1e30))
+    r, n = run("mlp")
+    assert np.array_equal(r, r_mlp) and np.array_equal(n, n_mlp)
+    assert ctx.mlp_fallback_read(reset=True) == 0
+    # an empty envelope gives the Vreman assembly at every Gauss point
+    ctx.mlp_set_envelope(np.full(6, 1e30), np.full(6, -1e30))
+    r, n = run("mlp")
+    assert ctx.mlp_fallback_read(reset=True) == NG
+    assert np.all(np.abs(n - n_vre) <= 1e-5 * np.abs(n_vre) + 1e-12)
+    assert np.linalg.norm(r - r_vre) <= 1e-6 * np.linalg.norm(r_vre)
+    # a partial envelope on the first feature: each point takes the network's
+    # or Vreman's value according to its own (oracle) feature
+    feats = oracle_gp_features(m, f)
+    x0 = np.concatenate([feats[t][:, :, 0].ravel() for t in range(4) if t in feats])
+    lo0, hi0 = np.quantile(x0, [0.15, 0.85])
+    lo = np.full(6, -1e30)
+    hi = np.full(6, 1e30)
+    lo[0], hi[0] = lo0, hi0
+    ctx.mlp_set_envelope(lo, hi)
+    _, n = run("mlp")
+    count = ctx.mlp_fallback_read(reset=True)
+    inside = (x0 >= lo0) & (x0 <= hi0)
+    clear = np.minimum(np.abs(x0 - lo0), np.abs(x0 - hi0)) > 1e-4 * np.abs(x0).max()
+    assert abs(count - int((~inside).sum())) <= int((~clear).sum())
+    a, b = clear & inside, clear & ~inside
+    assert np.all(np.abs(n[a] - n_mlp[a]) <= 1e-6 * np.abs(n_mlp[a]) + 1e-12)
+    assert np.all(np.abs(n[b] - n_vre[b]) <= 1e-6 * np.abs(n_vre[b]) + 1e-12)
+    assert 0.2 * NG < count < 0.4 * NG
+    ctx.mlp_set_envelope(None, None)
