@@ -228,8 +228,8 @@ def train(ctx: fea.Context, sets: Sequence[CoarseSet], steps: int = 2000, batch:
     """Fits the network to nu_t* on the GPU (the library's training step).
     Each set contributes at most max_per_set seeded random samples, so fine
     filter widths (many coarse elements) do not swamp the coarse ones.  The
-    per-feature [q, 1 - q] quantiles of the training features become the
-    closure's envelope (Vreman outside it)."""
+    per-feature [q, 1 - q] quantiles of the training features, widened by 5 %
+    of their range, become the closure's envelope (Vreman outside it)."""
     rng = np.random.default_rng(seed)
     xs, ys = [], []
     for c in sets:
@@ -274,8 +274,14 @@ def train(ctx: fea.Context, sets: Sequence[CoarseSet], steps: int = 2000, batch:
     ys = yt.double()
     mse = float(((pred.double() / scale - ys) ** 2).mean())
     var = float(ys.var(unbiased=False))
-    lo = np.quantile(x, envelope_q, axis=0).astype(np.float32)
-    hi = np.quantile(x, 1.0 - envelope_q, axis=0).astype(np.float32)
+    lo = np.quantile(x, envelope_q, axis=0)
+    hi = np.quantile(x, 1.0 - envelope_q, axis=0)
+    # widen by 5 % of each range: a feature that takes few distinct values (log
+    # Delta on a uniform grid) must not fail the test by the rounding of the
+    # kernel's own evaluation
+    pad = 0.05 * (hi - lo)
+    lo = (lo - pad).astype(np.float32)
+    hi = (hi + pad).astype(np.float32)
     ctx.mlp_set_envelope(lo, hi)
     return TrainedClosure(theta=ctx.mlp_get(), mean=mean, std=std, scale=scale, losses=losses,
                           fit_mse=mse, target_var=var, n_samples=n, env_lo=lo, env_hi=hi)

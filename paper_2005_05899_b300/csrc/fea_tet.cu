@@ -180,6 +180,137 @@ __device__ __forceinline__ void tet_element(const float4 xs[4], const float4 us[
     }
 }
 
+// ---- TET04 residual, two elements at once (packed FP32, sm_100+) -----------
+// The same arithmetic as tet_element, on float2 lanes (.x: element A, .y:
+// element B) with the paired FP32 instructions (one FFMA2 / FMUL2 / FADD2
+// does the operation of both elements).  Delta^2 = V^(2/3) and
+// sqrt(B'/G:G) = B' rsqrt(B' G:G) use the fast hardware functions.
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_s(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ float vreman_q_fast(float aa, float B) {
+    // c sqrt(B'/G:G) without c; 0 for a vanishing gradient
+    return (B > 0.f && aa > 0.f) ? B * rsqrtf(B * aa) : 0.f;
+}
+
+__device__ __forceinline__ void tet_element_x2(const float4 xa[4], const float4 ua[4], const float4 xb[4],
+                                               const float4 ub[4], const TetParams &tp, float4 ra[4], float4 rb[4],
+                                               float2 &nut, bool &bad) {
+    float2 X[4][3], U[4][3], P[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        X[a][0] = make_float2(xa[a].x, xb[a].x);
+        X[a][1] = make_float2(xa[a].y, xb[a].y);
+        X[a][2] = make_float2(xa[a].z, xb[a].z);
+        U[a][0] = make_float2(ua[a].x, ub[a].x);
+        U[a][1] = make_float2(ua[a].y, ub[a].y);
+        U[a][2] = make_float2(ua[a].z, ub[a].z);
+        P[a] = make_float2(ua[a].w, ub[a].w);
+    }
+    float2 d[3][3], nd[3][3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            d[q][k] = p_sub(X[q + 1][k], X[0][k]);
+            nd[q][k] = p_sub(X[0][k], X[q + 1][k]);
+        }
+    // cofactors: rows of det * J^-1
+    float2 cf[3][3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float2 *a = d[(q + 1) % 3], *b = d[(q + 2) % 3], *nb = nd[(q + 2) % 3];
+        cf[q][0] = p_fma(a[1], b[2], p_mul(a[2], nb[1]));
+        cf[q][1] = p_fma(a[2], b[0], p_mul(a[0], nb[2]));
+        cf[q][2] = p_fma(a[0], b[1], p_mul(a[1], nb[0]));
+    }
+    const float2 det = p_fma(d[0][0], cf[0][0], p_fma(d[0][1], cf[0][1], p_mul(d[0][2], cf[0][2])));
+    if (!(det.x > 0.f) || !(det.y > 0.f)) bad = true;
+    const float2 inv = make_float2(__fdividef(1.f, det.x), __fdividef(1.f, det.y));
+    const float2 V = p_mul(det, p_s(1.f / 6.f));
+    float2 gN[4][3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gN[q + 1][j] = p_mul(cf[q][j], inv);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gN[0][j] = p_mul(p_add(p_add(gN[1][j], gN[2][j]), gN[3][j]), p_s(-1.f));
+    float2 du[3][3], dp[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) du[q][i] = p_sub(U[q + 1][i], U[0][i]);
+        dp[q] = p_sub(P[q + 1], P[0]);
+    }
+    float2 G[3][3], gp[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        gp[j] = p_fma(dp[0], gN[1][j], p_fma(dp[1], gN[2][j], p_mul(dp[2], gN[3][j])));
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            G[i][j] = p_fma(du[0][i], gN[1][j], p_fma(du[1][i], gN[2][j], p_mul(du[2][i], gN[3][j])));
+    }
+    nut = make_float2(0.f, 0.f);
+    if (tp.want_q) {
+        float2 aa = p_s(0.f), B = p_s(0.f);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) aa = p_fma(G[i][j], G[i][j], aa);
+#pragma unroll
+        for (int pq = 0; pq < 3; ++pq) {
+            const int i = pq == 2 ? 1 : 0, j = pq == 0 ? 1 : 2;
+            const float2 x = p_sub(p_mul(G[i][1], G[j][2]), p_mul(G[i][2], G[j][1]));
+            const float2 y = p_sub(p_mul(G[i][2], G[j][0]), p_mul(G[i][0], G[j][2]));
+            const float2 z = p_sub(p_mul(G[i][0], G[j][1]), p_mul(G[i][1], G[j][0]));
+            B = p_fma(x, x, p_fma(y, y, p_fma(z, z, B)));
+        }
+        // Delta^2 = V^(2/3)
+        const float2 d2 = make_float2(__powf(V.x, 2.f / 3.f), __powf(V.y, 2.f / 3.f));
+        nut = p_mul(p_mul(p_s(tp.cv), d2), make_float2(vreman_q_fast(aa.x, B.x), vreman_q_fast(aa.y, B.y)));
+    }
+    // negated coefficients
+    const float2 s2 = p_mul(p_s(-2.f), p_mul(p_add(p_s(tp.nu), tp.sgs ? nut : p_s(0.f)), V));
+    const float2 hs2 = p_mul(s2, p_s(0.5f));
+    float2 ns[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        ns[i][i] = p_mul(s2, G[i][i]);
+#pragma unroll
+        for (int j = i + 1; j < 3; ++j) ns[i][j] = ns[j][i] = p_mul(hs2, p_add(G[i][j], G[j][i]));
+    }
+    const float2 trG = p_add(p_add(G[0][0], G[1][1]), G[2][2]);
+    const float2 nv20 = tp.conv ? p_mul(p_s(-0.05f), V) : p_s(0.f);
+    const float2 nv4 = tp.pres ? p_mul(p_s(-0.25f), V) : p_s(0.f);
+    float2 nA[3][3], c[3];
+    float2 su[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) su[j] = p_add(p_add(U[0][j], U[1][j]), p_add(U[2][j], U[3][j]));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) nA[i][j] = p_mul(nv20, i == j ? p_add(G[i][j], trG) : G[i][j]);
+        // the node-independent part: -V/4 grad p - V/20 A sum_b u_b
+        c[i] = p_fma(nA[i][0], su[0], p_fma(nA[i][1], su[1], p_fma(nA[i][2], su[2], p_mul(nv4, gp[i]))));
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        float2 v[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            v[i] = p_fma(nA[i][0], U[a][0],
+                         p_fma(nA[i][1], U[a][1],
+                               p_fma(nA[i][2], U[a][2],
+                                     p_fma(ns[i][0], gN[a][0],
+                                           p_fma(ns[i][1], gN[a][1], p_fma(ns[i][2], gN[a][2], c[i]))))));
+        ra[a] = make_float4(v[0].x, v[1].x, v[2].x, 0.f);
+        rb[a] = make_float4(v[0].y, v[1].y, v[2].y, 0.f);
+    }
+}
+
 // Residual slot k lives at k + k/8: node ranges of 8 m incidences (24 for the
 // interior nodes of a Kuhn-split grid) would otherwise start on the same
 // float4 bank group in every lane of the node phase.
@@ -191,7 +322,8 @@ __device__ __forceinline__ int swz(int k) { return k + (k >> 3); }
 // [LM] and element records [C] (4 local node ids + 4 incidence positions),
 // then three mbarriers.  Iteration i computes chunk c_i while the TMA engine
 // loads chunk c_{i+2} and cp.async gathers the field values of c_{i+1}.
-template <int T>
+// PAIR: each thread computes elements el and el + T together (packed FP32).
+template <int T, bool PAIR>
 __global__ void __launch_bounds__(T) k_tet_pipe(BucketDev b, FieldDev f, AsmArgs args, TetParams tp) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int C = b.chunk_elems, LM = b.max_chunk_nodes;
@@ -267,23 +399,62 @@ __global__ void __launch_bounds__(T) k_tet_pipe(BucketDev b, FieldDev f, AsmArgs
         const float4 *rec = REC(q);
         const float4 *up = UP(q);
         const uint4 *elr = ELR(q);
-        for (int el = tid; el < ne; el += T) {
-            const uint4 er = elr[el];
-            const int li[4] = {(int)(er.x & 0xffffu), (int)(er.x >> 16), (int)(er.y & 0xffffu), (int)(er.y >> 16)};
-            const int ps[4] = {(int)(er.z & 0xffffu), (int)(er.z >> 16), (int)(er.w & 0xffffu), (int)(er.w >> 16)};
-            float4 xs[4], us[4], r[4];
+        if constexpr (PAIR) {
+            for (int el = tid; el < ne; el += 2 * T) {
+                const int elb = el + T;
+                const bool hasb = elb < ne;
+                const uint4 era = elr[el], erb = elr[hasb ? elb : el];
+                const int la[4] = {(int)(era.x & 0xffffu), (int)(era.x >> 16), (int)(era.y & 0xffffu),
+                                   (int)(era.y >> 16)};
+                const int lb[4] = {(int)(erb.x & 0xffffu), (int)(erb.x >> 16), (int)(erb.y & 0xffffu),
+                                   (int)(erb.y >> 16)};
+                float4 xa[4], ua[4], xb[4], ub[4], ra[4], rb[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                xs[a] = rec[li[a]];
-                us[a] = up[li[a]];
+                for (int a = 0; a < 4; ++a) {
+                    xa[a] = rec[la[a]];
+                    ua[a] = up[la[a]];
+                    xb[a] = rec[lb[a]];
+                    ub[a] = up[lb[a]];
+                }
+                float2 nut;
+                tet_element_x2(xa, ua, xb, ub, tp, ra, rb, nut, bad);
+                sR[swz((int)(era.z & 0xffffu))] = ra[0];
+                sR[swz((int)(era.z >> 16))] = ra[1];
+                sR[swz((int)(era.w & 0xffffu))] = ra[2];
+                sR[swz((int)(era.w >> 16))] = ra[3];
+                if (hasb) {
+                    sR[swz((int)(erb.z & 0xffffu))] = rb[0];
+                    sR[swz((int)(erb.z >> 16))] = rb[1];
+                    sR[swz((int)(erb.w & 0xffffu))] = rb[2];
+                    sR[swz((int)(erb.w >> 16))] = rb[3];
+                }
+                if (args.nut) {
+                    float4 *nu4 = reinterpret_cast<float4 *>(args.nut);
+                    nu4[__ldg(&b.orig[e0 + el])] = make_float4(nut.x, nut.x, nut.x, nut.x);
+                    if (hasb) nu4[__ldg(&b.orig[e0 + elb])] = make_float4(nut.y, nut.y, nut.y, nut.y);
+                }
             }
-            float nut;
-            tet_element(xs, us, tp, r, nut, bad);
+        } else {
+            for (int el = tid; el < ne; el += T) {
+                const uint4 er = elr[el];
+                const int li[4] = {(int)(er.x & 0xffffu), (int)(er.x >> 16), (int)(er.y & 0xffffu),
+                                   (int)(er.y >> 16)};
+                const int ps[4] = {(int)(er.z & 0xffffu), (int)(er.z >> 16), (int)(er.w & 0xffffu),
+                                   (int)(er.w >> 16)};
+                float4 xs[4], us[4], r[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) sR[swz(ps[a])] = r[a];
-            if (args.nut) {
-                const int64_t o = (int64_t)__ldg(&b.orig[e0 + el]);
-                reinterpret_cast<float4 *>(args.nut)[o] = make_float4(nut, nut, nut, nut);
+                for (int a = 0; a < 4; ++a) {
+                    xs[a] = rec[li[a]];
+                    us[a] = up[li[a]];
+                }
+                float nut;
+                tet_element(xs, us, tp, r, nut, bad);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) sR[swz(ps[a])] = r[a];
+                if (args.nut) {
+                    const int64_t o = (int64_t)__ldg(&b.orig[e0 + el]);
+                    reinterpret_cast<float4 *>(args.nut)[o] = make_float4(nut, nut, nut, nut);
+                }
             }
         }
         __syncthreads();
@@ -361,9 +532,11 @@ cudaError_t launch_tet_pipe(const BucketDev &b, const FieldDev &f, const AsmArgs
         kern<<<(unsigned)grid, T, smem, s>>>(b, f, a, tp);
         return cudaGetLastError();
     };
-    if (threads >= 512) return launch(k_tet_pipe<512>, 512);
-    if (threads >= 256) return launch(k_tet_pipe<256>, 256);
-    return launch(k_tet_pipe<128>, 128);
+    // two elements per thread whenever every thread has at least two
+    const bool pair = b.chunk_elems >= 2 * threads;
+    if (threads >= 512) return pair ? launch(k_tet_pipe<512, true>, 512) : launch(k_tet_pipe<512, false>, 512);
+    if (threads >= 256) return pair ? launch(k_tet_pipe<256, true>, 256) : launch(k_tet_pipe<256, false>, 256);
+    return pair ? launch(k_tet_pipe<128, true>, 128) : launch(k_tet_pipe<128, false>, 128);
 }
 
 }  // namespace fea

@@ -186,6 +186,26 @@ def test_chunk_scatter_matches_oracle(ctx, mixed_small, chunk_elems, threads, ac
     assert l2 < MIXED_L2 and mx < MIXED_MAX
 
 
+@pytest.mark.parametrize("mask", [fea.TERM_ALL, fea.TERM_CONV, fea.TERM_SGS])
+def test_tet_two_per_thread_matches_oracle(ctx, mask):
+    """TET04 chunk kernel with two elements per thread (C >= 2T), on a mesh
+    whose last chunk is ragged (20,250 tets = 39 chunks of 512 + 282), against
+    the oracle; nu_t against the one-element-per-thread plan."""
+    m = mg.tgv_mesh(15)
+    f = mg.tgv_field(m)
+    dm = ctx.upload_mesh(m)
+    dm.set_plan("chunk", 128, 512, 0)
+    r2, nut2, _ = gpu_rhs(ctx, m, f, "mixed", mask=mask, scatter="chunk", want_nut=True, dm=dm)
+    ref, nref = oracle_rhs(m, f, mask=mask, want_nut=True)
+    l2, mx = errors(r2, ref)
+    assert l2 < MIXED_L2 and mx < MIXED_MAX, (l2, mx)
+    dm.set_plan("chunk", 256, 256, 0)
+    r1, nut1, _ = gpu_rhs(ctx, m, f, "mixed", mask=mask, scatter="chunk", want_nut=True, dm=dm)
+    assert errors(r1, ref)[0] < MIXED_L2
+    assert np.allclose(nut2, nut1, rtol=1e-5, atol=1e-12)
+    assert np.allclose(nut2, nref[fea.TET04].ravel(), rtol=1e-4, atol=1e-12)
+
+
 def test_atomic_and_chunk_agree_and_nut_identical(ctx, mixed_small):
     m, f = mixed_small
     dm = ctx.upload_mesh(m)
