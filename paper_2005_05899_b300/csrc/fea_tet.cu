@@ -87,8 +87,16 @@ struct TetParams {
     bool conv, pres, sgs, want_q;
 };
 
-__device__ __forceinline__ void tet_element(const float4 xs[4], const float4 us[4], const TetParams &tp, float4 r[4],
+__device__ __forceinline__ float vreman_q_fast(float aa, float B) {
+    // c sqrt(B'/G:G) without c; 0 for a vanishing gradient
+    return (B > 0.f && aa > 0.f) ? B * rsqrtf(B) * rsqrtf(aa) : 0.f;
+}
+
+template <bool FULL>
+__device__ __forceinline__ void tet_element(const float4 xs[4], const float4 us[4], const TetParams &tp_in, float4 r[4],
                                             float &nut, bool &bad) {
+    TetParams tp = tp_in;
+    if (FULL) tp.conv = tp.pres = tp.sgs = tp.want_q = true;
     float d[3][3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -142,10 +150,8 @@ __device__ __forceinline__ void tet_element(const float4 xs[4], const float4 us[
             const float z = G[i][0] * G[j][1] - G[i][1] * G[j][0];
             B += x * x + y * y + z * z;
         }
-        if (B > 0.f && aa > 0.f) {
-            const float dl = cbrtf(V);
-            nut = tp.cv * dl * dl * (B * rsqrtf(B)) * rsqrtf(aa);
-        }
+        // Delta^2 = V^(2/3); c sqrt(B'/G:G) = c B' rsqrt(B' G:G)
+        nut = tp.cv * __powf(fabsf(V), 2.f / 3.f) * vreman_q_fast(aa, B);
     }
     // negated coefficients
     const float s2 = -2.f * (tp.nu + (tp.sgs ? nut : 0.f)) * V;
@@ -191,14 +197,12 @@ __device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(
 __device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 p_s(float v) { return make_float2(v, v); }
 
-__device__ __forceinline__ float vreman_q_fast(float aa, float B) {
-    // c sqrt(B'/G:G) without c; 0 for a vanishing gradient
-    return (B > 0.f && aa > 0.f) ? B * rsqrtf(B * aa) : 0.f;
-}
-
+template <bool FULL>
 __device__ __forceinline__ void tet_element_x2(const float4 xa[4], const float4 ua[4], const float4 xb[4],
-                                               const float4 ub[4], const TetParams &tp, float4 ra[4], float4 rb[4],
+                                               const float4 ub[4], const TetParams &tp_in, float4 ra[4], float4 rb[4],
                                                float2 &nut, bool &bad) {
+    TetParams tp = tp_in;
+    if (FULL) tp.conv = tp.pres = tp.sgs = tp.want_q = true;
     float2 X[4][3], U[4][3], P[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -269,7 +273,7 @@ __device__ __forceinline__ void tet_element_x2(const float4 xa[4], const float4 
             B = p_fma(x, x, p_fma(y, y, p_fma(z, z, B)));
         }
         // Delta^2 = V^(2/3)
-        const float2 d2 = make_float2(__powf(V.x, 2.f / 3.f), __powf(V.y, 2.f / 3.f));
+        const float2 d2 = make_float2(__powf(fabsf(V.x), 2.f / 3.f), __powf(fabsf(V.y), 2.f / 3.f));
         nut = p_mul(p_mul(p_s(tp.cv), d2), make_float2(vreman_q_fast(aa.x, B.x), vreman_q_fast(aa.y, B.y)));
     }
     // negated coefficients
@@ -323,7 +327,8 @@ __device__ __forceinline__ int swz(int k) { return k + (k >> 3); }
 // then three mbarriers.  Iteration i computes chunk c_i while the TMA engine
 // loads chunk c_{i+2} and cp.async gathers the field values of c_{i+1}.
 // PAIR: each thread computes elements el and el + T together (packed FP32).
-template <int T, bool PAIR>
+// FULL: all terms with the Vreman closure (the flags fold at compile time).
+template <int T, bool PAIR, bool FULL>
 __global__ void __launch_bounds__(T) k_tet_pipe(BucketDev b, FieldDev f, AsmArgs args, TetParams tp) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int C = b.chunk_elems, LM = b.max_chunk_nodes;
@@ -386,13 +391,15 @@ __global__ void __launch_bounds__(T) k_tet_pipe(BucketDev b, FieldDev f, AsmArgs
             else
                 atomicExch(abort_flag, 1);
         }
-        if (tid == 0) issue_tma(c + 2 * G, q2);
         if (more)
             cp_async_wait<1>();
         else
             cp_async_wait<0>();
         __syncthreads();
         if (*abort_flag) break;
+        // stage q2 last held chunk i-1, whose node phase every thread has
+        // finished before the barrier above: it can be refilled now
+        if (tid == 0) issue_tma(c + 2 * G, q2);
         // B: element residuals into their node-sorted incidence positions
         const int64_t e0 = c * C;
         const int ne = (int)min((int64_t)C, b.count - e0);
@@ -417,7 +424,7 @@ __global__ void __launch_bounds__(T) k_tet_pipe(BucketDev b, FieldDev f, AsmArgs
                     ub[a] = up[lb[a]];
                 }
                 float2 nut;
-                tet_element_x2(xa, ua, xb, ub, tp, ra, rb, nut, bad);
+                tet_element_x2<FULL>(xa, ua, xb, ub, tp, ra, rb, nut, bad);
                 sR[swz((int)(era.z & 0xffffu))] = ra[0];
                 sR[swz((int)(era.z >> 16))] = ra[1];
                 sR[swz((int)(era.w & 0xffffu))] = ra[2];
@@ -448,7 +455,7 @@ __global__ void __launch_bounds__(T) k_tet_pipe(BucketDev b, FieldDev f, AsmArgs
                     us[a] = up[li[a]];
                 }
                 float nut;
-                tet_element(xs, us, tp, r, nut, bad);
+                tet_element<FULL>(xs, us, tp, r, nut, bad);
 #pragma unroll
                 for (int a = 0; a < 4; ++a) sR[swz(ps[a])] = r[a];
                 if (args.nut) {
@@ -458,7 +465,9 @@ __global__ void __launch_bounds__(T) k_tet_pipe(BucketDev b, FieldDev f, AsmArgs
             }
         }
         __syncthreads();
-        // C: node sums -> FP64 global RHS (store if exclusive, else atomic add)
+        // C: node sums -> FP64 global RHS (store if exclusive, else atomic add).
+        // The next iteration's first barrier orders this phase before the
+        // residual slots and this stage's buffers are written again.
         const int L = b.chunk_nodes[c];
         const uint32_t *rng = RNG(q);
         for (int j = tid; j < L; j += T) {
@@ -485,7 +494,6 @@ __global__ void __launch_bounds__(T) k_tet_pipe(BucketDev b, FieldDev f, AsmArgs
                 r0[2 * f.n] = v2;
             }
         }
-        __syncthreads();
     }
     if (bad) atomicOr(args.err, ERR_DETJ);
     cp_async_wait<0>();
@@ -534,9 +542,14 @@ cudaError_t launch_tet_pipe(const BucketDev &b, const FieldDev &f, const AsmArgs
     };
     // two elements per thread whenever every thread has at least two
     const bool pair = b.chunk_elems >= 2 * threads;
-    if (threads >= 512) return pair ? launch(k_tet_pipe<512, true>, 512) : launch(k_tet_pipe<512, false>, 512);
-    if (threads >= 256) return pair ? launch(k_tet_pipe<256, true>, 256) : launch(k_tet_pipe<256, false>, 256);
-    return pair ? launch(k_tet_pipe<128, true>, 128) : launch(k_tet_pipe<128, false>, 128);
+    const bool full = tp.conv && tp.pres && tp.sgs && tp.want_q;
+#define FEA_TET_LAUNCH(TT)                                                                             \
+    return pair ? (full ? launch(k_tet_pipe<TT, true, true>, TT) : launch(k_tet_pipe<TT, true, false>, TT)) \
+                : (full ? launch(k_tet_pipe<TT, false, true>, TT) : launch(k_tet_pipe<TT, false, false>, TT))
+    if (threads >= 512) FEA_TET_LAUNCH(512);
+    if (threads >= 256) FEA_TET_LAUNCH(256);
+    FEA_TET_LAUNCH(128);
+#undef FEA_TET_LAUNCH
 }
 
 }  // namespace fea
