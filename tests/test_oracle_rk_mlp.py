@@ -182,3 +182,23 @@ def test_mlp_features_closed_forms_and_invariance():
     G = rng.standard_normal((3, 3))
     q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
     assert np.allclose(O.mlp_features(q @ G @ q.T, 0.3), O.mlp_features(G, 0.3), rtol=1e-12, atol=1e-13)
+
+
+def test_mlp_closure_with_constant_output_is_a_viscosity():
+    """With all weights zero the network's output is the constant
+    s softplus(b4): the MLP closure's subgrid term must then equal the
+    viscous term with nu replaced by that constant, element type by type
+    (the 2 eps form is linear in the viscosity)."""
+    m = mg.channel_mesh(nx=6, ny=8, nz=4, seed=3, n_layers=2, split_frac=0.3)
+    assert len(m.conn) == 4
+    f = mg.channel_field(m, seed=2, nu=1e-3)
+    theta = np.zeros(O.nparam())
+    theta[-1] = 0.3
+    scale = 2e-4
+    mlp = O.MLPParams(theta, np.zeros(6), np.ones(6), out_scale=scale)
+    nut = scale * math.log1p(math.exp(0.3))
+    om = O.OracleMesh.of(m)
+    sgs, nut_gp = O.assemble_rhs(om, f.u, f.p, f.nu, f.c_vreman, "mlp", mask=O.TERM_SGS, mlp=mlp, want_nut=True)
+    visc = O.assemble_rhs(om, f.u, f.p, f.nu, f.c_vreman, "none", mask=O.TERM_VISC)
+    assert all(np.allclose(v, nut, rtol=1e-14, atol=0) for v in nut_gp.values())
+    assert np.abs(sgs - visc * (nut / f.nu)).max() <= 1e-12 * np.abs(visc * (nut / f.nu)).max()
