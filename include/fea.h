@@ -257,6 +257,47 @@ fea_status fea_mlp_forward(fea_ctx *ctx, const float *x, int64_t B, float *nut, 
 fea_status fea_mlp_train_step(fea_ctx *ctx, const float *x, const float *y, int64_t B, float lr, float *loss_out,
                               float *grad_out, void *stream);
 
+/* ---- a mesh partitioned over several devices ----------------------------
+ * Section 5: the mesh is split along a space-filling curve into parts of
+ * (nearly) equal cost; each device assembles its part; after the assembly
+ * the contributions at nodes shared by parts are summed (the per-stage
+ * exchange of section 2.3.1).  A "class" is a set of node copies that must
+ * end with one value: a node shared by parts together with its periodic
+ * copies, so that the periodic fold across parts is the same sum. */
+
+/* Space-filling-curve order of n points xyz [3][n] (host): the points are
+ * binned on a regular grid of 2^level cells per axis over their bounding box
+ * and ordered along a Hilbert curve through the cells; points of one cell
+ * keep their input order.  order [n] (host) receives the permutation.
+ * level in [1, 21].  Host only (no device call, no context).
+ * Errors: FEA_EINVAL. */
+fea_status fea_sfc_order(int64_t n, const double *xyz, int32_t level, int64_t *order);
+
+/* SFC partition of a mesh's elements into nparts parts (section 5, the
+ * partitioner's steps): element location = centroid, weight = Gauss points
+ * of the element's rule (TET04 4, PYR05 8, PEN06 6, HEX08 8), bins of a
+ * 2^level grid ordered along the Hilbert curve, the weighted 1-D sequence
+ * cut into nparts contiguous runs of nearly equal weight (each bin goes to
+ * the part holding the midpoint of its weight interval).  part[t]
+ * [n_elem[t]] (host) receives part ids in [0, nparts).  Host only.
+ * Errors: FEA_EINVAL (nparts < 1, level out of [1, 21], NULL arrays),
+ * FEA_EMESH (node index out of range). */
+fea_status fea_partition_sfc(const fea_mesh_desc *desc, int32_t nparts, int32_t level, int32_t *const part[4]);
+
+/* Interface pack: out [3][n_class] (device) is zeroed, then
+ * out[c][cls[k]] += v[c][loc[k]] for k < m, c < 3, with v [3][n] (device,
+ * FP64, the RHS layout) and loc, cls [m] (device, int64).  Summing out over
+ * all parts (e.g. an all-reduce) and unpacking gives every copy of a class
+ * the class total.  Out-of-range indices are skipped and reported by
+ * fea_sync_status (FEA_EMESH).  Asynchronous on stream. */
+fea_status fea_interface_pack(fea_ctx *ctx, const double *v, int64_t n, const int64_t *loc, const int64_t *cls,
+                              int64_t m, double *out, int64_t n_class, void *stream);
+
+/* Interface unpack: v[c][loc[k]] = in[c][cls[k]] for k < m, c < 3 (all
+ * device memory; in [3][n_class]).  Asynchronous on stream. */
+fea_status fea_interface_unpack(fea_ctx *ctx, const double *in, int64_t n_class, const int64_t *loc,
+                                const int64_t *cls, int64_t m, double *v, int64_t n, void *stream);
+
 /* Allocation-free RK stage (no counterpart in the paper).
  *
  * For callers that cannot allocate device memory at call time -- code that
@@ -290,9 +331,12 @@ fea_status fea_get_plan(fea_ctx *ctx, int32_t mesh, fea_plan *plan);
 fea_status fea_set_plan(fea_ctx *ctx, int32_t mesh, const fea_plan *plan);
 
 /* Times the candidate plans of one mesh (after a field upload) with CUDA
- * events and keeps the fastest; with cache_path != NULL the result is read
- * from / appended to that text file, keyed by device name and mesh
- * statistics.  Synchronous. */
+ * events and keeps the fastest.  With cache_path != NULL, a text file of
+ * lines "key scatter threads chunk_elems chunk_acc ms" keyed by device name,
+ * node and element counts, precision and closure: a matching line (the last
+ * one) is applied through fea_set_plan instead of timing; otherwise the
+ * result is appended.  Synchronous.  Errors: FEA_ESTATE (no field), the
+ * errors of fea_set_plan for a cached plan, FEA_EINVAL (cache not writable). */
 fea_status fea_autotune(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure closure, const char *cache_path);
 
 /* Synchronises the stream, then reads and clears the device error word:

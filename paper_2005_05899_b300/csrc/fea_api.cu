@@ -334,15 +334,6 @@ fea_status get_mesh(fea_ctx *ctx, int32_t id, Mesh **m) {
     return FEA_OK;
 }
 
-uint64_t spread3(uint64_t v) {
-    v &= 0x1FFFFFull;
-    v = (v | (v << 32)) & 0x1F00000000FFFFull;
-    v = (v | (v << 16)) & 0x1F0000FF0000FFull;
-    v = (v | (v << 8)) & 0x100F00F00F00F00Full;
-    v = (v | (v << 4)) & 0x10C30C30C30C30C3ull;
-    v = (v | (v << 2)) & 0x1249249249249249ull;
-    return v;
-}
 
 int64_t type_nut_offset(const Mesh &m, int et) {
     int64_t off = 0;
@@ -749,7 +740,7 @@ fea_status fea_mesh_upload(fea_ctx *ctx, const fea_mesh_desc *d, void *stream, i
                 for (int i = 0; i < 3; ++i) {
                     double q = (c[i] / nen - lo[i]) * scale[i];
                     q = std::min(std::max(q, 0.0), double((1u << 21) - 1));
-                    key |= spread3((uint64_t)q) << i;
+                    key |= morton_spread3((uint64_t)q) << i;
                 }
                 keys.emplace_back(key, (int32_t)e);
             }
@@ -1117,7 +1108,37 @@ fea_status fea_autotune(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure c
     if (st) return st;
     if ((st = check_args(ctx, prec, closure, FEA_TERM_ALL))) return st;
     if (!m->has_field) return fail(ctx, FEA_ESTATE, "no field uploaded for mesh %d", mesh);
-    (void)cache_path;
+    // cache key: device name and mesh statistics, then precision and closure
+    std::string key;
+    if (cache_path) {
+        cudaDeviceProp prop;
+        CK(cudaGetDeviceProperties(&prop, ctx->device));
+        std::string dev(prop.name);
+        for (char &ch : dev)
+            if (ch == ' ' || ch == '\t') ch = '_';
+        char buf[640];
+        snprintf(buf, sizeof buf, "%s|nodes=%lld|elems=%lld,%lld,%lld,%lld|prec=%d|closure=%d", dev.c_str(),
+                 (long long)m->n, (long long)m->n_elem[0], (long long)m->n_elem[1], (long long)m->n_elem[2],
+                 (long long)m->n_elem[3], (int)prec, (int)closure);
+        key = buf;
+        if (FILE *f = fopen(cache_path, "r")) {
+            char line[1024];
+            fea_plan cached{};
+            bool hit = false;
+            while (fgets(line, sizeof line, f)) {
+                char k[700];
+                fea_plan p{};
+                if (sscanf(line, "%699s %d %d %d %d", k, &p.scatter, &p.threads_per_block, &p.chunk_elems,
+                           &p.chunk_acc) == 5 &&
+                    key == k) {
+                    cached = p;   // the last entry for a key wins
+                    hit = true;
+                }
+            }
+            fclose(f);
+            if (hit) return fea_set_plan(ctx, mesh, &cached);
+        }
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1161,6 +1182,13 @@ fea_status fea_autotune(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure c
     if (best.scatter == FEA_SCATTER_CHUNK && (st = ensure_chunks(ctx, *m, best.chunk_elems))) return st;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "a");
+        if (!f) return fail(ctx, FEA_EINVAL, "cannot append to autotune cache %s", cache_path);
+        fprintf(f, "%s %d %d %d %d %.6f\n", key.c_str(), best.scatter, best.threads_per_block, best.chunk_elems,
+                best.chunk_acc, (double)best_ms / 5.0);
+        fclose(f);
+    }
     m->plan = best;
     if (m->graph.exec) {
         cudaGraphExecDestroy(m->graph.exec);
@@ -1207,6 +1235,28 @@ fea_status fea_mlp_load(fea_ctx *ctx, const float *theta, const float *feat_mean
     ctx->mlp_step = 0;
     ctx->mlp_scale = out_scale;
     ctx->mlp_ready = true;
+    return FEA_OK;
+}
+
+fea_status fea_interface_pack(fea_ctx *ctx, const double *v, int64_t n, const int64_t *loc, const int64_t *cls,
+                              int64_t m, double *out, int64_t n_class, void *stream) {
+    if (!ctx) return FEA_EINVAL;
+    if (n < 0 || m < 0 || n_class < 0 || (m > 0 && (!v || !loc || !cls)) || (n_class > 0 && !out))
+        return fail(ctx, FEA_EINVAL, "bad interface pack arguments");
+    CK(cudaSetDevice(ctx->device));
+    CK(launch_iface_pack(v, n, loc, cls, m, out, n_class, ctx->d_err, ctx->sms, (cudaStream_t)stream));
+    ctx->launches += m > 0 ? 1 : 0;
+    return FEA_OK;
+}
+
+fea_status fea_interface_unpack(fea_ctx *ctx, const double *in, int64_t n_class, const int64_t *loc,
+                                const int64_t *cls, int64_t m, double *v, int64_t n, void *stream) {
+    if (!ctx) return FEA_EINVAL;
+    if (n < 0 || m < 0 || n_class < 0 || (m > 0 && (!v || !loc || !cls || !in)))
+        return fail(ctx, FEA_EINVAL, "bad interface unpack arguments");
+    CK(cudaSetDevice(ctx->device));
+    CK(launch_iface_unpack(in, n_class, loc, cls, m, v, n, ctx->d_err, ctx->sms, (cudaStream_t)stream));
+    ctx->launches += m > 0 ? 1 : 0;
     return FEA_OK;
 }
 

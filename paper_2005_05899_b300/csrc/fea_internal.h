@@ -116,6 +116,16 @@ cudaError_t launch_pack_field(int64_t n, const double *u64, const double *p64, f
 cudaError_t launch_f32_to_f64(const float *src, double *dst, int64_t count, cudaStream_t s);
 cudaError_t launch_recip(const double *m, double *minv, int64_t n, cudaStream_t s);
 
+// interface exchange of a partitioned mesh (fea_kernels.cu)
+cudaError_t launch_iface_pack(const double *v, int64_t n, const int64_t *loc, const int64_t *cls, int64_t m,
+                              double *out, int64_t nc, unsigned *err, int sms, cudaStream_t s);
+cudaError_t launch_iface_unpack(const double *in, int64_t nc, const int64_t *loc, const int64_t *cls, int64_t m,
+                                double *v, int64_t n, unsigned *err, int sms, cudaStream_t s);
+
+// space-filling curves (fea_partition.cu)
+uint64_t morton_spread3(uint64_t v);                              // 21 bits -> every third bit
+uint64_t hilbert_key3(uint32_t x0, uint32_t x1, uint32_t x2, int bits);   // Hilbert index in a 2^bits grid
+
 // MLP closure (fea_mlp.cu)
 size_t mlp_weights_bytes();
 const void *mlp_fast_ptr(const void *w);   // inference layout inside the weights block

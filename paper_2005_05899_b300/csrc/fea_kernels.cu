@@ -833,6 +833,55 @@ cudaError_t launch_assemble_batch(const void *buckets, const void *fields, const
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Interface exchange of a partitioned mesh: classes of node copies that must
+// end with one value (a node shared by parts, with its periodic copies).
+// pack: out[c][cls[k]] += v[c][loc[k]]; unpack: v[c][loc[k]] = in[c][cls[k]].
+// Out-of-range indices are skipped and flagged (ERR_INDEX).
+
+__global__ void k_iface_pack(const double *v, int64_t n, const int64_t *loc, const int64_t *cls, int64_t m,
+                             double *out, int64_t nc, unsigned *err) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = loc[k], c = cls[k];
+        if (i < 0 || i >= n || c < 0 || c >= nc) {
+            set_err(err, ERR_INDEX);
+            continue;
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) atomicAdd(&out[d * nc + c], v[d * n + i]);
+    }
+}
+
+__global__ void k_iface_unpack(const double *in, int64_t nc, const int64_t *loc, const int64_t *cls, int64_t m,
+                               double *v, int64_t n, unsigned *err) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = loc[k], c = cls[k];
+        if (i < 0 || i >= n || c < 0 || c >= nc) {
+            set_err(err, ERR_INDEX);
+            continue;
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) v[d * n + i] = in[d * nc + c];
+    }
+}
+
+cudaError_t launch_iface_pack(const double *v, int64_t n, const int64_t *loc, const int64_t *cls, int64_t m,
+                              double *out, int64_t nc, unsigned *err, int sms, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * 3 * (size_t)nc, s);
+    if (e != cudaSuccess || m == 0) return e;
+    const int64_t grid = std::min<int64_t>((m + 255) / 256, (int64_t)sms * 8);
+    k_iface_pack<<<(unsigned)grid, 256, 0, s>>>(v, n, loc, cls, m, out, nc, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iface_unpack(const double *in, int64_t nc, const int64_t *loc, const int64_t *cls, int64_t m,
+                                double *v, int64_t n, unsigned *err, int sms, cudaStream_t s) {
+    if (m == 0) return cudaSuccess;
+    const int64_t grid = std::min<int64_t>((m + 255) / 256, (int64_t)sms * 8);
+    k_iface_unpack<<<(unsigned)grid, 256, 0, s>>>(in, nc, loc, cls, m, v, n, err);
+    return cudaGetLastError();
+}
+
 size_t batch_item_bytes() { return sizeof(BatchItem); }
 
 // zero the RHS of every mesh of a batch in one launch: blockIdx.y = mesh

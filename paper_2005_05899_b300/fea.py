@@ -32,10 +32,65 @@ EXPORTED = (
     "fea_rk_stage", "fea_rk_step_graph", "fea_state_download", "fea_get_plan", "fea_set_plan", "fea_autotune",
     "fea_sync_status", "fea_launch_count", "fea_profile_enable", "fea_profile_read", "fea_rk_stage_noalloc",
     "fea_mlp_load", "fea_mlp_get", "fea_mlp_forward", "fea_mlp_train_step", "fea_mlp_set_envelope",
-    "fea_mlp_fallback_read",
+    "fea_mlp_fallback_read", "fea_sfc_order", "fea_partition_sfc", "fea_interface_pack", "fea_interface_unpack",
 )
 MLP_NPARAM = 8833
 NOALLOC_MAX_NODES = 262144
+
+
+def mesh_desc(mesh):
+    """fea_mesh_desc of a meshgen.Mesh-like object; returns (desc, the arrays
+    it points to (keep them alive), elements per type)."""
+    xyz = np.ascontiguousarray(np.asarray(mesh.xyz, dtype=np.float64).T)
+    keep = [xyz]
+    d = MeshDesc()
+    d.n_nodes = xyz.shape[1]
+    d.xyz = xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    n_elem = [0, 0, 0, 0]
+    for t in range(4):
+        c = mesh.conn.get(t)
+        if c is not None and len(c):
+            c = np.ascontiguousarray(c, dtype=np.int32)
+            keep.append(c)
+            d.conn[t] = c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            d.n_elem[t] = c.shape[0]
+            n_elem[t] = c.shape[0]
+        f = getattr(mesh, "fp64_flag", {}).get(t) if getattr(mesh, "fp64_flag", None) else None
+        if f is not None and len(f):
+            f = np.ascontiguousarray(f, dtype=np.uint8)
+            keep.append(f)
+            d.fp64_jac[t] = f.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    if getattr(mesh, "periodic_master", None) is not None:
+        pm = np.ascontiguousarray(mesh.periodic_master, dtype=np.int32)
+        keep.append(pm)
+        d.periodic_master = pm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    if getattr(mesh, "dirichlet", None) is not None:
+        dm = np.ascontiguousarray(mesh.dirichlet, dtype=np.uint8)
+        keep.append(dm)
+        d.dirichlet = dm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    return d, keep, n_elem
+
+
+def sfc_order(xyz, level: int = 10) -> np.ndarray:
+    """Hilbert-curve order of points xyz (N, 3) binned on a 2^level grid (host)."""
+    x = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).T)
+    n = x.shape[1]
+    out = np.empty(n, np.int64)
+    st = lib().fea_sfc_order(n, x.ctypes.data_as(ctypes.c_void_p), int(level), out.ctypes.data_as(ctypes.c_void_p))
+    if st:
+        raise FeaError(st, "fea_sfc_order failed")
+    return out
+
+
+def partition_sfc(mesh, nparts: int, level: int = 10) -> dict:
+    """SFC partition of the elements: {etype: part id per element} (host)."""
+    d, keep, n_elem = mesh_desc(mesh)
+    parts = {t: np.zeros(n_elem[t], np.int32) for t in range(4)}
+    ptrs = (ctypes.c_void_p * 4)(*[parts[t].ctypes.data if n_elem[t] else None for t in range(4)])
+    st = lib().fea_partition_sfc(ctypes.byref(d), int(nparts), int(level), ptrs)
+    if st:
+        raise FeaError(st, "fea_partition_sfc failed")
+    return {t: parts[t] for t in range(4) if n_elem[t]}
 
 
 class FeaError(RuntimeError):
@@ -101,6 +156,10 @@ def lib() -> ctypes.CDLL:
         L.fea_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
         L.fea_mlp_train_step.argtypes = [vp, vp, vp, i64, ctypes.c_float, vp, vp, vp]
         L.fea_mlp_set_envelope.argtypes = [vp, vp, vp, vp]
+        L.fea_sfc_order.argtypes = [i64, vp, i32, vp]
+        L.fea_partition_sfc.argtypes = [ctypes.POINTER(MeshDesc), i32, i32, ctypes.c_void_p * 4]
+        L.fea_interface_pack.argtypes = [vp, vp, i64, vp, vp, i64, vp, i64, vp]
+        L.fea_interface_unpack.argtypes = [vp, vp, i64, vp, vp, i64, vp, i64, vp]
         L.fea_mlp_fallback_read.argtypes = [vp, ctypes.POINTER(i64), ctypes.c_int]
         L.fea_rk_stage_noalloc.argtypes = [vp, i32, i32, dbl, ctypes.c_int, ctypes.c_int, dbl, dbl, vp, vp, vp, vp,
                                            vp]
@@ -185,6 +244,20 @@ class Context:
         self.check(self._lib.fea_mlp_load(self.handle, _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]),
                                           float(out_scale), _stream(stream)))
 
+    # ---- interface exchange of a partitioned mesh ----
+    def interface_pack(self, v, loc, cls, out, stream=None):
+        """v: float64 device [3][n]; loc, cls: int64 device [m]; out: float64
+        device [3][n_class] (zeroed, then the class sums of this part)."""
+        self.check(self._lib.fea_interface_pack(self.handle, _ptr(v), int(v.shape[1]), _ptr(loc), _ptr(cls),
+                                                int(loc.shape[0]), _ptr(out), int(out.shape[1]), _stream(stream)))
+        return out
+
+    def interface_unpack(self, buf, loc, cls, v, stream=None):
+        """v[:, loc[k]] = buf[:, cls[k]] (all device)."""
+        self.check(self._lib.fea_interface_unpack(self.handle, _ptr(buf), int(buf.shape[1]), _ptr(loc), _ptr(cls),
+                                                  int(loc.shape[0]), _ptr(v), int(v.shape[1]), _stream(stream)))
+        return v
+
     def mlp_set_envelope(self, lo=None, hi=None, stream=None):
         """Raw-feature bounds lo [6], hi [6] (None, None: no envelope); outside
         them the fused closure uses Vreman's nu_t."""
@@ -225,33 +298,8 @@ class Context:
     def upload_mesh(self, mesh, stream=None) -> "DeviceMesh":
         """mesh: meshgen.Mesh-like object (xyz (N,3), conn dict, optional
         periodic_master, dirichlet, fp64_flag).  Host arrays only."""
-        xyz = np.ascontiguousarray(np.asarray(mesh.xyz, dtype=np.float64).T)
-        keep = [xyz]
-        d = MeshDesc()
-        d.n_nodes = xyz.shape[1]
-        d.xyz = xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        n_elem = [0, 0, 0, 0]
-        for t in range(4):
-            c = mesh.conn.get(t)
-            if c is not None and len(c):
-                c = np.ascontiguousarray(c, dtype=np.int32)
-                keep.append(c)
-                d.conn[t] = c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
-                d.n_elem[t] = c.shape[0]
-                n_elem[t] = c.shape[0]
-            f = getattr(mesh, "fp64_flag", {}).get(t) if getattr(mesh, "fp64_flag", None) else None
-            if f is not None and len(f):
-                f = np.ascontiguousarray(f, dtype=np.uint8)
-                keep.append(f)
-                d.fp64_jac[t] = f.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
-        if getattr(mesh, "periodic_master", None) is not None:
-            pm = np.ascontiguousarray(mesh.periodic_master, dtype=np.int32)
-            keep.append(pm)
-            d.periodic_master = pm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
-        if getattr(mesh, "dirichlet", None) is not None:
-            dm = np.ascontiguousarray(mesh.dirichlet, dtype=np.uint8)
-            keep.append(dm)
-            d.dirichlet = dm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        d, keep, n_elem = mesh_desc(mesh)
+        xyz = keep[0]
         mid = ctypes.c_int32(-1)
         self.check(self._lib.fea_mesh_upload(self.handle, ctypes.byref(d), _stream(stream), ctypes.byref(mid)))
         return DeviceMesh(self, mid.value, xyz.shape[1], n_elem)

@@ -242,6 +242,30 @@ def test_plan_validation_and_autotune(ctx, mixed_small):
     assert errors(r, oracle_rhs(m, f))[0] < MIXED_L2
 
 
+def test_autotune_cache_round_trip(ctx, mixed_small, tmp_path):
+    m, f = mixed_small
+    dm = ctx.upload_mesh(m)
+    dm.upload_field(f.u, f.p, f.nu, f.c_vreman)
+    path = str(tmp_path / "tune.txt")
+    dm.autotune(prec="mixed", closure="vreman", cache_path=path)
+    lines = open(path).read().splitlines()
+    assert len(lines) == 1
+    key = lines[0].split()[0]
+    assert "nodes=%d" % m.n_nodes in key
+    # a later entry for the same key is applied as is, without timing or appending
+    with open(path, "a") as fh:
+        fh.write(f"{key} 1 128 256 0 0.0\n")
+    dm.set_plan("chunk", 256, 512, 0)
+    p = dm.autotune(prec="mixed", closure="vreman", cache_path=path)
+    assert p.scatter == 1 and p.threads_per_block == 128
+    assert len(open(path).read().splitlines()) == 2
+    # another closure is another key
+    dm.autotune(prec="mixed", closure="none", cache_path=path)
+    assert len(open(path).read().splitlines()) == 3
+    r, _ = gpu_rhs(ctx, m, f, "mixed", dm=dm)
+    assert errors(r, oracle_rhs(m, f))[0] < MIXED_L2
+
+
 def sampled_parity(ctx, mesh, field, n_sample=3000, seed=0, prec="mixed", plan=None):
     """RHS at sampled nodes: the oracle assembles only the elements incident to
     them (their RHS is then complete) on a compacted sub-mesh."""
