@@ -73,6 +73,10 @@ def lib():
         _lib.orc_mlp_loss_grad.restype = ctypes.c_double
         _lib.orc_bad_element.restype = ctypes.c_int64
         _lib.orc_quadrature.argtypes = [ctypes.c_int, dp, dp]
+        vp = ctypes.c_void_p
+        _lib.orc_assemble_laplacian_coo.argtypes = [vp, vp, vp, dp]
+        _lib.orc_assemble_divergence.argtypes = [vp, dp, dp]
+        _lib.orc_assemble_gradient.argtypes = [vp, dp, dp]
         _lib.orc_shape.argtypes = [ctypes.c_int, dp, dp, dp]
     return _lib
 
@@ -295,6 +299,70 @@ def lumped_mass(om: OracleMesh) -> np.ndarray:
     m = np.zeros(om.n_nodes)
     _check(lib().orc_lumped_mass(ctypes.byref(om.struct), _dp(m)), "lumped_mass")
     return m
+
+
+# ---- pressure projection (Algorithm 1: Laplacian, pressure equation, velocity
+# correction; the reading of the step is documented with project()) ----------
+
+def assemble_laplacian(om: OracleMesh):
+    """K_ab = sum_e sum_g W_g grad N_a . grad N_b as a SciPy CSR matrix."""
+    import scipy.sparse as sp
+    nnz = sum(om.conn[t].shape[0] * NNODE[t] ** 2 for t in om.conn)
+    rows = np.zeros(nnz, np.int64)
+    cols = np.zeros(nnz, np.int64)
+    vals = np.zeros(nnz)
+    _check(lib().orc_assemble_laplacian_coo(ctypes.byref(om.struct), rows.ctypes.data_as(ctypes.c_void_p),
+                                            cols.ctypes.data_as(ctypes.c_void_p), _dp(vals)), "laplacian")
+    n = om.n_nodes
+    return sp.coo_matrix((vals, (rows, cols)), shape=(n, n)).tocsr()
+
+
+def divergence(om: OracleMesh, u: np.ndarray) -> np.ndarray:
+    """B_a(u) = sum_e sum_g W_g N_a (div u)_g for u (N, 3)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros(om.n_nodes)
+    _check(lib().orc_assemble_divergence(ctypes.byref(om.struct), _dp(u), _dp(out)), "divergence")
+    return out
+
+
+def gradient(om: OracleMesh, p: np.ndarray) -> np.ndarray:
+    """G_a(p) = sum_e sum_g W_g N_a (grad p)_g, (N, 3)."""
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    out = np.zeros((om.n_nodes, 3))
+    _check(lib().orc_assemble_gradient(ctypes.byref(om.struct), _dp(p), _dp(out)), "gradient")
+    return out
+
+
+def fold_matrix(master: np.ndarray):
+    """P (N x n_classes): P[i, class(i)] = 1, classes numbered by first master;
+    returns (P, class index per node, the master node of each class)."""
+    import scipy.sparse as sp
+    masters, cls = np.unique(np.asarray(master, dtype=np.int64), return_inverse=True)
+    n = cls.size
+    return sp.csr_matrix((np.ones(n), (np.arange(n), cls)), shape=(n, masters.size)), cls, masters
+
+
+def project(om: OracleMesh, master, vel_dirichlet, pinned, mass_folded, u_star, p, dt):
+    """Incremental pressure projection after the Runge-Kutta stages (reading of
+    Algorithm 1; the scheme's details are in a reference absent here):
+      K dp = -(1/dt) B(u*)      on the periodic classes, dp = 0 at pinned nodes,
+      u = u* - dt M_L^-1 G(dp)  (G folded; velocity-Dirichlet nodes keep u*),
+      p = p + dp.
+    Solved directly (SciPy sparse LU).  Returns (u, p, dp)."""
+    import scipy.sparse.linalg as spla
+    P, cls, _ = fold_matrix(master)
+    K = (P.T @ assemble_laplacian(om) @ P).tocsr()
+    b = P.T @ (-(1.0 / dt) * divergence(om, u_star))
+    keep = np.ones(K.shape[0], bool)
+    keep[np.unique(cls[np.asarray(pinned, dtype=np.int64)])] = False
+    dpc = np.zeros(K.shape[0])
+    dpc[keep] = spla.spsolve(K[keep][:, keep].tocsc(), b[keep])
+    dp = dpc[cls]
+    g = periodic_fold(master, gradient(om, dp))
+    u = np.array(u_star, dtype=np.float64, copy=True)
+    free = ~np.asarray(vel_dirichlet, dtype=bool)
+    u[free] -= dt * g[free] / np.asarray(mass_folded)[free, None]
+    return u, np.asarray(p, dtype=np.float64) + dp, dp
 
 
 def periodic_fold(master: np.ndarray, v: np.ndarray) -> np.ndarray:

@@ -620,6 +620,93 @@ int orc_element_mass(int etype, const double *X, double *Ae /*[nen][nen]*/) {
     return 0;
 }
 
+/* ---- pressure projection operators (Algorithm 1: "element assembly of the
+ * Laplacian matrix", the pressure equation and the velocity correction) ----
+ * Galerkin forms over every element and Gauss point, W_g = w_g det J:
+ *   K_ab  = sum W_g grad N_a . grad N_b          (Laplacian, assembled once)
+ *   B_a(u) = sum W_g N_a (div u)_g               (divergence of a nodal field)
+ *   G_a(p) = sum W_g N_a (grad p)_g              (gradient of a nodal scalar)  */
+
+/* K as COO triplets: entry k = e*nen^2 + a*nen + b of each type block, in the
+ * order of the types 0..3 (duplicates are summed by the caller). */
+int orc_assemble_laplacian_coo(const orc_mesh *m, int64_t *rows, int64_t *cols, double *vals) {
+    if (check_conn(m)) return -3;
+    double X[3 * MAXN], dN[MAXG * MAXN * 3], W[MAXG];
+    int64_t k = 0;
+    for (int t = 0; t < 4; ++t) {
+        const int nen = orc_nnode(t), ng = orc_ngauss(t);
+        for (int64_t e = 0; e < m->n_elem[t]; ++e) {
+            const int32_t *c = m->conn[t] + e * nen;
+            for (int a = 0; a < nen; ++a)
+                for (int i = 0; i < 3; ++i) X[3 * a + i] = m->xyz[3 * (int64_t)c[a] + i];
+            if (orc_element_geometry(t, X, NULL, dN, W, NULL) != 0) {
+                g_bad_type = t;
+                g_bad_elem = e;
+                return -1;
+            }
+            for (int a = 0; a < nen; ++a)
+                for (int b = 0; b < nen; ++b) {
+                    double s = 0.0;
+                    for (int g = 0; g < ng; ++g)
+                        for (int i = 0; i < 3; ++i)
+                            s += W[g] * dN[(g * nen + a) * 3 + i] * dN[(g * nen + b) * 3 + i];
+                    rows[k] = c[a];
+                    cols[k] = c[b];
+                    vals[k] = s;
+                    ++k;
+                }
+        }
+    }
+    return 0;
+}
+
+/* B(u) [n_nodes] for a nodal velocity u [n_nodes][3]. */
+int orc_assemble_divergence(const orc_mesh *m, const double *u, double *out) {
+    if (check_conn(m)) return -3;
+    memset(out, 0, sizeof(double) * m->n_nodes);
+    double X[3 * MAXN], N[MAXG * MAXN], dN[MAXG * MAXN * 3], W[MAXG];
+    for (int t = 0; t < 4; ++t) {
+        const int nen = orc_nnode(t), ng = orc_ngauss(t);
+        for (int64_t e = 0; e < m->n_elem[t]; ++e) {
+            const int32_t *c = m->conn[t] + e * nen;
+            for (int a = 0; a < nen; ++a)
+                for (int i = 0; i < 3; ++i) X[3 * a + i] = m->xyz[3 * (int64_t)c[a] + i];
+            if (orc_element_geometry(t, X, N, dN, W, NULL) != 0) return -1;
+            for (int g = 0; g < ng; ++g) {
+                double div = 0.0;
+                for (int b = 0; b < nen; ++b)
+                    for (int i = 0; i < 3; ++i) div += u[3 * (int64_t)c[b] + i] * dN[(g * nen + b) * 3 + i];
+                for (int a = 0; a < nen; ++a) out[c[a]] += W[g] * N[g * nen + a] * div;
+            }
+        }
+    }
+    return 0;
+}
+
+/* G(p) [n_nodes][3] for a nodal scalar p [n_nodes]. */
+int orc_assemble_gradient(const orc_mesh *m, const double *p, double *out) {
+    if (check_conn(m)) return -3;
+    memset(out, 0, sizeof(double) * 3 * m->n_nodes);
+    double X[3 * MAXN], N[MAXG * MAXN], dN[MAXG * MAXN * 3], W[MAXG];
+    for (int t = 0; t < 4; ++t) {
+        const int nen = orc_nnode(t), ng = orc_ngauss(t);
+        for (int64_t e = 0; e < m->n_elem[t]; ++e) {
+            const int32_t *c = m->conn[t] + e * nen;
+            for (int a = 0; a < nen; ++a)
+                for (int i = 0; i < 3; ++i) X[3 * a + i] = m->xyz[3 * (int64_t)c[a] + i];
+            if (orc_element_geometry(t, X, N, dN, W, NULL) != 0) return -1;
+            for (int g = 0; g < ng; ++g) {
+                double gp[3] = {0.0, 0.0, 0.0};
+                for (int b = 0; b < nen; ++b)
+                    for (int i = 0; i < 3; ++i) gp[i] += p[c[b]] * dN[(g * nen + b) * 3 + i];
+                for (int a = 0; a < nen; ++a)
+                    for (int i = 0; i < 3; ++i) out[3 * (int64_t)c[a] + i] += W[g] * N[g * nen + a] * gp[i];
+            }
+        }
+    }
+    return 0;
+}
+
 /* Periodic fold of a nodal array with ncomp components per node:
  * every slave's value is added to its master, then copied back. */
 void orc_periodic_fold(int64_t n, const int32_t *master, double *v, int ncomp) {
