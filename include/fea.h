@@ -257,6 +257,48 @@ fea_status fea_mlp_forward(fea_ctx *ctx, const float *x, int64_t B, float *nut, 
 fea_status fea_mlp_train_step(fea_ctx *ctx, const float *x, const float *y, int64_t B, float lr, float *loss_out,
                               float *grad_out, void *stream);
 
+/* ---- pressure projection (Algorithm 1) -----------------------------------
+ * Algorithm 1 assembles the Laplacian matrix once, and each time step ends
+ * with the solution of the pressure equation by CG with Jacobi diagonal
+ * scaling (section 2.1).  Forms (FP64, W_g = w_g det J):
+ *   K_ab = sum_e sum_g W_g grad N_a . grad N_b,
+ *   B_a(u) = sum_e sum_g W_g N_a (div u)_g,   G_a(p) = sum_e sum_g W_g N_a (grad p)_g.
+ * The pressure unknowns are periodic classes (a node and its periodic
+ * copies); pinned classes hold 0 (their rows and columns become identity),
+ * which fixes the constant of the pure-Neumann / periodic problem. */
+
+/* Builds the CSR matrix of K over periodic classes (pattern on the host,
+ * values by the element kernels) and its Jacobi diagonal.  pinned: optional
+ * host [n_nodes], nonzero = the node's class is pinned; NULL pins the class
+ * of node 0.  Synchronous.  Errors: FEA_EMESH (det J <= 0, a missing CSR
+ * entry), FEA_ENOMEM. */
+fea_status fea_poisson_setup(fea_ctx *ctx, int32_t mesh, const uint8_t *pinned, void *stream);
+
+/* Solves K x = scale * fold(b) by Jacobi-preconditioned CG: b [n_nodes]
+ * (device) is summed over the copies of each class; x [n_nodes] (device) is
+ * the initial guess (its masters' values) and receives the solution at
+ * every copy (0 at pinned classes).  Stops when ||r|| <= rtol ||b|| or after
+ * max_iter iterations; *iters and *rel_res (optional) receive the count and
+ * ||r|| / ||b||.  Synchronises the stream.  Errors: FEA_ESTATE (no setup),
+ * FEA_EINVAL. */
+fea_status fea_poisson_solve(fea_ctx *ctx, int32_t mesh, const double *b, double scale, double *x, double rtol,
+                             int32_t max_iter, int32_t *iters, double *rel_res, void *stream);
+
+/* out [n_nodes] = B(u) for u [3][n_nodes] (device, not folded).  Async. */
+fea_status fea_divergence(fea_ctx *ctx, int32_t mesh, const double *u, double *out, void *stream);
+
+/* out [3][n_nodes] = G(p) for p [n_nodes] (device, not folded).  Async. */
+fea_status fea_gradient(fea_ctx *ctx, int32_t mesh, const double *p, double *out, void *stream);
+
+/* Projection step on the mesh's state after the Runge-Kutta stages
+ * (incremental form): K dp = -(1/dt) fold(B(u)), then u <- u - dt M^-1
+ * fold(G(dp)) on nodes without velocity Dirichlet (M: folded lumped mass),
+ * p <- p + dp; the FP32 copy of the field is refreshed.  rtol, max_iter,
+ * iters, rel_res as in fea_poisson_solve.  Synchronises the stream.
+ * Errors: FEA_ESTATE (no field or no fea_poisson_setup), FEA_EINVAL. */
+fea_status fea_project(fea_ctx *ctx, int32_t mesh, double dt, double rtol, int32_t max_iter, int32_t *iters,
+                       double *rel_res, void *stream);
+
 /* ---- a mesh partitioned over several devices ----------------------------
  * Section 5: the mesh is split along a space-filling curve into parts of
  * (nearly) equal cost; each device assembles its part; after the assembly

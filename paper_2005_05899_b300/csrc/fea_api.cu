@@ -255,8 +255,12 @@ struct Mesh {
     std::vector<int32_t> inc_total;     // element incidences per node over all buckets
     fea_plan plan{FEA_SCATTER_CHUNK, 256, 256, 0};
     GraphCache graph;
+    std::vector<int32_t> master_h;      // host periodic masters (empty: none)
+    PoissonSystem *poisson = nullptr;   // pressure equation (fea_poisson_setup)
+    DevBuf<double> proj_b, proj_dp, proj_g;
     ~Mesh() {
         if (graph.exec) cudaGraphExecDestroy(graph.exec);
+        if (poisson) poisson_free(poisson);
     }
     FieldDev field() const {
         FieldDev f;
@@ -780,6 +784,7 @@ fea_status fea_mesh_upload(fea_ctx *ctx, const fea_mesh_desc *d, void *stream, i
         CK(cudaMemcpy(m->xyz32.p, x32.data(), sizeof(float4) * n, cudaMemcpyHostToDevice));
     }
     if (d->periodic_master) {
+        m->master_h.assign(d->periodic_master, d->periodic_master + n);
         std::vector<int32_t> sl, ms;
         for (int64_t i = 0; i < n; ++i)
             if (d->periodic_master[i] != i) {
@@ -1235,6 +1240,123 @@ fea_status fea_mlp_load(fea_ctx *ctx, const float *theta, const float *feat_mean
     ctx->mlp_step = 0;
     ctx->mlp_scale = out_scale;
     ctx->mlp_ready = true;
+    return FEA_OK;
+}
+
+// ---- pressure projection -----------------------------------------------------
+
+fea_status fea_poisson_setup(fea_ctx *ctx, int32_t mesh, const uint8_t *pinned, void *stream) {
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    PoissonBuild pb;
+    pb.n = m->n;
+    for (auto &b : m->buckets)
+        if (b->count) {
+            pb.conn.push_back(b->conn_h.data());
+            pb.count.push_back(b->count);
+            pb.nen.push_back(kNen[b->etype]);
+        }
+    pb.class_of = m->master_h.empty() ? nullptr : m->master_h.data();
+    pb.pinned = pinned;
+    if (m->poisson) {
+        CK(cudaDeviceSynchronize());
+        poisson_free(m->poisson);
+        m->poisson = nullptr;
+    }
+    CK(poisson_build(pb, ctx->sms, &m->poisson));
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), s));
+    for (auto &b : m->buckets) {
+        CK(launch_lap_assemble(b->dev(), m->xyz64.p, m->n, poisson_cls(m->poisson), poisson_rowptr(m->poisson),
+                               poisson_col(m->poisson), poisson_val(m->poisson), ctx->d_err, s));
+        ctx->launches += b->count ? 1 : 0;
+    }
+    CK(poisson_finish(m->poisson, ctx->d_err, ctx->sms, s));
+    ctx->launches += 2;
+    if (!m->proj_b.n) {
+        CK(m->proj_b.alloc(m->n));
+        CK(m->proj_dp.alloc(m->n));
+        CK(m->proj_g.alloc(3 * m->n));
+    }
+    unsigned w = 0;
+    CK(cudaMemcpyAsync(&w, ctx->d_err, sizeof w, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (w) {
+        CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), s));
+        poisson_free(m->poisson);
+        m->poisson = nullptr;
+        return fail(ctx, FEA_EMESH, "Laplacian assembly failed (device word 0x%x)", w);
+    }
+    return FEA_OK;
+}
+
+fea_status fea_poisson_solve(fea_ctx *ctx, int32_t mesh, const double *b, double scale, double *x, double rtol,
+                             int32_t max_iter, int32_t *iters, double *rel_res, void *stream) {
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    if (!m->poisson) return fail(ctx, FEA_ESTATE, "fea_poisson_setup has not run for mesh %d", mesh);
+    if (!b || !x || !(rtol > 0.0) || max_iter < 0) return fail(ctx, FEA_EINVAL, "bad Poisson solve arguments");
+    CK(cudaSetDevice(ctx->device));
+    int it = 0;
+    double rr = 0.0;
+    CK(poisson_solve(m->poisson, b, scale, x, rtol, max_iter, ctx->sms, (cudaStream_t)stream, &it, &rr,
+                     &ctx->launches));
+    if (iters) *iters = it;
+    if (rel_res) *rel_res = rr;
+    return FEA_OK;
+}
+
+namespace {
+fea_status divgrad(fea_ctx *ctx, int32_t mesh, bool div, const double *in, double *out, cudaStream_t s) {
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    if (!in || !out) return fail(ctx, FEA_EINVAL, "null array");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemsetAsync(out, 0, sizeof(double) * (div ? 1 : 3) * m->n, s));
+    for (auto &b : m->buckets) {
+        CK(launch_divgrad_assemble(b->dev(), m->xyz64.p, m->n, div, in, out, ctx->d_err, s));
+        ctx->launches += b->count ? 1 : 0;
+    }
+    return FEA_OK;
+}
+}  // namespace
+
+fea_status fea_divergence(fea_ctx *ctx, int32_t mesh, const double *u, double *out, void *stream) {
+    return divgrad(ctx, mesh, true, u, out, (cudaStream_t)stream);
+}
+
+fea_status fea_gradient(fea_ctx *ctx, int32_t mesh, const double *p, double *out, void *stream) {
+    return divgrad(ctx, mesh, false, p, out, (cudaStream_t)stream);
+}
+
+fea_status fea_project(fea_ctx *ctx, int32_t mesh, double dt, double rtol, int32_t max_iter, int32_t *iters,
+                       double *rel_res, void *stream) {
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    if (!m->has_field) return fail(ctx, FEA_ESTATE, "no field uploaded for mesh %d", mesh);
+    if (!m->poisson) return fail(ctx, FEA_ESTATE, "fea_poisson_setup has not run for mesh %d", mesh);
+    if (!(dt > 0.0)) return fail(ctx, FEA_EINVAL, "dt must be > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = m->n;
+    // b = B(u*);  K dp = -(1/dt) b;  g = G(dp), folded;  u -= dt g / M;  p += dp
+    if ((st = divgrad(ctx, mesh, true, m->uk.p, m->proj_b.p, s))) return st;
+    CK(cudaMemsetAsync(m->proj_dp.p, 0, sizeof(double) * n, s));
+    if ((st = fea_poisson_solve(ctx, mesh, m->proj_b.p, -1.0 / dt, m->proj_dp.p, rtol, max_iter, iters, rel_res,
+                                stream)))
+        return st;
+    if ((st = divgrad(ctx, mesh, false, m->proj_dp.p, m->proj_g.p, s))) return st;
+    if (m->slaves.n) {
+        CK(launch_fold(m->slaves.p, m->masters.p, (int64_t)m->slaves.n, m->proj_g.p, 3, n, s));
+        ctx->launches += 2;
+    }
+    CK(launch_project_update(n, m->uk.p, m->un.p, m->proj_g.p, m->minv.p, m->dirichlet.n ? m->dirichlet.p : nullptr,
+                             m->p64.p, m->proj_dp.p, m->up32.p, dt, ctx->sms, s));
+    ctx->launches++;
     return FEA_OK;
 }
 

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "fea.h"
 
 namespace fea {
@@ -115,6 +117,38 @@ cudaError_t launch_rk_update(int64_t n, const double *un, double *uk, double *un
 cudaError_t launch_pack_field(int64_t n, const double *u64, const double *p64, float4 *up32, cudaStream_t s);
 cudaError_t launch_f32_to_f64(const float *src, double *dst, int64_t count, cudaStream_t s);
 cudaError_t launch_recip(const double *m, double *minv, int64_t n, cudaStream_t s);
+
+// pressure projection element operators (fea_kernels.cu), FP64
+cudaError_t launch_lap_assemble(const BucketDev &b, const double *xyz, int64_t n, const int32_t *cls,
+                                const int64_t *rowptr, const int32_t *col, double *val, unsigned *err,
+                                cudaStream_t s);
+cudaError_t launch_divgrad_assemble(const BucketDev &b, const double *xyz, int64_t n, bool div, const double *in,
+                                    double *out, unsigned *err, cudaStream_t s);
+cudaError_t launch_project_update(int64_t n, double *uk, double *un, const double *g, const double *minv,
+                                  const uint8_t *dirichlet, double *p, const double *dp, float4 *up32, double dt,
+                                  int sms, cudaStream_t s);
+
+// pressure equation on periodic classes (fea_poisson.cu)
+struct PoissonSystem;
+struct PoissonBuild {
+    int64_t n = 0;                        // nodes
+    std::vector<const int32_t *> conn;    // per bucket, host [nen][count]
+    std::vector<int64_t> count;
+    std::vector<int> nen;
+    const int32_t *class_of = nullptr;    // host [n]: periodic master of each node (NULL: none)
+    const uint8_t *pinned = nullptr;      // host [n]: pinned nodes (NULL: the class of node 0)
+};
+cudaError_t poisson_build(const PoissonBuild &in, int sms, PoissonSystem **out);
+cudaError_t poisson_finish(PoissonSystem *ps, unsigned *err, int sms, cudaStream_t s);
+cudaError_t poisson_solve(PoissonSystem *ps, const double *b_node, double scale, double *x_node, double rtol,
+                          int max_iter, int sms, cudaStream_t s, int *iters_out, double *rel_res_out, int64_t *launches);
+void poisson_free(PoissonSystem *ps);
+int64_t poisson_classes(const PoissonSystem *ps);
+int64_t poisson_nnz(const PoissonSystem *ps);
+const int32_t *poisson_cls(const PoissonSystem *ps);
+const int64_t *poisson_rowptr(const PoissonSystem *ps);
+const int32_t *poisson_col(const PoissonSystem *ps);
+double *poisson_val(PoissonSystem *ps);
 
 // interface exchange of a partitioned mesh (fea_kernels.cu)
 cudaError_t launch_iface_pack(const double *v, int64_t n, const int64_t *loc, const int64_t *cls, int64_t m,

@@ -834,6 +834,203 @@ cudaError_t launch_assemble_batch(const void *buckets, const void *fields, const
 }
 
 // ---------------------------------------------------------------------------
+// Pressure projection operators (Algorithm 1), FP64, one thread per element,
+// FP64 atomics into the outputs:
+//   K_ab = sum_g W_g grad N_a . grad N_b  into a CSR matrix over periodic
+//          classes (row/column = class of the node; entry found by binary
+//          search in the row);
+//   B_a(u) = sum_g W_g N_a (div u)_g,   G_a(p) = sum_g W_g N_a (grad p)_g.
+
+template <int ET>
+__device__ __forceinline__ double proj_geometry(const double X[][3], int g, double dN[][3]) {
+    constexpr int nen = kNen[ET];
+    double J[3][3], Ji[3][3];
+    jacobian_at<ET, double, double>(X, g, J);
+    const double det = inv3(J, Ji);
+#pragma unroll
+    for (int a = 0; a < nen; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            dN[a][j] = c_ref.dN[ET][g][a][0] * Ji[0][j] + c_ref.dN[ET][g][a][1] * Ji[1][j] +
+                       c_ref.dN[ET][g][a][2] * Ji[2][j];
+    return det;
+}
+
+__device__ __forceinline__ int64_t csr_find(const int64_t *rowptr, const int32_t *col, int32_t r, int32_t c) {
+    int64_t lo = rowptr[r], hi = rowptr[r + 1] - 1;
+    while (lo <= hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const int32_t v = col[mid];
+        if (v == c) return mid;
+        if (v < c)
+            lo = mid + 1;
+        else
+            hi = mid - 1;
+    }
+    return -1;
+}
+
+template <int ET>
+__global__ void k_lap_assemble(BucketDev b, const double *xyz, int64_t n, const int32_t *cls, const int64_t *rowptr,
+                               const int32_t *col, double *val, unsigned *err) {
+    constexpr int nen = kNen[ET], ng = kNg[ET];
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= b.count) return;
+    int idx[nen];
+    double X[nen][3];
+#pragma unroll
+    for (int a = 0; a < nen; ++a) {
+        idx[a] = b.conn[(int64_t)a * b.count + e];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) X[a][i] = xyz[(int64_t)i * n + idx[a]];
+    }
+    double K[nen][nen];
+#pragma unroll
+    for (int a = 0; a < nen; ++a)
+#pragma unroll
+        for (int c = 0; c < nen; ++c) K[a][c] = 0.0;
+    bool bad = false;
+    for (int g = 0; g < ng; ++g) {
+        double dN[nen][3];
+        const double det = proj_geometry<ET>(X, g, dN);
+        if (!(det > 0.0)) bad = true;
+        const double W = c_ref.w[ET][g] * det;
+#pragma unroll
+        for (int a = 0; a < nen; ++a)
+#pragma unroll
+            for (int c = 0; c < nen; ++c) K[a][c] += W * (dN[a][0] * dN[c][0] + dN[a][1] * dN[c][1] + dN[a][2] * dN[c][2]);
+    }
+    if (bad) set_err(err, ERR_DETJ);
+#pragma unroll
+    for (int a = 0; a < nen; ++a) {
+        const int32_t r = cls[idx[a]];
+#pragma unroll
+        for (int c = 0; c < nen; ++c) {
+            const int64_t pos = csr_find(rowptr, col, r, cls[idx[c]]);
+            if (pos < 0)
+                set_err(err, ERR_INDEX);
+            else
+                atomicAdd(&val[pos], K[a][c]);
+        }
+    }
+}
+
+// DIV: out[a] += W N_a div u;  otherwise out[i][a] += W N_a d_i p
+template <int ET, bool DIV>
+__global__ void k_divgrad_assemble(BucketDev b, const double *xyz, int64_t n, const double *in, double *out,
+                                   unsigned *err) {
+    constexpr int nen = kNen[ET], ng = kNg[ET];
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= b.count) return;
+    int idx[nen];
+    double X[nen][3];
+#pragma unroll
+    for (int a = 0; a < nen; ++a) {
+        idx[a] = b.conn[(int64_t)a * b.count + e];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) X[a][i] = xyz[(int64_t)i * n + idx[a]];
+    }
+    double acc[nen][3];
+#pragma unroll
+    for (int a = 0; a < nen; ++a) acc[a][0] = acc[a][1] = acc[a][2] = 0.0;
+    bool bad = false;
+    for (int g = 0; g < ng; ++g) {
+        double dN[nen][3];
+        const double det = proj_geometry<ET>(X, g, dN);
+        if (!(det > 0.0)) bad = true;
+        const double W = c_ref.w[ET][g] * det;
+        double v[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int c = 0; c < nen; ++c) {
+            if constexpr (DIV) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) v[0] += in[(int64_t)i * n + idx[c]] * dN[c][i];
+            } else {
+                const double pc = in[idx[c]];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) v[i] += pc * dN[c][i];
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < nen; ++a) {
+            const double wn = W * c_ref.N[ET][g][a];
+#pragma unroll
+            for (int i = 0; i < (DIV ? 1 : 3); ++i) acc[a][i] += wn * v[i];
+        }
+    }
+    if (bad) set_err(err, ERR_DETJ);
+#pragma unroll
+    for (int a = 0; a < nen; ++a) {
+        if constexpr (DIV) {
+            atomicAdd(&out[idx[a]], acc[a][0]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) atomicAdd(&out[(int64_t)i * n + idx[a]], acc[a][i]);
+        }
+    }
+}
+
+cudaError_t launch_lap_assemble(const BucketDev &b, const double *xyz, int64_t n, const int32_t *cls,
+                                const int64_t *rowptr, const int32_t *col, double *val, unsigned *err,
+                                cudaStream_t s) {
+    if (b.count == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((b.count + 127) / 128);
+    switch (b.etype) {
+        case FEA_TET04: k_lap_assemble<FEA_TET04><<<blocks, 128, 0, s>>>(b, xyz, n, cls, rowptr, col, val, err); break;
+        case FEA_PYR05: k_lap_assemble<FEA_PYR05><<<blocks, 128, 0, s>>>(b, xyz, n, cls, rowptr, col, val, err); break;
+        case FEA_PEN06: k_lap_assemble<FEA_PEN06><<<blocks, 128, 0, s>>>(b, xyz, n, cls, rowptr, col, val, err); break;
+        case FEA_HEX08: k_lap_assemble<FEA_HEX08><<<blocks, 128, 0, s>>>(b, xyz, n, cls, rowptr, col, val, err); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_divgrad_assemble(const BucketDev &b, const double *xyz, int64_t n, bool div, const double *in,
+                                    double *out, unsigned *err, cudaStream_t s) {
+    if (b.count == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((b.count + 127) / 128);
+#define FEA_DG(ET)                                                                             \
+    (div ? (k_divgrad_assemble<ET, true><<<blocks, 128, 0, s>>>(b, xyz, n, in, out, err), 0) \
+         : (k_divgrad_assemble<ET, false><<<blocks, 128, 0, s>>>(b, xyz, n, in, out, err), 0))
+    switch (b.etype) {
+        case FEA_TET04: FEA_DG(FEA_TET04); break;
+        case FEA_PYR05: FEA_DG(FEA_PYR05); break;
+        case FEA_PEN06: FEA_DG(FEA_PEN06); break;
+        case FEA_HEX08: FEA_DG(FEA_HEX08); break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef FEA_DG
+    return cudaGetLastError();
+}
+
+// u -= dt g / M on free nodes (un = the result), p += dp, FP32 copy refreshed
+__global__ void k_project_update(int64_t n, double *uk, double *un, const double *g, const double *minv,
+                                 const uint8_t *dirichlet, double *p, const double *dp, float4 *up32, double dt) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double u[3];
+        const bool hold = dirichlet && dirichlet[i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            u[c] = uk[(int64_t)c * n + i];
+            if (!hold) u[c] -= dt * g[(int64_t)c * n + i] * minv[i];
+            uk[(int64_t)c * n + i] = u[c];
+            un[(int64_t)c * n + i] = u[c];
+        }
+        const double pn = p[i] + dp[i];
+        p[i] = pn;
+        up32[i] = make_float4((float)u[0], (float)u[1], (float)u[2], (float)pn);
+    }
+}
+
+cudaError_t launch_project_update(int64_t n, double *uk, double *un, const double *g, const double *minv,
+                                  const uint8_t *dirichlet, double *p, const double *dp, float4 *up32, double dt,
+                                  int sms, cudaStream_t s) {
+    const int64_t grid = std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
+    k_project_update<<<(unsigned)grid, 256, 0, s>>>(n, uk, un, g, minv, dirichlet, p, dp, up32, dt);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Interface exchange of a partitioned mesh: classes of node copies that must
 // end with one value (a node shared by parts, with its periodic copies).
 // pack: out[c][cls[k]] += v[c][loc[k]]; unpack: v[c][loc[k]] = in[c][cls[k]].

@@ -33,6 +33,7 @@ EXPORTED = (
     "fea_sync_status", "fea_launch_count", "fea_profile_enable", "fea_profile_read", "fea_rk_stage_noalloc",
     "fea_mlp_load", "fea_mlp_get", "fea_mlp_forward", "fea_mlp_train_step", "fea_mlp_set_envelope",
     "fea_mlp_fallback_read", "fea_sfc_order", "fea_partition_sfc", "fea_interface_pack", "fea_interface_unpack",
+    "fea_poisson_setup", "fea_poisson_solve", "fea_divergence", "fea_gradient", "fea_project",
 )
 MLP_NPARAM = 8833
 NOALLOC_MAX_NODES = 262144
@@ -157,6 +158,11 @@ def lib() -> ctypes.CDLL:
         L.fea_mlp_train_step.argtypes = [vp, vp, vp, i64, ctypes.c_float, vp, vp, vp]
         L.fea_mlp_set_envelope.argtypes = [vp, vp, vp, vp]
         L.fea_sfc_order.argtypes = [i64, vp, i32, vp]
+        L.fea_poisson_setup.argtypes = [vp, i32, vp, vp]
+        L.fea_poisson_solve.argtypes = [vp, i32, vp, dbl, vp, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl), vp]
+        L.fea_divergence.argtypes = [vp, i32, vp, vp, vp]
+        L.fea_gradient.argtypes = [vp, i32, vp, vp, vp]
+        L.fea_project.argtypes = [vp, i32, dbl, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl), vp]
         L.fea_partition_sfc.argtypes = [ctypes.POINTER(MeshDesc), i32, i32, ctypes.c_void_p * 4]
         L.fea_interface_pack.argtypes = [vp, vp, i64, vp, vp, i64, vp, i64, vp]
         L.fea_interface_unpack.argtypes = [vp, vp, i64, vp, vp, i64, vp, i64, vp]
@@ -364,6 +370,36 @@ class DeviceMesh:
         ncomp = 1 if v.dim() == 1 else v.shape[0]
         self.ctx.check(self._L().fea_periodic_fold(self.ctx.handle, self.id, _ptr(v), ncomp, _stream(stream)))
         return v
+
+    # ---- pressure projection ----
+    def poisson_setup(self, pinned=None, stream=None):
+        """Laplacian over periodic classes; pinned: optional host bool/uint8 [n]."""
+        pin = None if pinned is None else np.ascontiguousarray(pinned, dtype=np.uint8)
+        self.ctx.check(self._L().fea_poisson_setup(self.ctx.handle, self.id, _ptr(pin), _stream(stream)))
+
+    def poisson_solve(self, b, x, scale=1.0, rtol=1e-10, max_iter=2000, stream=None):
+        """K x = scale fold(b) (device float64 [n]); x: initial guess / solution.
+        Returns (iterations, ||r|| / ||b||)."""
+        it, rr = ctypes.c_int32(0), ctypes.c_double(0.0)
+        self.ctx.check(self._L().fea_poisson_solve(self.ctx.handle, self.id, _ptr(b), float(scale), _ptr(x),
+                                                   float(rtol), int(max_iter), ctypes.byref(it), ctypes.byref(rr),
+                                                   _stream(stream)))
+        return it.value, rr.value
+
+    def divergence(self, u, out, stream=None):
+        self.ctx.check(self._L().fea_divergence(self.ctx.handle, self.id, _ptr(u), _ptr(out), _stream(stream)))
+        return out
+
+    def gradient(self, p, out, stream=None):
+        self.ctx.check(self._L().fea_gradient(self.ctx.handle, self.id, _ptr(p), _ptr(out), _stream(stream)))
+        return out
+
+    def project(self, dt: float, rtol=1e-10, max_iter=2000, stream=None):
+        """Projection step on the state; returns (iterations, ||r|| / ||b||)."""
+        it, rr = ctypes.c_int32(0), ctypes.c_double(0.0)
+        self.ctx.check(self._L().fea_project(self.ctx.handle, self.id, float(dt), float(rtol), int(max_iter),
+                                             ctypes.byref(it), ctypes.byref(rr), _stream(stream)))
+        return it.value, rr.value
 
     def rk_stage(self, stage: int, dt: float, prec="mixed", closure="vreman", stream=None):
         self.ctx.check(self._L().fea_rk_stage(self.ctx.handle, self.id, stage, float(dt), PREC[prec],
