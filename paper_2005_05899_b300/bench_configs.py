@@ -3,7 +3,7 @@
 the learned closure (trained on filtered fine Taylor-Green runs, then fused
 into the assembly of an 8M-element mixed channel mesh against Vreman).
 
-    python -m paper_2005_05899_b300.bench_configs [--channel] [--batch] [--closure] [--reps 20]
+    python -m paper_2005_05899_b300.bench_configs [--channel] [--batch] [--closure] [--projection] [--reps 20]
 
 Prints one JSON line per measurement (CUDA-event times on the current stream,
 after warm-up; inputs are larger than L2 for the channel and the batch).
@@ -179,15 +179,49 @@ def closure(reps: int, n_f: int = 256, steps: int = 8000, dims=(269, 134, 135)):
     ctx.close()
 
 
+def projection(n_axis: int = 170, dt: float = 2e-4, rtol: float = 1e-6, steps: int = 3):
+    """Pressure projection on the airplane-like mesh: Laplacian set-up
+    (host pattern + device values), then `steps` fractional steps (RK3 graph
+    step + projection) with CG iteration counts and times; SpMV traffic per
+    iteration = 12 B per stored entry + 8 B x 10 class vectors touched."""
+    import torch
+    from . import fea
+    from . import meshgen as mg
+    m = mg.airplane_mesh(n_axis, seed=4)
+    f = mg.inflow_field(m, seed=5)
+    ctx = fea.Context(0)
+    dm = ctx.upload_mesh(m)
+    dm.upload_field(f.u, f.p, f.nu, f.c_vreman)
+    t = time.time()
+    dm.poisson_setup()
+    setup_s = time.time() - t
+    res = []
+    for k in range(steps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        dm.rk_step_graph(dt)
+        e1.record()
+        it, rr = dm.project(dt, rtol=rtol, max_iter=20000)
+        e2.record()
+        torch.cuda.synchronize()
+        res.append({"rk3_ms": e0.elapsed_time(e1), "project_ms": e1.elapsed_time(e2), "cg_iters": it,
+                    "rel_res": rr, "ms_per_cg_iter": e1.elapsed_time(e2) / max(it, 1)})
+    ctx.sync_status()
+    E = m.n_elem_total
+    print(json.dumps({"workload": f"projection on the airplane-like mesh ({E:,} elements, {m.n_nodes:,} nodes)",
+                      "setup_s": setup_s, "dt": dt, "rtol": rtol, "steps": res}), flush=True)
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--channel", action="store_true")
     ap.add_argument("--batch", action="store_true")
     ap.add_argument("--closure", action="store_true")
+    ap.add_argument("--projection", action="store_true")
     ap.add_argument("--n-f", type=int, default=256, help="fine Taylor-Green grid of the closure's training runs")
     ap.add_argument("--reps", type=int, default=20)
     a = ap.parse_args(argv)
-    if not (a.channel or a.batch or a.closure):
+    if not (a.channel or a.batch or a.closure or a.projection):
         a.channel = a.batch = True
     if a.channel:
         channel(a.reps)
@@ -195,6 +229,8 @@ def main(argv=None) -> int:
         batch(a.reps)
     if a.closure:
         closure(a.reps, n_f=a.n_f)
+    if a.projection:
+        projection()
     return 0
 
 

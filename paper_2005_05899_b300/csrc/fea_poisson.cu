@@ -7,7 +7,9 @@
 // removes the constant null space of the pure-Neumann / periodic problem.
 //
 // Host: the CSR pattern over classes (from the element connectivity).
-// Device (FP64): the values are assembled by the element kernels; one CG
+// Device (FP64): the values are assembled by the element kernels into the
+// CSR matrix and copied once into a sliced-ELLPACK matrix (32-row slices,
+// column-major within a slice) for the iteration; one CG
 // iteration is three kernels (SpMV + dot, update of x, r, z + two dots,
 // update of p), the dot products finished by the last block of each kernel
 // in a fixed order (deterministic), the iteration stopped by a device flag
@@ -67,43 +69,61 @@ __device__ bool finish_partials(const double (&v)[NV], double *partial, unsigned
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < NV; ++k) {
-            double s = 0.0;
-            for (unsigned b = 0; b < gridDim.x; ++b) s += ((volatile double *)partial)[k * gridDim.x + b];
-            sums[k] = s;
-        }
-        *ticket = 0u;
+    // the whole last block adds the partials: strided per thread, then the
+    // block tree (a fixed order for a fixed grid, so the sums are reproducible)
+    for (int k = 0; k < NV; ++k) {
+        double t = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+            t += ((volatile double *)partial)[k * gridDim.x + b];
+        t = block_sum(t, sh);
+        if (threadIdx.x == 0) sums[k] = t;
     }
+    if (threadIdx.x == 0) *ticket = 0u;
     __syncthreads();
     return true;
 }
 
-// q = A p, scal[S_PQ] = p.q ; 8 lanes per row, rows in warp-uniform groups of 4
-__global__ void __launch_bounds__(kThreads) k_cg_spmv(const int64_t *rowptr, const int32_t *col, const double *val,
-                                                      const double *p, double *q, int64_t nc, double *scal,
-                                                      double *partial, unsigned *ticket, const int *done) {
+// q = A p, scal[S_PQ] = p.q.  Sliced ELLPACK: slice s holds rows 32 s ..
+// 32 s + 31, entry j of the slice's rows at sell_off[s] + 32 j + lane (padding:
+// value 0, column = the row), width sell_w[s].  A warp is one slice: one row
+// per lane, coalesced value / column loads, the width's gathers independent.
+__global__ void __launch_bounds__(kThreads) k_cg_spmv(const int64_t *sell_off, const int32_t *sell_w,
+                                                      const int32_t *col, const double *val, const double *p,
+                                                      double *q, int64_t nc, double *scal, double *partial,
+                                                      unsigned *ticket, const int *done) {
     if (*done) return;
-    const int lane = threadIdx.x & 31, sub = lane & 7;
+    const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nslices = (nc + 31) >> 5;
     double dot = 0.0;
-    for (int64_t r0 = warp * 4; r0 < nc; r0 += warps * 4) {
-        const int64_t row = r0 + (lane >> 3);
-        double s = 0.0;
-        if (row < nc)
-            for (int64_t k = rowptr[row] + sub; k < rowptr[row + 1]; k += 8) s += val[k] * p[col[k]];
-        s += __shfl_xor_sync(0xffffffffu, s, 1);
-        s += __shfl_xor_sync(0xffffffffu, s, 2);
-        s += __shfl_xor_sync(0xffffffffu, s, 4);
-        if (row < nc && sub == 0) {
-            q[row] = s;
-            dot += p[row] * s;
+    for (int64_t sl = warp; sl < nslices; sl += warps) {
+        const int64_t row = (sl << 5) + lane;
+        const int64_t off = __ldg(&sell_off[sl]) + lane;
+        const int w = __ldg(&sell_w[sl]);
+        double acc = 0.0;
+#pragma unroll 4
+        for (int j = 0; j < w; ++j) {
+            const int64_t k = off + ((int64_t)j << 5);
+            acc += __ldg(&val[k]) * __ldg(&p[__ldg(&col[k])]);
+        }
+        if (row < nc) {
+            q[row] = acc;
+            dot += p[row] * acc;
         }
     }
     double v[1] = {dot};
     double out[1];
     if (finish_partials<1>(v, partial, ticket, out) && threadIdx.x == 0) scal[S_PQ] = out[0];
+}
+
+// CSR values -> sliced ELLPACK positions (pattern built on the host)
+__global__ void k_csr_to_sell(const int64_t *rowptr, const double *val, int64_t nc, const int64_t *sell_off,
+                              double *sval) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nc; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t base = sell_off[r >> 5] + (r & 31);
+        for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) sval[base + ((k - rowptr[r]) << 5)] = val[k];
+    }
 }
 
 // r = b - q (q = A x0), z = D^-1 r, p = z; rz, rr, bb
@@ -218,15 +238,23 @@ __global__ void k_diag_inverse(const int64_t *rowptr, const int32_t *col, const 
 
 struct PoissonSystem {
     int64_t n = 0, nc = 0, nnz = 0, npin = 0;
-    int grid = 1;
+    int grid = 1;        // vector kernels
+    int grid_mv = 1;     // SpMV grid (one 32-row slice per warp)
     int32_t *cls = nullptr, *rep = nullptr, *col = nullptr, *pins = nullptr;
     int64_t *rowptr = nullptr;
     double *val = nullptr, *dinv = nullptr;
+    // sliced ELLPACK copy of the matrix for the iteration
+    int64_t *sell_off = nullptr;
+    int32_t *sell_w = nullptr, *sell_col = nullptr;
+    double *sell_val = nullptr;
+    int64_t sell_n = 0;
     double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *b = nullptr;
     double *partial = nullptr, *scal = nullptr;
     unsigned *ticket = nullptr;
     int *done = nullptr, *iters = nullptr;
     ~PoissonSystem() {
+        for (void *ptr : {(void *)sell_off, (void *)sell_w, (void *)sell_col, (void *)sell_val})
+            if (ptr) cudaFree(ptr);
         for (void *ptr : {(void *)cls, (void *)rep, (void *)col, (void *)pins, (void *)rowptr, (void *)val, (void *)dinv,
                           (void *)x, (void *)r, (void *)z, (void *)p, (void *)q, (void *)b, (void *)partial,
                           (void *)scal, (void *)ticket, (void *)done, (void *)iters})
@@ -293,6 +321,26 @@ cudaError_t poisson_build(const PoissonBuild &in, int sms, PoissonSystem **out) 
         col.insert(col.end(), row.begin(), row.end());
         rowptr[(size_t)c + 1] = (int64_t)col.size();
     }
+    // sliced ELLPACK pattern: slices of 32 rows, width = longest row of the slice
+    const int64_t nslices = (nc + 31) / 32;
+    std::vector<int64_t> soff((size_t)nslices + 1, 0);
+    std::vector<int32_t> sw((size_t)std::max<int64_t>(nslices, 1), 0);
+    for (int64_t sl = 0; sl < nslices; ++sl) {
+        int64_t w = 0;
+        for (int64_t r = sl * 32; r < std::min(nc, sl * 32 + 32); ++r) w = std::max(w, rowptr[(size_t)r + 1] - rowptr[(size_t)r]);
+        sw[(size_t)sl] = (int32_t)w;
+        soff[(size_t)sl + 1] = soff[(size_t)sl] + 32 * w;
+    }
+    std::vector<int32_t> scol((size_t)soff[(size_t)nslices]);
+    for (int64_t sl = 0; sl < nslices; ++sl)
+        for (int lane = 0; lane < 32; ++lane) {
+            const int64_t r = sl * 32 + lane;
+            for (int64_t j = 0; j < sw[(size_t)sl]; ++j) {
+                const int64_t k = r < nc ? rowptr[(size_t)r] + j : -1;
+                scol[(size_t)(soff[(size_t)sl] + j * 32 + lane)] =
+                    (r < nc && k < rowptr[(size_t)r + 1]) ? col[(size_t)k] : (int32_t)std::min<int64_t>(r, nc - 1);
+            }
+        }
     // pinned classes (the class of node 0 when none are given)
     std::vector<int32_t> pins;
     if (in.pinned) {
@@ -310,7 +358,9 @@ cudaError_t poisson_build(const PoissonBuild &in, int sms, PoissonSystem **out) 
     ps->nc = nc;
     ps->nnz = (int64_t)col.size();
     ps->npin = (int64_t)pins.size();
-    ps->grid = (int)std::max<int64_t>(1, std::min<int64_t>((nc + kThreads - 1) / kThreads, (int64_t)sms * 4));
+    ps->grid = (int)std::max<int64_t>(1, std::min<int64_t>((nc + kThreads - 1) / kThreads, (int64_t)sms * 8));
+    // SpMV: one slice of 32 rows per warp
+    ps->grid_mv = (int)std::max<int64_t>(1, std::min<int64_t>((nc + 255) / 256, (int64_t)sms * 16));
     cudaError_t e = cudaSuccess;
 #define PS_TRY(x)                  \
     do {                           \
@@ -328,7 +378,7 @@ cudaError_t poisson_build(const PoissonBuild &in, int sms, PoissonSystem **out) 
     PS_TRY(dalloc(&ps->dinv, (size_t)nc));
     PS_TRY(dalloc(&ps->pins, std::max<size_t>(pins.size(), 1)));
     for (double **v : {&ps->x, &ps->r, &ps->z, &ps->p, &ps->q, &ps->b}) PS_TRY(dalloc(v, (size_t)std::max<int64_t>(nc, 1)));
-    PS_TRY(dalloc(&ps->partial, (size_t)3 * ps->grid));
+    PS_TRY(dalloc(&ps->partial, (size_t)3 * std::max(ps->grid, ps->grid_mv)));
     PS_TRY(dalloc(&ps->scal, (size_t)S_COUNT));
     PS_TRY(dalloc(&ps->ticket, 1));
     PS_TRY(dalloc(&ps->done, 1));
@@ -339,6 +389,16 @@ cudaError_t poisson_build(const PoissonBuild &in, int sms, PoissonSystem **out) 
     PS_TRY(cudaMemcpy(ps->col, col.data(), sizeof(int32_t) * col.size(), cudaMemcpyHostToDevice));
     if (!pins.empty()) PS_TRY(cudaMemcpy(ps->pins, pins.data(), sizeof(int32_t) * pins.size(), cudaMemcpyHostToDevice));
     PS_TRY(cudaMemset(ps->val, 0, sizeof(double) * col.size()));
+    ps->sell_n = (int64_t)scol.size();
+    PS_TRY(dalloc(&ps->sell_off, soff.size()));
+    PS_TRY(dalloc(&ps->sell_w, sw.size()));
+    PS_TRY(dalloc(&ps->sell_col, std::max<size_t>(scol.size(), 1)));
+    PS_TRY(dalloc(&ps->sell_val, std::max<size_t>(scol.size(), 1)));
+    PS_TRY(cudaMemcpy(ps->sell_off, soff.data(), sizeof(int64_t) * soff.size(), cudaMemcpyHostToDevice));
+    PS_TRY(cudaMemcpy(ps->sell_w, sw.data(), sizeof(int32_t) * sw.size(), cudaMemcpyHostToDevice));
+    if (!scol.empty())
+        PS_TRY(cudaMemcpy(ps->sell_col, scol.data(), sizeof(int32_t) * scol.size(), cudaMemcpyHostToDevice));
+    PS_TRY(cudaMemset(ps->sell_val, 0, sizeof(double) * std::max<size_t>(scol.size(), 1)));
     PS_TRY(cudaMemset(ps->ticket, 0, sizeof(unsigned)));
 #undef PS_TRY
     *out = ps;
@@ -350,6 +410,7 @@ cudaError_t poisson_finish(PoissonSystem *ps, unsigned *err, int sms, cudaStream
                                                                                   ps->npin);
     const int64_t g = std::max<int64_t>(1, std::min<int64_t>((ps->nc + 255) / 256, (int64_t)sms * 8));
     k_diag_inverse<<<(unsigned)g, 256, 0, s>>>(ps->rowptr, ps->col, ps->val, ps->nc, ps->dinv, err);
+    k_csr_to_sell<<<(unsigned)g, 256, 0, s>>>(ps->rowptr, ps->val, ps->nc, ps->sell_off, ps->sell_val);
     return cudaGetLastError();
 }
 
@@ -357,7 +418,7 @@ cudaError_t poisson_solve(PoissonSystem *ps, const double *b_node, double scale,
                           int max_iter, int sms, cudaStream_t s, int *iters_out, double *rel_res_out,
                           int64_t *launches) {
     const int64_t n = ps->n, nc = ps->nc;
-    const int G = ps->grid;
+    const int G = ps->grid, GM = ps->grid_mv;
     const int64_t gn = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8));
     const double rtol2 = rtol * rtol;
     cudaError_t e;
@@ -371,8 +432,8 @@ cudaError_t poisson_solve(PoissonSystem *ps, const double *b_node, double scale,
         k_zero_at<<<1, 128, 0, s>>>(ps->x, ps->pins, ps->npin);
     }
     // r = b - A x0
-    k_cg_spmv<<<G, kThreads, 0, s>>>(ps->rowptr, ps->col, ps->val, ps->x, ps->q, nc, ps->scal, ps->partial, ps->ticket,
-                                     ps->done);
+    k_cg_spmv<<<GM, kThreads, 0, s>>>(ps->sell_off, ps->sell_w, ps->sell_col, ps->sell_val, ps->x, ps->q, nc,
+                                      ps->scal, ps->partial, ps->ticket, ps->done);
     k_cg_init<<<G, kThreads, 0, s>>>(ps->b, ps->q, ps->dinv, ps->r, ps->z, ps->p, nc, ps->scal, ps->partial, ps->ticket,
                                      ps->done, rtol2);
     *launches += 4 + (ps->npin ? 2 : 0);
@@ -381,8 +442,8 @@ cudaError_t poisson_solve(PoissonSystem *ps, const double *b_node, double scale,
         const int batch = std::min(8, max_iter - it);
         for (int k = 0; k < batch; ++k, ++it) {
             const int par = it & 1;
-            k_cg_spmv<<<G, kThreads, 0, s>>>(ps->rowptr, ps->col, ps->val, ps->p, ps->q, nc, ps->scal, ps->partial,
-                                             ps->ticket, ps->done);
+            k_cg_spmv<<<GM, kThreads, 0, s>>>(ps->sell_off, ps->sell_w, ps->sell_col, ps->sell_val, ps->p, ps->q,
+                                              nc, ps->scal, ps->partial, ps->ticket, ps->done);
             k_cg_update<<<G, kThreads, 0, s>>>(ps->x, ps->r, ps->z, ps->p, ps->q, ps->dinv, nc, ps->scal, par,
                                                ps->partial, ps->ticket, ps->done, ps->iters, rtol2);
             k_cg_pupdate<<<G, kThreads, 0, s>>>(ps->p, ps->z, nc, ps->scal, par, ps->done);

@@ -27,6 +27,8 @@ def main(argv=None) -> int:
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--rk3", action="store_true")
     ap.add_argument("--closure", choices=["vreman", "mlp"], default="vreman")
+    ap.add_argument("--project-iters", type=int, default=0,
+                    help="instead of assemblies: Laplacian set-up, then projections of this many CG iterations")
     a = ap.parse_args(argv)
     import torch
 
@@ -55,6 +57,14 @@ def main(argv=None) -> int:
         mean = np.array([1.0, 1.0, 0.5, -0.5, 1.0, -3.0], np.float32)
         ctx.mlp_load(theta, mean, np.ones(6, np.float32), float(nut.double().mean()) + 1e-12)
     t = time.time()
+    if a.project_iters:
+        dm.poisson_setup()
+        for _ in range(a.reps):
+            dm.project(1e-4, rtol=1e-30, max_iter=a.project_iters)
+        torch.cuda.synchronize()
+        ctx.sync_status()
+        print(f"ok projection {a.reps} x {a.project_iters} CG iterations {time.time() - t:.3f}s", flush=True)
+        return 0
     for _ in range(a.reps):
         if a.rk3:
             dm.rk_step_graph(1e-4, prec=a.prec, closure=a.closure)
