@@ -1242,22 +1242,47 @@ cudaError_t launch_fold(const int32_t *slaves, const int32_t *masters, int64_t n
 // RK stage update (streaming): u^(k+1) = a u^n + b (u^(k) + dt R / M), Dirichlet
 // nodes keep u^n; also refreshes the FP32 packed copy (u, v, w, p).
 
+// FP64 -> FP32, round to nearest even, by integer operations for results in
+// the normal FP32 range (B300's FP64 pipe runs at 1/64 of the FP32 rate and
+// the stage update is otherwise bound by it); zero, subnormal, overflowing,
+// infinite and NaN inputs take the hardware conversion.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    if (e < 897u || e > 1150u) return __double2float_rn(x);
+    const unsigned long long m = b & 0x000FFFFFFFFFFFFFull;
+    const unsigned long long rem = m & 0x1FFFFFFFull;   // the 29 bits dropped
+    unsigned r = (unsigned)(m >> 29);
+    r += (rem > 0x10000000ull || (rem == 0x10000000ull && (r & 1u))) ? 1u : 0u;
+    // a carry out of the 23-bit fraction moves into the exponent, as it must
+    return __uint_as_float(((hi & 0x80000000u) | ((e - 896u) << 23)) + r);
+}
+
+// u^(k+1) = a u^n + b (u^(k) + dt M^-1 R) = a u^n + b u^(k) + c R, c = b dt / M;
+// A0: a = 0 (first stage) reads no u^n except at held nodes
+template <bool A0>
 __global__ void k_rk_update(int64_t n, const double *__restrict__ un, double *uk, double *un_out,
                             const double *__restrict__ rhs, const double *__restrict__ minv,
                             const uint8_t *__restrict__ dirichlet, const double *__restrict__ p64, float4 *up32,
-                            double a, double b, double dt) {
+                            double a, double b, double bdt) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const bool hold = dirichlet && dirichlet[i];
-        const double mi = minv[i];
+        const double c = bdt * minv[i];
         double v[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const double u0 = un[c * n + i];
-            v[c] = hold ? u0 : a * u0 + b * (uk[c * n + i] + dt * rhs[c * n + i] * mi);
-            uk[c * n + i] = v[c];
-            if (un_out) un_out[c * n + i] = v[c];
+        for (int q = 0; q < 3; ++q) {
+            const int64_t k = (int64_t)q * n + i;
+            if (hold)
+                v[q] = un[k];
+            else if (A0)
+                v[q] = fma(c, rhs[k], uk[k]);
+            else
+                v[q] = fma(c, rhs[k], fma(a, un[k], b * uk[k]));
+            uk[k] = v[q];
+            if (un_out) un_out[k] = v[q];
         }
-        up32[i] = make_float4(float(v[0]), float(v[1]), float(v[2]), float(p64[i]));
+        up32[i] = make_float4(f64_to_f32_rn(v[0]), f64_to_f32_rn(v[1]), f64_to_f32_rn(v[2]), f64_to_f32_rn(p64[i]));
     }
 }
 
@@ -1267,7 +1292,10 @@ cudaError_t launch_rk_update(int64_t n, const double *un, double *uk, double *un
     const int t = 256;
     const int64_t want = (n + t - 1) / t;
     const unsigned blocks = (unsigned)(want < 148 * 16 ? (want > 0 ? want : 1) : 148 * 16);
-    k_rk_update<<<blocks, t, 0, s>>>(n, un, uk, un_out, rhs, minv, dirichlet, p64, up32, a, b, dt);
+    if (a == 0.0 && b == 1.0)
+        k_rk_update<true><<<blocks, t, 0, s>>>(n, un, uk, un_out, rhs, minv, dirichlet, p64, up32, a, b, b * dt);
+    else
+        k_rk_update<false><<<blocks, t, 0, s>>>(n, un, uk, un_out, rhs, minv, dirichlet, p64, up32, a, b, b * dt);
     return cudaGetLastError();
 }
 

@@ -68,3 +68,31 @@ def test_graph_step_matches_stages_and_oracle(ctx):
     ref1 = oracle_step(m, f, dt, steps=1)
     upd = np.abs(ref1 - f.u).max()
     assert np.abs(gm - ref1).max() < 2e-4 * upd
+
+
+def test_stage_update_refreshes_the_fp32_field_exactly(ctx):
+    """The stage update rewrites the FP32 copy of the field with its own
+    round-to-nearest FP64 -> FP32 conversion.  A first stage with dt = 1e-300
+    leaves the FP64 state unchanged bit for bit (and zeros stay zero), so the
+    mixed assembly that follows must reproduce the one made right after the
+    field upload, whose FP32 copy the hardware conversion wrote; one ulp of
+    FP32 in u would move the RHS by ~1e-8."""
+    m = mg.channel_mesh(nx=10, ny=12, nz=8, seed=21, n_layers=2, split_frac=0.3)
+    f = mg.channel_field(m, seed=5, nu=1e-3)
+    rng = np.random.default_rng(4)
+    # values over six decades (the conversion's exponent handling), walls at 0
+    u = f.u * (1.0 + rng.standard_normal(f.u.shape)) * 10.0 ** rng.uniform(-3.0, 3.0, (f.u.shape[0], 1))
+    dm = ctx.upload_mesh(m)
+    dm.set_plan("atomic", 128, 256, 0)
+    dm.upload_field(u, f.p, f.nu, f.c_vreman)
+    r0 = torch.empty((3, dm.n_nodes), dtype=torch.float64, device="cuda")
+    dm.assemble(r0, prec="mixed")
+    before = state(dm)
+    dm.rk_stage(0, 1e-300, prec="mixed")
+    after = state(dm)
+    assert np.array_equal(before, after)
+    r1 = torch.empty_like(r0)
+    dm.assemble(r1, prec="mixed")
+    ctx.sync_status()
+    a, b = r0.cpu().numpy(), r1.cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
