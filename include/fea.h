@@ -319,12 +319,28 @@ fea_status fea_sfc_order(int64_t n, const double *xyz, int32_t level, int64_t *o
  * partitioner's steps): element location = centroid, weight = Gauss points
  * of the element's rule (TET04 4, PYR05 8, PEN06 6, HEX08 8), bins of a
  * 2^level grid ordered along the Hilbert curve, the weighted 1-D sequence
- * cut into nparts contiguous runs of nearly equal weight (each bin goes to
- * the part holding the midpoint of its weight interval).  part[t]
- * [n_elem[t]] (host) receives part ids in [0, nparts).  Host only.
- * Errors: FEA_EINVAL (nparts < 1, level out of [1, 21], NULL arrays),
- * FEA_EMESH (node index out of range). */
-fea_status fea_partition_sfc(const fea_mesh_desc *desc, int32_t nparts, int32_t level, int32_t *const part[4]);
+ * cut into nparts contiguous runs; each bin goes to the part whose target
+ * interval holds the midpoint of its weight interval.  Targets: part p gets
+ * lambda[p] / sum(lambda) of the total weight (the correction coefficients
+ * of the load-balancing section; NULL: equal shares).  part[t] [n_elem[t]]
+ * (host) receives part ids in [0, nparts).  Host only.
+ * Errors: FEA_EINVAL (nparts < 1, level out of [1, 21], NULL arrays, a
+ * negative or all-zero lambda), FEA_EMESH (node index out of range). */
+fea_status fea_partition_sfc(const fea_mesh_desc *desc, int32_t nparts, int32_t level, const double *lambda,
+                             int32_t *const part[4]);
+
+/* Correction coefficients of the partition from measured times (the
+ * load-balancing section): observations k = 0..n_obs-1 of the cumulative
+ * coefficients Lambda [n_obs][nparts+1] (Lambda_0 = 0, Lambda_P = P) and of
+ * the per-part times times [n_obs][nparts]; for every splitting point i, a
+ * weighted linear regression (weight 1.5^k, plus the origin with weight 1)
+ * of Upsilon_i = (t_1 + ... + t_i) / mean(t) against Lambda_i is cut with
+ * Upsilon = i, and lambda_out [nparts] = the differences of the new
+ * Lambda (ordered, sum P).  Host only.  Errors: FEA_EINVAL (bad sizes,
+ * negative or all-zero times), FEA_ENUMERIC (a regression without positive
+ * slope). */
+fea_status fea_balance_update(int32_t nparts, int32_t n_obs, const double *Lambda, const double *times,
+                              double *lambda_out);
 
 /* Interface pack: out [3][n_class] (device) is zeroed, then
  * out[c][cls[k]] += v[c][loc[k]] for k < m, c < 3, with v [3][n] (device,

@@ -365,6 +365,36 @@ def project(om: OracleMesh, master, vel_dirichlet, pinned, mass_folded, u_star, 
     return u, np.asarray(p, dtype=np.float64) + dp, dp
 
 
+# ---- correction coefficients of the partition (the load-balancing section) ----
+
+def balance_update(Lambda_hist, times_hist) -> np.ndarray:
+    """New correction coefficients lambda [P] from the observations k of the
+    cumulative coefficients Lambda^k [P+1] (Lambda_0 = 0, Lambda_P = P) and
+    of the per-part times t^k [P], following the section's steps:
+      t_bar^k = mean of t^k;  T_i^k = t_1 + ... + t_i;  Upsilon_i^k = T_i^k / t_bar^k;
+      for every splitting point i: weighted linear regression y = alpha + beta x
+      of the points (Lambda_i^k, Upsilon_i^k), weights 1.5^k, together with the
+      origin (weight 1: no work takes no time); Lambda_i^new = (i - alpha)/beta;
+      lambda_i = Lambda_i^new - Lambda_(i-1)^new.
+    Readings: the section's normalisation sum(lambda) = 1 contradicts its
+    Lambda_P = P and Gamma_i = lambda_i W / P; sum(lambda) = P is taken, and
+    t_bar is the mean time.  Splitting points are kept ordered in [0, P]."""
+    L = np.asarray(Lambda_hist, dtype=np.float64)
+    T = np.asarray(times_hist, dtype=np.float64)
+    K, P = T.shape
+    new = np.zeros(P + 1)
+    new[P] = P
+    for i in range(1, P):
+        x = [0.0] + [L[k, i] for k in range(K)]
+        y = [0.0] + [T[k, :i].sum() / T[k].mean() for k in range(K)]
+        w = np.array([1.0] + [1.5 ** k for k in range(K)])
+        beta, alpha = np.polyfit(np.array(x), np.array(y), 1, w=np.sqrt(w))   # polyfit weighs the residuals
+        new[i] = (i - alpha) / beta
+    for i in range(1, P):
+        new[i] = min(max(new[i], new[i - 1]), P)
+    return np.diff(new)
+
+
 def periodic_fold(master: np.ndarray, v: np.ndarray) -> np.ndarray:
     v = np.ascontiguousarray(v, dtype=np.float64).copy()
     ncomp = 1 if v.ndim == 1 else v.shape[1]

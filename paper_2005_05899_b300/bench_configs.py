@@ -3,7 +3,8 @@
 the learned closure (trained on filtered fine Taylor-Green runs, then fused
 into the assembly of an 8M-element mixed channel mesh against Vreman).
 
-    python -m paper_2005_05899_b300.bench_configs [--channel] [--batch] [--closure] [--projection] [--reps 20]
+    python -m paper_2005_05899_b300.bench_configs [--channel] [--batch] [--closure] [--projection] [--balance]
+        [--reps 20]
 
 Prints one JSON line per measurement (CUDA-event times on the current stream,
 after warm-up; inputs are larger than L2 for the channel and the batch).
@@ -212,16 +213,58 @@ def projection(n_axis: int = 170, dt: float = 2e-4, rtol: float = 1e-6, steps: i
                       "setup_s": setup_s, "dt": dt, "rtol": rtol, "steps": res}), flush=True)
 
 
+def part_times(ctx, mesh, field, parts, reps: int):
+    """Assembly time of every part (mixed precision, Vreman, autotuned plan
+    of the first call), parts uploaded as meshes of their own, timed one
+    after the other with CUDA events."""
+    import torch
+    times = []
+    for part in parts:
+        dm = ctx.upload_mesh(part.mesh)
+        dm.upload_field(field.u[part.nodes], field.p[part.nodes], field.nu, field.c_vreman)
+        out = torch.empty((3, dm.n_nodes), dtype=torch.float64, device="cuda")
+        times.append(_time_assemble(dm, out, reps))
+        del dm
+    return times
+
+
+def balance(reps: int, n_parts: int = 4, iters: int = 8, n_axis: int = 140):
+    """The correction coefficients on measured times: the airplane-like mesh
+    (tets everywhere, FP64-Jacobian prisms around the body) split into
+    n_parts by the Gauss-point cost model, each part's assembly timed on the
+    GPU, the partition corrected from the times, repeated."""
+    from . import fea
+    from . import meshgen as mg
+    from . import partition as P
+    m = mg.airplane_mesh(n_axis, seed=4)
+    f = mg.inflow_field(m, seed=5)
+    ctx = fea.Context(0)
+    bal = P.Balancer(n_parts)
+    hist = []
+    for k in range(iters):
+        parts = P.build_parts(m, n_parts, lam=bal.lam)
+        t = part_times(ctx, m, f, parts, reps)
+        hist.append({"iteration": k, "lambda": [round(x, 4) for x in bal.lam], "part_ms": [round(x, 4) for x in t],
+                     "imbalance": round(P.Balancer.imbalance(t), 4),
+                     "elements": [int(sum(v.size for v in p.elems.values())) for p in parts]})
+        bal.update(t)
+    ctx.sync_status()
+    print(json.dumps({"workload": f"airplane-like {n_axis}^3 ({m.n_elem_total:,} elements: {m.counts()}) in "
+                                  f"{n_parts} parts, Gauss-point weights corrected from measured part times",
+                      "iterations": hist}), flush=True)
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--channel", action="store_true")
     ap.add_argument("--batch", action="store_true")
     ap.add_argument("--closure", action="store_true")
     ap.add_argument("--projection", action="store_true")
+    ap.add_argument("--balance", action="store_true")
     ap.add_argument("--n-f", type=int, default=256, help="fine Taylor-Green grid of the closure's training runs")
     ap.add_argument("--reps", type=int, default=20)
     a = ap.parse_args(argv)
-    if not (a.channel or a.batch or a.closure or a.projection):
+    if not (a.channel or a.batch or a.closure or a.projection or a.balance):
         a.channel = a.batch = True
     if a.channel:
         channel(a.reps)
@@ -231,6 +274,8 @@ def main(argv=None) -> int:
         closure(a.reps, n_f=a.n_f)
     if a.projection:
         projection()
+    if a.balance:
+        balance(a.reps)
     return 0
 
 

@@ -1,5 +1,6 @@
-// Space-filling-curve order of points and SFC partition of a mesh's elements
-// (section 5, the SFC-based partitioner): a bounding box, a regular grid of
+// Space-filling-curve order of points, SFC partition of a mesh's elements
+// and the correction coefficients of the partition (section 5 and the
+// load-balancing section).  The partitioner: a bounding box, a regular grid of
 // bins inside it, bins weighted by their elements (weight = Gauss points of
 // the element's rule), the bins projected to 1-D along a space-filling curve,
 // and the weighted 1-D sequence cut into contiguous parts.  The curve is a
@@ -104,8 +105,18 @@ fea_status fea_sfc_order(int64_t n, const double *xyz, int32_t level, int64_t *o
     return FEA_OK;
 }
 
-fea_status fea_partition_sfc(const fea_mesh_desc *desc, int32_t nparts, int32_t level, int32_t *const part[4]) {
+fea_status fea_partition_sfc(const fea_mesh_desc *desc, int32_t nparts, int32_t level, const double *lambda,
+                             int32_t *const part[4]) {
     if (!desc || !part || nparts < 1 || level < 1 || level > 21 || desc->n_nodes < 0 || !desc->xyz) return FEA_EINVAL;
+    // cumulative target fractions: part p ends at (lambda_0 + ... + lambda_p) / P
+    std::vector<double> cum((size_t)nparts + 1, 0.0);
+    for (int32_t p = 0; p < nparts; ++p) {
+        const double l = lambda ? lambda[p] : 1.0;
+        if (!(l >= 0.0)) return FEA_EINVAL;
+        cum[(size_t)p + 1] = cum[(size_t)p] + l;
+    }
+    if (!(cum[(size_t)nparts] > 0.0)) return FEA_EINVAL;
+    for (auto &c : cum) c /= cum[(size_t)nparts];
     const int64_t n = desc->n_nodes;
     // element centroids (the "location of each element" of the partitioner)
     std::vector<double> cen[3];
@@ -148,7 +159,9 @@ fea_status fea_partition_sfc(const fea_mesh_desc *desc, int32_t nparts, int32_t 
         int64_t k1 = k;
         double w = 0.0;
         while (k1 < N && key[(size_t)idx[(size_t)k1]] == key[(size_t)idx[(size_t)k]]) w += weight[(size_t)idx[(size_t)k1++]];
-        int32_t p = (int32_t)std::floor((before + 0.5 * w) * nparts / total);
+        // the part whose target interval holds the midpoint of the bin's weight
+        const double mid = (before + 0.5 * w) / total;
+        int32_t p = (int32_t)(std::upper_bound(cum.begin() + 1, cum.end(), mid) - (cum.begin() + 1));
         p = std::min(std::max(p, 0), nparts - 1);
         for (int64_t j = k; j < k1; ++j) {
             const auto &te = who[(size_t)idx[(size_t)j]];
@@ -157,6 +170,46 @@ fea_status fea_partition_sfc(const fea_mesh_desc *desc, int32_t nparts, int32_t 
         before += w;
         k = k1;
     }
+    return FEA_OK;
+}
+
+fea_status fea_balance_update(int32_t nparts, int32_t n_obs, const double *Lambda, const double *times,
+                              double *lambda_out) {
+    if (nparts < 1 || n_obs < 1 || !Lambda || !times || !lambda_out) return FEA_EINVAL;
+    const size_t P = (size_t)nparts;
+    std::vector<double> Lnew(P + 1, 0.0);
+    Lnew[P] = (double)nparts;
+    for (size_t i = 1; i < P; ++i) {
+        // weighted least squares over (Lambda_i^k, Upsilon_i^k), k = 0..n_obs-1 (weights 1.5^k),
+        // plus the origin (no weight takes no time) with weight 1
+        double sw = 1.0, sx = 0.0, sy = 0.0, sxx = 0.0, sxy = 0.0;
+        double wk = 1.0;
+        for (int32_t k = 0; k < n_obs; ++k, wk *= 1.5) {
+            const double *t = times + (size_t)k * P;
+            double total = 0.0, head = 0.0;
+            for (size_t j = 0; j < P; ++j) {
+                if (!(t[j] >= 0.0)) return FEA_EINVAL;
+                total += t[j];
+                if (j < i) head += t[j];
+            }
+            if (!(total > 0.0)) return FEA_EINVAL;
+            const double x = Lambda[(size_t)k * (P + 1) + i];
+            const double y = head / (total / (double)nparts);   // Upsilon_i = T_i / mean time
+            sw += wk;
+            sx += wk * x;
+            sy += wk * y;
+            sxx += wk * x * x;
+            sxy += wk * x * y;
+        }
+        const double den = sw * sxx - sx * sx;
+        if (!(std::fabs(den) > 0.0)) return FEA_ENUMERIC;
+        const double beta = (sw * sxy - sx * sy) / den, alpha = (sy - beta * sx) / sw;
+        if (!(beta > 0.0)) return FEA_ENUMERIC;
+        Lnew[i] = ((double)i - alpha) / beta;
+    }
+    // keep the splitting points ordered inside [0, P]
+    for (size_t i = 1; i < P; ++i) Lnew[i] = std::min(std::max(Lnew[i], Lnew[i - 1]), (double)nparts);
+    for (size_t i = 0; i < P; ++i) lambda_out[i] = Lnew[i + 1] - Lnew[i];
     return FEA_OK;
 }
 

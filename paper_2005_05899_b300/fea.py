@@ -34,6 +34,7 @@ EXPORTED = (
     "fea_mlp_load", "fea_mlp_get", "fea_mlp_forward", "fea_mlp_train_step", "fea_mlp_set_envelope",
     "fea_mlp_fallback_read", "fea_sfc_order", "fea_partition_sfc", "fea_interface_pack", "fea_interface_unpack",
     "fea_poisson_setup", "fea_poisson_solve", "fea_divergence", "fea_gradient", "fea_project",
+    "fea_balance_update",
 )
 MLP_NPARAM = 8833
 NOALLOC_MAX_NODES = 262144
@@ -72,6 +73,21 @@ def mesh_desc(mesh):
     return d, keep, n_elem
 
 
+def balance_update(Lambda_hist, times_hist) -> np.ndarray:
+    """New correction coefficients from the history of cumulative coefficients
+    Lambda [k][P+1] and measured per-part times [k][P] (host)."""
+    L = np.ascontiguousarray(Lambda_hist, dtype=np.float64)
+    T = np.ascontiguousarray(times_hist, dtype=np.float64)
+    k, P = T.shape
+    assert L.shape == (k, P + 1)
+    out = np.zeros(P)
+    st = lib().fea_balance_update(int(P), int(k), L.ctypes.data_as(ctypes.c_void_p), T.ctypes.data_as(ctypes.c_void_p),
+                                  out.ctypes.data_as(ctypes.c_void_p))
+    if st:
+        raise FeaError(st, "fea_balance_update failed")
+    return out
+
+
 def sfc_order(xyz, level: int = 10) -> np.ndarray:
     """Hilbert-curve order of points xyz (N, 3) binned on a 2^level grid (host)."""
     x = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).T)
@@ -83,12 +99,15 @@ def sfc_order(xyz, level: int = 10) -> np.ndarray:
     return out
 
 
-def partition_sfc(mesh, nparts: int, level: int = 10) -> dict:
-    """SFC partition of the elements: {etype: part id per element} (host)."""
+def partition_sfc(mesh, nparts: int, level: int = 10, lam=None) -> dict:
+    """SFC partition of the elements: {etype: part id per element} (host);
+    lam: optional correction coefficients [nparts] (target shares)."""
     d, keep, n_elem = mesh_desc(mesh)
     parts = {t: np.zeros(n_elem[t], np.int32) for t in range(4)}
     ptrs = (ctypes.c_void_p * 4)(*[parts[t].ctypes.data if n_elem[t] else None for t in range(4)])
-    st = lib().fea_partition_sfc(ctypes.byref(d), int(nparts), int(level), ptrs)
+    lam_a = None if lam is None else np.ascontiguousarray(lam, dtype=np.float64)
+    st = lib().fea_partition_sfc(ctypes.byref(d), int(nparts), int(level),
+                                 None if lam_a is None else lam_a.ctypes.data_as(ctypes.c_void_p), ptrs)
     if st:
         raise FeaError(st, "fea_partition_sfc failed")
     return {t: parts[t] for t in range(4) if n_elem[t]}
@@ -163,7 +182,8 @@ def lib() -> ctypes.CDLL:
         L.fea_divergence.argtypes = [vp, i32, vp, vp, vp]
         L.fea_gradient.argtypes = [vp, i32, vp, vp, vp]
         L.fea_project.argtypes = [vp, i32, dbl, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl), vp]
-        L.fea_partition_sfc.argtypes = [ctypes.POINTER(MeshDesc), i32, i32, ctypes.c_void_p * 4]
+        L.fea_partition_sfc.argtypes = [ctypes.POINTER(MeshDesc), i32, i32, vp, ctypes.c_void_p * 4]
+        L.fea_balance_update.argtypes = [i32, i32, vp, vp, vp]
         L.fea_interface_pack.argtypes = [vp, vp, i64, vp, vp, i64, vp, i64, vp]
         L.fea_interface_unpack.argtypes = [vp, vp, i64, vp, vp, i64, vp, i64, vp]
         L.fea_mlp_fallback_read.argtypes = [vp, ctypes.POINTER(i64), ctypes.c_int]

@@ -46,12 +46,13 @@ class Part:
 
 
 def build_parts(mesh: Mesh, n_parts: int, level: int = 10,
-                part_of: Optional[Dict[int, np.ndarray]] = None) -> List[Part]:
-    """Splits `mesh` into `n_parts` parts (SFC partition unless `part_of`, a
-    part id per element and type, is given).  Every rank calls this with the
-    same mesh and gets the same parts."""
+                part_of: Optional[Dict[int, np.ndarray]] = None, lam=None) -> List[Part]:
+    """Splits `mesh` into `n_parts` parts (SFC partition with correction
+    coefficients `lam`, unless `part_of`, a part id per element and type, is
+    given).  Every rank calls this with the same mesh and gets the same
+    parts."""
     if part_of is None:
-        part_of = fea.partition_sfc(mesh, n_parts, level)
+        part_of = fea.partition_sfc(mesh, n_parts, level, lam)
     N = mesh.n_nodes
     cls_of = (np.asarray(mesh.periodic_master, dtype=np.int64) if mesh.periodic_master is not None
               else np.arange(N, dtype=np.int64))
@@ -97,6 +98,31 @@ def build_parts(mesh: Mesh, n_parts: int, level: int = 10,
         out.append(Part(index=p, mesh=sub, nodes=nodes, elems=elems, iface_loc=iface_loc,
                         iface_cls=shared_no[cls[iface_loc]], n_shared=int(shared.size)))
     return out
+
+
+class Balancer:
+    """Correction coefficients of the partition from measured times (the
+    load-balancing section): keeps the history of cumulative coefficients
+    and per-part times and asks the library for the next coefficients."""
+
+    def __init__(self, n_parts: int):
+        self.n_parts = n_parts
+        self.lam = np.ones(n_parts)
+        self.Lambda_hist: List[np.ndarray] = []
+        self.times_hist: List[np.ndarray] = []
+
+    @staticmethod
+    def imbalance(times) -> float:
+        t = np.asarray(times, dtype=np.float64)
+        return float(t.max() / t.mean())
+
+    def update(self, times) -> np.ndarray:
+        """Records the times measured with the current coefficients; returns
+        the next coefficients (also kept in self.lam)."""
+        self.Lambda_hist.append(np.concatenate([[0.0], np.cumsum(self.lam)]))
+        self.times_hist.append(np.asarray(times, dtype=np.float64))
+        self.lam = fea.balance_update(np.array(self.Lambda_hist), np.array(self.times_hist))
+        return self.lam
 
 
 class Exchange:
