@@ -245,7 +245,8 @@ fea_status fea_mlp_fallback_read(fea_ctx *ctx, int64_t *points, int reset);
 /* Copies the current FP32 parameters to theta_out [8833] (host or device). */
 fea_status fea_mlp_get(fea_ctx *ctx, float *theta_out, void *stream);
 
-/* nu_t for B rows of raw features x [B][6] (device) into nut [B] (device). */
+/* nu_t for B rows of raw features x [B][6] (device) into nut [B] (device);
+ * B = 0 is a no-op (x and nut may then be NULL). */
 fea_status fea_mlp_forward(fea_ctx *ctx, const float *x, int64_t B, float *nut, void *stream);
 
 /* One training step on B samples: raw features x [B][6] and targets y [B]

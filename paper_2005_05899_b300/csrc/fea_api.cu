@@ -1423,7 +1423,7 @@ fea_status fea_mlp_get(fea_ctx *ctx, float *theta_out, void *stream) {
 
 fea_status fea_mlp_forward(fea_ctx *ctx, const float *x, int64_t B, float *nut, void *stream) {
     if (!ctx) return FEA_EINVAL;
-    if (!x || !nut || B < 0) return fail(ctx, FEA_EINVAL, "bad MLP forward arguments");
+    if (B < 0 || (B > 0 && (!x || !nut))) return fail(ctx, FEA_EINVAL, "bad MLP forward arguments");
     if (!ctx->mlp_ready) return fail(ctx, FEA_ESTATE, "no MLP loaded");
     CK(launch_mlp_forward(ctx->mlp_w.p, x, B, nut, ctx->sms, (cudaStream_t)stream));
     ctx->launches++;

@@ -150,6 +150,13 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(const double *b, const dou
     }
 }
 
+// b = 0: the solution is x = 0 (pinned classes fix the constant)
+__global__ void k_cg_zero_if_b0(double *x, int64_t nc, const double *scal) {
+    if (scal[S_BB] != 0.0) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = 0.0;
+}
+
 // alpha = rz / pq; x += alpha p; r -= alpha q; z = D^-1 r; new rz, rr
 __global__ void __launch_bounds__(kThreads) k_cg_update(double *x, double *r, double *z, const double *p,
                                                         const double *q, const double *dinv, int64_t nc,
@@ -436,7 +443,8 @@ cudaError_t poisson_solve(PoissonSystem *ps, const double *b_node, double scale,
                                       ps->scal, ps->partial, ps->ticket, ps->done);
     k_cg_init<<<G, kThreads, 0, s>>>(ps->b, ps->q, ps->dinv, ps->r, ps->z, ps->p, nc, ps->scal, ps->partial, ps->ticket,
                                      ps->done, rtol2);
-    *launches += 4 + (ps->npin ? 2 : 0);
+    k_cg_zero_if_b0<<<G, kThreads, 0, s>>>(ps->x, nc, ps->scal);
+    *launches += 5 + (ps->npin ? 2 : 0);
     int it = 0, done_h = 0;
     while (it < max_iter) {
         const int batch = std::min(8, max_iter - it);
