@@ -92,6 +92,18 @@ typedef enum {
                                chunk shares with other chunks */
 } fea_scatter;
 
+/* convective form (section 2.1 writes the EMAC bracket; see fea_set_model) */
+typedef enum {
+    FEA_CONV_GU = 0,    /* c = G u + (tr G) u: the bracket evaluated pointwise on the interpolant */
+    FEA_CONV_EMAC = 1   /* c = 2 eps u + (tr G) u - 1/2 grad (|u|^2)_h, (|u|^2)_h = sum_a N_a |u_a|^2 */
+} fea_conv_form;
+
+/* filter width of the Vreman closure */
+typedef enum {
+    FEA_DELTA_VOLUME = 0,   /* Delta = V_e^(1/3) */
+    FEA_DELTA_AXES = 1      /* a width per direction: the element's extents along the axes */
+} fea_delta_form;
+
 typedef struct fea_ctx fea_ctx;
 
 /* Mesh description for fea_mesh_upload.  All pointers: HOST memory, read
@@ -257,6 +269,16 @@ fea_status fea_mlp_forward(fea_ctx *ctx, const float *x, int64_t B, float *nut, 
  * host or device, [8833]) the gradient d loss / d theta. */
 fea_status fea_mlp_train_step(fea_ctx *ctx, const float *x, const float *y, int64_t B, float lr, float *loss_out,
                               float *grad_out, void *stream);
+
+/* Model variants of a mesh's assembly (default FEA_CONV_GU, FEA_DELTA_VOLUME).
+ * FEA_CONV_EMAC: the convective term with the kinetic-energy gradient taken
+ * from the interpolated nodal |u|^2, which differs from the pointwise form by
+ * G^T u - 1/2 grad (|u|^2)_h.  FEA_DELTA_AXES: Vreman's beta_ij =
+ * sum_m Delta_m^2 alpha_mi alpha_mj with Delta_m the element's extent along
+ * axis m (the model as written for anisotropic grids).  The fused TET04
+ * pipeline serves the defaults; other forms run in the generic kernels.
+ * Drops a captured RK graph of the mesh.  Errors: FEA_EINVAL. */
+fea_status fea_set_model(fea_ctx *ctx, int32_t mesh, int32_t conv_form, int32_t delta_form);
 
 /* ---- pressure projection (Algorithm 1) -----------------------------------
  * Algorithm 1 assembles the Laplacian matrix once, and each time step ends

@@ -58,7 +58,8 @@ class _Mlp(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("c_vreman", ctypes.c_double), ("closure", ctypes.c_int),
-                ("mask", ctypes.c_uint32), ("mlp", ctypes.POINTER(_Mlp))]
+                ("mask", ctypes.c_uint32), ("mlp", ctypes.POINTER(_Mlp)), ("conv_form", ctypes.c_int),
+                ("delta_form", ctypes.c_int)]
 
 
 _lib = None
@@ -70,6 +71,7 @@ def lib():
         _lib = ctypes.CDLL(build())
         dp = ctypes.POINTER(ctypes.c_double)
         _lib.orc_vreman.restype = ctypes.c_double
+        _lib.orc_vreman_aniso.restype = ctypes.c_double
         _lib.orc_mlp_loss_grad.restype = ctypes.c_double
         _lib.orc_bad_element.restype = ctypes.c_int64
         _lib.orc_quadrature.argtypes = [ctypes.c_int, dp, dp]
@@ -158,8 +160,10 @@ def nparam() -> int:
     return int(lib().orc_mlp_nparam())
 
 
-def _params(nu, c_vreman, closure, mask, mlp: Optional[MLPParams]):
+def _params(nu, c_vreman, closure, mask, mlp: Optional[MLPParams], conv_form: int = 0, delta_form: int = 0):
     prm = _Params()
+    prm.conv_form = int(conv_form)
+    prm.delta_form = int(delta_form)
     prm.nu = float(nu)
     prm.c_vreman = float(c_vreman)
     prm.closure = CLOSURE[closure] if isinstance(closure, str) else int(closure)
@@ -212,6 +216,12 @@ def element_mass(etype: int, X: np.ndarray) -> np.ndarray:
     return Ae
 
 
+def vreman_aniso(G: np.ndarray, dm, c: float) -> float:
+    G = np.ascontiguousarray(G, dtype=np.float64).reshape(9)
+    d = np.ascontiguousarray(dm, dtype=np.float64)
+    return float(lib().orc_vreman_aniso(_dp(G), _dp(d), ctypes.c_double(c)))
+
+
 def vreman(G: np.ndarray, delta: float, c: float) -> float:
     G = np.ascontiguousarray(G, dtype=np.float64).reshape(9)
     return float(lib().orc_vreman(_dp(G), ctypes.c_double(delta), ctypes.c_double(c)))
@@ -251,14 +261,15 @@ def adam_step(theta, grad, m1, m2, lr, beta1, beta2, eps, t):
 
 def assemble_rhs(om: OracleMesh, u: np.ndarray, p: np.ndarray, nu: float, c_vreman: float = 0.07,
                  closure="vreman", mask: int = TERM_ALL, mlp: Optional[MLPParams] = None,
-                 want_nut: bool = False, want_vol: bool = False):
+                 want_nut: bool = False, want_vol: bool = False, conv_form: int = 0, delta_form: int = 0):
     """Serial FP64 assembly in natural element order.  Returns rhs (N, 3) and,
-    on request, nu_t per type (E_t, ng) and element volumes per type (E_t,)."""
+    on request, nu_t per type (E_t, ng) and element volumes per type (E_t,).
+    conv_form 1: EMAC convective form; delta_form 1: per-direction Vreman widths."""
     u = np.ascontiguousarray(u, dtype=np.float64)
     p = np.ascontiguousarray(p, dtype=np.float64)
     assert u.shape == (om.n_nodes, 3) and p.shape == (om.n_nodes,)
     rhs = np.zeros((om.n_nodes, 3))
-    prm = _params(nu, c_vreman, closure, mask, mlp)
+    prm = _params(nu, c_vreman, closure, mask, mlp, conv_form, delta_form)
     nut = {t: np.zeros((c.shape[0], NGAUSS[t])) for t, c in om.conn.items()} if want_nut else {}
     vol = {t: np.zeros(c.shape[0]) for t, c in om.conn.items()} if want_vol else {}
     nut_arr = (ctypes.POINTER(ctypes.c_double) * 4)()

@@ -87,6 +87,8 @@ typedef struct {
     int closure;
     uint32_t mask;
     const orc_mlp *mlp;
+    int conv_form;    /* 0: c = G u + (tr G) u;  1: EMAC, c = 2 eps u + (tr G) u - 1/2 grad (|u|^2)_h */
+    int delta_form;   /* 0: Delta = V^(1/3);  1: per-direction widths (element extents) in Vreman */
 } orc_params;
 
 int orc_nnode(int etype) {
@@ -320,6 +322,26 @@ double orc_vreman(const double *G /*[3][3]*/, double delta, double c) {
     return c * sqrt(B / aa);
 }
 
+/* Vreman with a filter width per direction (Vreman 2004 writes the model
+ * for an anisotropic grid): beta_ij = sum_m Delta_m^2 alpha_mi alpha_mj with
+ * alpha = G^T, i.e. beta = H H^T for H = G diag(Delta).  Its principal 2x2
+ * minors are |h_i x h_j|^2 (h_i = row i of H, Lagrange identity), so
+ * B_beta = |h_1 x h_2|^2 + |h_1 x h_3|^2 + |h_2 x h_3|^2. */
+double orc_vreman_aniso(const double *G /*[3][3]*/, const double *dm /*[3]*/, double c) {
+    double aa = 0.0, H[9];
+    for (int k = 0; k < 9; ++k) aa += G[k] * G[k];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) H[3 * i + j] = G[3 * i + j] * dm[j];
+    double x12[3], x13[3], x23[3];
+    cross3(H, H + 3, x12);
+    cross3(H, H + 6, x13);
+    cross3(H + 3, H + 6, x23);
+    double B = 0.0;
+    for (int i = 0; i < 3; ++i) B += x12[i] * x12[i] + x13[i] * x13[i] + x23[i] * x23[i];
+    if (aa == 0.0 || B <= 0.0) return 0.0;
+    return c * sqrt(B / aa);
+}
+
 /* ---------------------------------------------------------------------- */
 /* MLP closure.  Features from S = (G + G^T)/2 and O = (G - G^T)/2:
  *   I1 = tr S^2, I2 = tr O^2, I3 = tr S^3, I4 = tr S O^2, I5 = tr S^2 O^2,
@@ -404,6 +426,16 @@ static int element_rhs(int etype, const double *X, const double *U, const double
     for (int g = 0; g < ng; ++g) V += W[g];
     if (vol) *vol = V;
     const double delta = cbrt(V);
+    /* per-direction widths: the element's extents along the axes */
+    double dm[3];
+    for (int i = 0; i < 3; ++i) {
+        double lo = X[i], hi = X[i];
+        for (int a = 1; a < nen; ++a) {
+            lo = fmin(lo, X[3 * a + i]);
+            hi = fmax(hi, X[3 * a + i]);
+        }
+        dm[i] = hi - lo;
+    }
     memset(r, 0, sizeof(double) * 3 * nen);
     for (int g = 0; g < ng; ++g) {
         const double *Ng = N + g * nen;
@@ -423,7 +455,7 @@ static int element_rhs(int etype, const double *X, const double *U, const double
         double nut_g = 0.0;
         if ((prm->mask & ORC_TERM_SGS) || nut) {
             if (prm->closure == ORC_CLOSURE_VREMAN) {
-                nut_g = orc_vreman(G, delta, prm->c_vreman);
+                nut_g = prm->delta_form ? orc_vreman_aniso(G, dm, prm->c_vreman) : orc_vreman(G, delta, prm->c_vreman);
             } else if (prm->closure == ORC_CLOSURE_MLP && prm->mlp) {
                 double f[MLP_IN];
                 orc_mlp_features(G, delta, f);
@@ -432,12 +464,22 @@ static int element_rhs(int etype, const double *X, const double *U, const double
         }
         if (nut) nut[g] = nut_g;
         double cvec[3] = {0, 0, 0};
-        if (prm->mask & ORC_TERM_CONV)
+        if (prm->mask & ORC_TERM_CONV) {
+            /* EMAC: grad of the interpolated kinetic energy (|u|^2)_h = sum_a N_a |u_a|^2 */
+            double k[3] = {0, 0, 0};
+            if (prm->conv_form)
+                for (int a = 0; a < nen; ++a) {
+                    const double q = U[3 * a] * U[3 * a] + U[3 * a + 1] * U[3 * a + 1] + U[3 * a + 2] * U[3 * a + 2];
+                    for (int i = 0; i < 3; ++i) k[i] += q * dg[3 * a + i];
+                }
             for (int i = 0; i < 3; ++i) {
                 double s = trG * ug[i];
                 for (int j = 0; j < 3; ++j) s += G[3 * i + j] * ug[j];
-                cvec[i] = s;
+                if (prm->conv_form)
+                    for (int j = 0; j < 3; ++j) s += G[3 * j + i] * ug[j];
+                cvec[i] = prm->conv_form ? s - 0.5 * k[i] : s;
             }
+        }
         double f0[3];
         for (int i = 0; i < 3; ++i) f0[i] = cvec[i] + ((prm->mask & ORC_TERM_PRES) ? gp[i] : 0.0);
         double visc = 0.0;

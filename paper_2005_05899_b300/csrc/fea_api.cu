@@ -256,6 +256,7 @@ struct Mesh {
     fea_plan plan{FEA_SCATTER_CHUNK, 256, 256, 0};
     GraphCache graph;
     std::vector<int32_t> master_h;      // host periodic masters (empty: none)
+    int conv_form = 0, delta_form = 0;  // model variants (fea_set_model)
     PoissonSystem *poisson = nullptr;   // pressure equation (fea_poisson_setup)
     DevBuf<double> proj_b, proj_dp, proj_g;
     ~Mesh() {
@@ -272,6 +273,8 @@ struct Mesh {
         f.up32 = up32.p;
         f.nu = nu;
         f.c_vreman = c_vreman;
+        f.conv_form = conv_form;
+        f.delta_form = delta_form;
         return f;
     }
 };
@@ -1240,6 +1243,22 @@ fea_status fea_mlp_load(fea_ctx *ctx, const float *theta, const float *feat_mean
     ctx->mlp_step = 0;
     ctx->mlp_scale = out_scale;
     ctx->mlp_ready = true;
+    return FEA_OK;
+}
+
+fea_status fea_set_model(fea_ctx *ctx, int32_t mesh, int32_t conv_form, int32_t delta_form) {
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    if (conv_form != FEA_CONV_GU && conv_form != FEA_CONV_EMAC) return fail(ctx, FEA_EINVAL, "unknown convective form");
+    if (delta_form != FEA_DELTA_VOLUME && delta_form != FEA_DELTA_AXES)
+        return fail(ctx, FEA_EINVAL, "unknown filter-width form");
+    m->conv_form = conv_form;
+    m->delta_form = delta_form;
+    if (m->graph.exec) {   // a captured step holds the old field descriptor
+        cudaGraphExecDestroy(m->graph.exec);
+        m->graph.exec = nullptr;
+    }
     return FEA_OK;
 }
 

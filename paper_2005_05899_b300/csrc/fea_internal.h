@@ -70,6 +70,8 @@ struct FieldDev {
     const float4 *up32;   // [n] (u, v, w, p), FP32 copy of the state
     double nu;
     double c_vreman;
+    int conv_form = 0;    // fea_conv_form: 0 G u + (tr G) u, 1 EMAC
+    int delta_form = 0;   // fea_delta_form: 0 V^(1/3), 1 widths per direction
 };
 
 struct AsmArgs {

@@ -91,6 +91,45 @@ __device__ __forceinline__ void set_err(unsigned *err, unsigned bit) {
 // ---------------------------------------------------------------------------
 // gather helpers
 
+// Vreman with a width per direction: beta = H H^T, H = G diag(dm), so
+// B_beta = sum over row pairs of |h_i x h_j|^2 and nu_t = c sqrt(B_beta / G:G).
+template <typename R>
+__device__ __forceinline__ R vreman_aniso(const R G[3][3], const R dm[3], R c) {
+    R H[3][3], aa = R(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            aa += G[i][j] * G[i][j];
+            H[i][j] = G[i][j] * dm[j];
+        }
+    R B = R(0);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const int i = p == 2 ? 1 : 0, j = p == 0 ? 1 : 2;
+        const R x = H[i][1] * H[j][2] - H[i][2] * H[j][1];
+        const R y = H[i][2] * H[j][0] - H[i][0] * H[j][2];
+        const R z = H[i][0] * H[j][1] - H[i][1] * H[j][0];
+        B += x * x + y * y + z * z;
+    }
+    return (aa > R(0) && B > R(0)) ? c * sqrt(B / aa) : R(0);
+}
+
+// element extents along the axes (the per-direction filter widths)
+template <int NEN, typename R, typename XR>
+__device__ __forceinline__ void element_extents(const XR X[][3], R dm[3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        XR lo = X[0][i], hi = X[0][i];
+#pragma unroll
+        for (int a = 1; a < NEN; ++a) {
+            lo = X[a][i] < lo ? X[a][i] : lo;
+            hi = X[a][i] > hi ? X[a][i] : hi;
+        }
+        dm[i] = R(hi - lo);
+    }
+}
+
 template <typename R, bool J64>
 struct Gathered {
     R U[kMaxNen][3];
@@ -221,6 +260,16 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
     constexpr int nen = kNen[ET], ng = kNg[ET];
     const uint32_t mask = args.mask;
     const bool want_q = !MLP && args.closure == FEA_CLOSURE_VREMAN && ((mask & FEA_TERM_SGS) || nut_out);
+    // model variants: EMAC needs |u_a|^2 at the nodes, anisotropic Vreman the extents
+    const bool emac = f.conv_form == 1 && (mask & FEA_TERM_CONV);
+    const bool aniso = f.delta_form == 1;
+    R q2[kMaxNen];
+    if (emac) {
+#pragma unroll
+        for (int a = 0; a < nen; ++a) q2[a] = el.U[a][0] * el.U[a][0] + el.U[a][1] * el.U[a][1] + el.U[a][2] * el.U[a][2];
+    }
+    R dm[3] = {R(0), R(0), R(0)};
+    if (aniso) element_extents<nen, R>(el.X, dm);
     const R nu = (mask & FEA_TERM_VISC) ? R(f.nu) : R(0);
     const R cv = R(f.c_vreman);
     R rs[kMaxNen][3];
@@ -280,7 +329,8 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
 #pragma unroll
             for (int i = 0; i < 3; ++i) G[i][j] = Gx[i][0] * Ji[0][j] + Gx[i][1] * Ji[1][j] + Gx[i][2] * Ji[2][j];
         }
-        R q = want_q ? vreman(G, R(1), cv) : R(0);
+        // nu_t / Delta^2 (isotropic, scaled once V is known) or nu_t itself (per-direction widths)
+        R q = want_q ? (aniso ? vreman_aniso(G, dm, cv) : vreman(G, R(1), cv)) : R(0);
         const R visc_g = nu;
         if constexpr (MLP) {
             float Gf[3][3];
@@ -296,18 +346,31 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
             row[2] = wds[2];
             row[3] = 0u;
             inside_mask |= (uint32_t)inside << g;
-            // with an envelope, Vreman's q = nu_t / Delta^2 for the fallback
-            if (mu.w->env_on) qtile[g * 32 + lane] = float(vreman(G, R(1), cv));
+            // with an envelope, Vreman's q = nu_t / Delta^2 (nu_t itself with
+            // per-direction widths) for the fallback
+            if (mu.w->env_on) qtile[g * 32 + lane] = float(aniso ? vreman_aniso(G, dm, cv) : vreman(G, R(1), cv));
         } else {
             if (nut_out) nut_out[g] = float(q);
         }
         const R qs = (mask & FEA_TERM_SGS) ? q : R(0);
         const R trG = G[0][0] + G[1][1] + G[2][2];
+        // EMAC: + G^T u - 1/2 grad (|u|^2)_h, the gradient from the reference derivatives
+        R kx[3] = {R(0), R(0), R(0)};
+        if (emac) {
+            R kr[3] = {R(0), R(0), R(0)};
+#pragma unroll
+            for (int a = 0; a < nen; ++a)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) kr[j] += q2[a] * R(c_ref.dN[ET][g][a][j]);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) kx[j] = kr[0] * Ji[0][j] + kr[1] * Ji[1][j] + kr[2] * Ji[2][j];
+        }
         R f0[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             R c = R(0);
             if (mask & FEA_TERM_CONV) c = G[i][0] * ug[0] + G[i][1] * ug[1] + G[i][2] * ug[2] + trG * ug[i];
+            if (emac) c += G[0][i] * ug[0] + G[1][i] * ug[1] + G[2][i] * ug[2] - R(0.5) * kx[i];
             f0[i] = W * (c + ((mask & FEA_TERM_PRES) ? gp[i] : R(0)));
         }
         // S_ik = 2 W sum_j eps_ij Ji_kj; viscous part nu S, subgrid part q S
@@ -354,7 +417,7 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
         for (int g = 0; g < ng; ++g) {
             const bool use = (inside_mask >> g) & 1u;
             fallbacks += !use;
-            const R nt = use ? R(ntile[g * 32 + lane]) : R(qtile[g * 32 + lane]) * d2;
+            const R nt = use ? R(ntile[g * 32 + lane]) : R(qtile[g * 32 + lane]) * (aniso ? R(1) : d2);
             if (nut_out) nut_out[g] = float(nt);
             if (mask & FEA_TERM_SGS) {
                 R Sg[3][3];
@@ -374,12 +437,12 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
         __syncwarp();   // the scratch is rewritten for the warp's next elements
     } else {
         const R delta = cbrt_r(R(V));
-        const R d2 = delta * delta;
+        const R d2 = aniso ? R(1) : delta * delta;
 #pragma unroll
         for (int a = 0; a < nen; ++a)
 #pragma unroll
             for (int i = 0; i < 3; ++i) r[a][i] += d2 * rs[a][i];
-        if (nut_out)
+        if (nut_out && !aniso)
             for (int g = 0; g < ng; ++g) nut_out[g] = float(R(nut_out[g]) * d2);
     }
     return fallbacks;
@@ -466,13 +529,25 @@ __device__ int tet_residual(const Gathered<R, J64> &el, const FieldDev &f, const
             nut = R(ntile[lane]);
         } else {
             const R delta = cbrt_r(V);
-            nut = vreman(G, delta * delta, R(f.c_vreman));
+            if (f.delta_form == 1) {
+                R dmx[3];
+                element_extents<4, R>(el.X, dmx);
+                nut = vreman_aniso(G, dmx, R(f.c_vreman));
+            } else {
+                nut = vreman(G, delta * delta, R(f.c_vreman));
+            }
             fallbacks = 4;   // all four Gauss points
         }
         __syncwarp();
     } else if (args.closure == FEA_CLOSURE_VREMAN && ((mask & FEA_TERM_SGS) || nut_out)) {
-        const R delta = cbrt_r(V);
-        nut = vreman(G, delta * delta, R(f.c_vreman));
+        if (f.delta_form == 1) {
+            R dmx[3];
+            element_extents<4, R>(el.X, dmx);
+            nut = vreman_aniso(G, dmx, R(f.c_vreman));
+        } else {
+            const R delta = cbrt_r(V);
+            nut = vreman(G, delta * delta, R(f.c_vreman));
+        }
     }
     if (nut_out) {
 #pragma unroll
@@ -491,6 +566,18 @@ __device__ int tet_residual(const Gathered<R, J64> &el, const FieldDev &f, const
     R su[3] = {el.U[0][0] + el.U[1][0] + el.U[2][0] + el.U[3][0], el.U[0][1] + el.U[1][1] + el.U[2][1] + el.U[3][1],
                el.U[0][2] + el.U[1][2] + el.U[2][2] + el.U[3][2]};
     const R v20 = V * R(0.05), v4 = V * R(0.25);
+    // EMAC: + G^T u (same closed form as G u) and -1/2 grad (|u|^2)_h, constant
+    // on the element, whose integral against N_a is V/4
+    const bool emac = f.conv_form == 1 && (mask & FEA_TERM_CONV);
+    R kq[3] = {R(0), R(0), R(0)};
+    if (emac) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const R q = el.U[a][0] * el.U[a][0] + el.U[a][1] * el.U[a][1] + el.U[a][2] * el.U[a][2];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) kq[j] += q * dN[a][j];
+        }
+    }
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         R m[3];
@@ -500,6 +587,7 @@ __device__ int tet_residual(const Gathered<R, J64> &el, const FieldDev &f, const
         for (int i = 0; i < 3; ++i) {
             R v = R(0);
             if (mask & FEA_TERM_CONV) v += G[i][0] * m[0] + G[i][1] * m[1] + G[i][2] * m[2] + trG * m[i];
+            if (emac) v += G[0][i] * m[0] + G[1][i] * m[1] + G[2][i] * m[2] - R(0.5) * v4 * kq[i];
             if (mask & FEA_TERM_PRES) v += v4 * gp[i];
             v += sig[i][0] * dN[a][0] + sig[i][1] * dN[a][1] + sig[i][2] * dN[a][2];
             r[a][i] = -v;
@@ -1142,8 +1230,8 @@ cudaError_t launch_assemble_chunk(const BucketDev &b, const FieldDev &f, const A
                                   int compensated, cudaStream_t s) {
     if (b.count == 0) return cudaSuccess;
     if (!b.lconn || b.n_chunks <= 0) return cudaErrorInvalidValue;
-    if (b.etype == FEA_TET04 && !b.fp64j && !compensated && a.closure != FEA_CLOSURE_MLP &&
-        tet_pipe_smem_bytes(b) <= kChunkSmemLimit)
+    if (b.etype == FEA_TET04 && !b.fp64j && !compensated && a.closure != FEA_CLOSURE_MLP && f.conv_form == 0 &&
+        f.delta_form == 0 && tet_pipe_smem_bytes(b) <= kChunkSmemLimit)
         return launch_tet_pipe(b, f, a, threads, 0, s);
     if (threads > 256) threads = 256;
     switch (b.etype) {

@@ -34,7 +34,7 @@ EXPORTED = (
     "fea_mlp_load", "fea_mlp_get", "fea_mlp_forward", "fea_mlp_train_step", "fea_mlp_set_envelope",
     "fea_mlp_fallback_read", "fea_sfc_order", "fea_partition_sfc", "fea_interface_pack", "fea_interface_unpack",
     "fea_poisson_setup", "fea_poisson_solve", "fea_divergence", "fea_gradient", "fea_project",
-    "fea_balance_update",
+    "fea_balance_update", "fea_set_model",
 )
 MLP_NPARAM = 8833
 NOALLOC_MAX_NODES = 262144
@@ -184,6 +184,7 @@ def lib() -> ctypes.CDLL:
         L.fea_project.argtypes = [vp, i32, dbl, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl), vp]
         L.fea_partition_sfc.argtypes = [ctypes.POINTER(MeshDesc), i32, i32, vp, ctypes.c_void_p * 4]
         L.fea_balance_update.argtypes = [i32, i32, vp, vp, vp]
+        L.fea_set_model.argtypes = [vp, i32, i32, i32]
         L.fea_interface_pack.argtypes = [vp, vp, i64, vp, vp, i64, vp, i64, vp]
         L.fea_interface_unpack.argtypes = [vp, vp, i64, vp, vp, i64, vp, i64, vp]
         L.fea_mlp_fallback_read.argtypes = [vp, ctypes.POINTER(i64), ctypes.c_int]
@@ -390,6 +391,11 @@ class DeviceMesh:
         ncomp = 1 if v.dim() == 1 else v.shape[0]
         self.ctx.check(self._L().fea_periodic_fold(self.ctx.handle, self.id, _ptr(v), ncomp, _stream(stream)))
         return v
+
+    def set_model(self, conv="gu", delta="volume"):
+        """Convective form "gu" | "emac"; Vreman filter width "volume" | "axes"."""
+        self.ctx.check(self._L().fea_set_model(self.ctx.handle, self.id, {"gu": 0, "emac": 1}[conv],
+                                               {"volume": 0, "axes": 1}[delta]))
 
     # ---- pressure projection ----
     def poisson_setup(self, pinned=None, stream=None):
