@@ -80,6 +80,8 @@ def lib():
         _lib.orc_assemble_divergence.argtypes = [vp, dp, dp]
         _lib.orc_assemble_gradient.argtypes = [vp, dp, dp]
         _lib.orc_shape.argtypes = [ctypes.c_int, dp, dp, dp]
+        _lib.orc_reichardt.restype = ctypes.c_double
+        _lib.orc_reichardt.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
     return _lib
 
 
@@ -415,7 +417,9 @@ def periodic_fold(master: np.ndarray, v: np.ndarray) -> np.ndarray:
 
 
 def rk_stage(om: OracleMesh, master, dirichlet, mass_folded, un, uk, p, nu, c_vreman, closure, stage, dt,
-             mask=TERM_ALL, mlp=None) -> np.ndarray:
+             mask=TERM_ALL, mlp=None, wall=None) -> np.ndarray:
+    """One SSP-RK3 stage; wall (optional) = wall-model faces (see wall_rhs), whose
+    boundary term at u^(k) joins the element RHS (Algorithm 1)."""
     un = np.ascontiguousarray(un, dtype=np.float64)
     uk = np.ascontiguousarray(uk, dtype=np.float64)
     p = np.ascontiguousarray(p, dtype=np.float64)
@@ -426,20 +430,67 @@ def rk_stage(om: OracleMesh, master, dirichlet, mass_folded, un, uk, p, nu, c_vr
     if dirichlet is not None:
         dmask = np.ascontiguousarray(dirichlet, dtype=np.uint8)
     prm = _params(nu, c_vreman, closure, mask, mlp)
+    extra = None
+    if wall is not None:
+        extra = wall_rhs(om, uk, nu, **wall)
     st = lib().orc_rk_stage(ctypes.byref(om.struct), mp,
                             dmask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)) if dmask is not None else None,
                             _dp(mass_folded), _dp(un), _dp(uk), _dp(p), ctypes.byref(prm), ctypes.c_int(stage),
-                            ctypes.c_double(dt), _dp(out))
+                            ctypes.c_double(dt), _dp(extra) if extra is not None else None, _dp(out))
     _check(st, "rk_stage")
     return out
 
 
-def rk3_step(om: OracleMesh, master, dirichlet, un, p, nu, c_vreman, closure, dt, mask=TERM_ALL, mlp=None):
+def rk3_step(om: OracleMesh, master, dirichlet, un, p, nu, c_vreman, closure, dt, mask=TERM_ALL, mlp=None,
+             wall=None):
     """Three SSP-RK3 stages from u^n; returns u^(n+1)."""
     mass = lumped_mass(om)
     if master is not None:
         mass = periodic_fold(master, mass)
     uk = un
     for s in range(3):
-        uk = rk_stage(om, master, dirichlet, mass, un, uk, p, nu, c_vreman, closure, s, dt, mask, mlp)
+        uk = rk_stage(om, master, dirichlet, mass, un, uk, p, nu, c_vreman, closure, s, dt, mask, mlp, wall)
     return uk
+
+
+# ---- equilibrium wall model (the boundary assembly of Algorithm 1; the law of
+# the wall and the sampling are readings, documented in fea_oracle.c) ---------
+
+WALL_KAPPA, WALL_C = 0.41, 7.8
+
+
+def reichardt(yp: float, kappa: float = WALL_KAPPA, c: float = WALL_C):
+    """(f(y+), f'(y+)) of Reichardt's law of the wall."""
+    d = ctypes.c_double(0.0)
+    f = lib().orc_reichardt(ctypes.c_double(yp), ctypes.c_double(kappa), ctypes.c_double(c), ctypes.byref(d))
+    return f, d.value
+
+
+def wall_utau(U: float, y: float, nu: float, kappa: float = WALL_KAPPA, c: float = WALL_C):
+    """(u_tau, Newton steps) with U = u_tau f(y u_tau / nu)."""
+    v = ctypes.c_double(0.0)
+    it = ctypes.c_int(0)
+    st = lib().orc_wall_utau(ctypes.c_double(U), ctypes.c_double(y), ctypes.c_double(nu), ctypes.c_double(kappa),
+                             ctypes.c_double(c), ctypes.byref(v), ctypes.byref(it))
+    _check(st, "wall_utau")
+    return v.value, it.value
+
+
+def wall_rhs(om: OracleMesh, u: np.ndarray, nu: float, tri=None, tri_exch=None, quad=None, quad_exch=None,
+             kappa: float = WALL_KAPPA, c: float = WALL_C) -> np.ndarray:
+    """Wall-model boundary term (N, 3) of triangular and quadrilateral wall
+    faces: tri / tri_exch (F, 3) and quad / quad_exch (F, 4) node ids, face
+    nodes ordered so that x_xi x x_eta points out of the fluid."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    rhs = np.zeros((om.n_nodes, 3))
+    for nv, f, x in ((3, tri, tri_exch), (4, quad, quad_exch)):
+        if f is None or len(f) == 0:
+            continue
+        f = np.ascontiguousarray(f, dtype=np.int32)
+        x = np.ascontiguousarray(x, dtype=np.int32)
+        assert f.shape == x.shape and f.shape[1] == nv
+        st = lib().orc_wall_rhs(ctypes.c_int64(om.n_nodes), _dp(om.xyz), _dp(u), ctypes.c_int(nv),
+                                ctypes.c_int64(f.shape[0]), _ip(f), _ip(x), ctypes.c_double(nu),
+                                ctypes.c_double(kappa), ctypes.c_double(c), _dp(rhs))
+        _check(st, "wall_rhs")
+    return rhs

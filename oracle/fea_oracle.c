@@ -20,6 +20,8 @@
  *     listing, M_a = sum_e sum_g W_g N_a.
  *   Time integration: a three-stage Runge-Kutta momentum update (Algorithm 1);
  *     the stage coefficients are the SSP-RK3 (Shu-Osher) ones, pressure frozen.
+ *   Boundary assembly (Algorithm 1): an equilibrium wall model, a law of the
+ *     wall applied as a traction on wall faces (readings at orc_reichardt).
  *
  * Readings where the paper is silent (each one is listed in the design notes):
  *   - quadrature per element type (the paper only says a category is a type
@@ -760,14 +762,157 @@ void orc_periodic_fold(int64_t n, const int32_t *master, double *v, int ncomp) {
             for (int c = 0; c < ncomp; ++c) v[i * ncomp + c] = v[(int64_t)master[i] * ncomp + c];
 }
 
+/* ---------------------------------------------------------------------- */
+/* Equilibrium wall model: the boundary assembly of Algorithm 1 ("assembly of
+ * the wall model", a law of the wall; the paper defers the formulation to a
+ * reference that is absent here, so every item below is a reading).
+ *   Law of the wall (Reichardt): u+ = f(y+) with
+ *     f(y+) = ln(1 + kappa y+) / kappa + C (1 - exp(-y+/11) - (y+/11) exp(-y+/3)),
+ *     kappa = 0.41, C = 7.8 by default.
+ *   At every Gauss point of a wall face the velocity is sampled at an
+ *   exchange location: the face's shape functions applied to the velocities
+ *   and positions of each face node's exchange node (an interior node, e.g.
+ *   the opposite node of the wall prism).  y = normal distance of that point
+ *   from the wall, U = |tangential part of the sampled velocity|.
+ *   u_tau > 0 solves U = u_tau f(y u_tau / nu) (Newton from the viscous-
+ *   sublayer value sqrt(nu U / y)); the wall shear stress is u_tau^2 along
+ *   the tangential velocity, against it on the fluid:
+ *     R_a += - sum_g w_g |x_xi x x_eta| N_a(g) u_tau^2 t,  t = u_t / U.
+ *   Faces: triangles (3-point degree-2 rule) and bilinear quads (2x2 Gauss);
+ *   the node order makes (x_xi x x_eta) point out of the fluid.           */
+
+/* Reichardt's f(y+) and, if df != NULL, its derivative. */
+double orc_reichardt(double yp, double kappa, double c, double *df) {
+    const double e11 = exp(-yp / 11.0), e3 = exp(-yp / 3.0);
+    if (df) *df = 1.0 / (1.0 + kappa * yp) + c * (e11 / 11.0 - e3 / 11.0 + yp * e3 / 33.0);
+    return log1p(kappa * yp) / kappa + c * (1.0 - e11 - (yp / 11.0) * e3);
+}
+
+/* u_tau from U = u_tau f(y u_tau / nu): Newton on g(v) = v f(y v / nu) - U,
+ * g'(v) = f + y+ f'; a step that would leave v <= 0 halves v instead.
+ * Stops when |dv| <= 1e-14 v (returns 0) or after 100 steps (returns -5).
+ * U = 0 gives u_tau = 0.                                                   */
+int orc_wall_utau(double U, double y, double nu, double kappa, double c, double *utau, int *iters) {
+    if (!(y > 0.0) || !(nu > 0.0) || !(U >= 0.0)) return -3;
+    if (iters) *iters = 0;
+    if (U == 0.0) {
+        *utau = 0.0;
+        return 0;
+    }
+    double v = sqrt(nu * U / y);
+    for (int it = 1; it <= 100; ++it) {
+        double df;
+        const double yp = y * v / nu;
+        const double f = orc_reichardt(yp, kappa, c, &df);
+        const double g = v * f - U, dg = f + yp * df;
+        double vn = v - g / dg;
+        if (!(vn > 0.0)) vn = 0.5 * v;
+        const double dv = fabs(vn - v);
+        v = vn;
+        if (iters) *iters = it;
+        if (dv <= 1e-14 * v) {
+            *utau = v;
+            return 0;
+        }
+    }
+    *utau = v;
+    return -5;
+}
+
+/* Face rules: triangle points (1/6,1/6), (2/3,1/6), (1/6,2/3), weights 1/6;
+ * quad 2x2 Gauss on [-1,1]^2, weights 1, node order (-1,-1) (1,-1) (1,1) (-1,1). */
+static int face_rule(int nv, double pts[4][2], double w[4]) {
+    if (nv == 3) {
+        const double a = 1.0 / 6.0, b = 2.0 / 3.0;
+        pts[0][0] = a; pts[0][1] = a;
+        pts[1][0] = b; pts[1][1] = a;
+        pts[2][0] = a; pts[2][1] = b;
+        for (int g = 0; g < 3; ++g) w[g] = 1.0 / 6.0;
+        return 3;
+    }
+    const double q = 1.0 / sqrt(3.0);
+    const double sx[4] = {-q, q, q, -q}, sy[4] = {-q, -q, q, q};
+    for (int g = 0; g < 4; ++g) {
+        pts[g][0] = sx[g];
+        pts[g][1] = sy[g];
+        w[g] = 1.0;
+    }
+    return 4;
+}
+
+static void face_shape(int nv, const double *xi, double *N, double (*dN)[2]) {
+    if (nv == 3) {
+        N[0] = 1.0 - xi[0] - xi[1]; N[1] = xi[0]; N[2] = xi[1];
+        dN[0][0] = -1.0; dN[0][1] = -1.0;
+        dN[1][0] = 1.0;  dN[1][1] = 0.0;
+        dN[2][0] = 0.0;  dN[2][1] = 1.0;
+        return;
+    }
+    const double sx[4] = {-1, 1, 1, -1}, sy[4] = {-1, -1, 1, 1};
+    for (int a = 0; a < 4; ++a) {
+        N[a] = 0.25 * (1 + sx[a] * xi[0]) * (1 + sy[a] * xi[1]);
+        dN[a][0] = 0.25 * sx[a] * (1 + sy[a] * xi[1]);
+        dN[a][1] = 0.25 * sy[a] * (1 + sx[a] * xi[0]);
+    }
+}
+
+/* Adds the wall-model boundary term of n_faces faces with nv (3 or 4) nodes
+ * to rhs [n][3].  face, exch: [n_faces][nv] node ids.  Returns -3 for a
+ * Gauss point whose exchange location is not on the fluid side (y <= 0) or
+ * a degenerate face, -1 for a bad node id, -5 if Newton did not converge. */
+int orc_wall_rhs(int64_t n, const double *xyz, const double *u, int nv, int64_t n_faces, const int32_t *face,
+                 const int32_t *exch, double nu, double kappa, double c, double *rhs) {
+    if (nv != 3 && nv != 4) return -2;
+    double pts[4][2], w[4];
+    const int ng = face_rule(nv, pts, w);
+    for (int64_t f = 0; f < n_faces; ++f) {
+        const int32_t *fa = face + f * nv, *ex = exch + f * nv;
+        for (int a = 0; a < nv; ++a)
+            if (fa[a] < 0 || fa[a] >= n || ex[a] < 0 || ex[a] >= n) return -1;
+        for (int g = 0; g < ng; ++g) {
+            double N[4], dN[4][2];
+            face_shape(nv, pts[g], N, dN);
+            double xg[3] = {0, 0, 0}, xs[3] = {0, 0, 0}, us[3] = {0, 0, 0}, t1[3] = {0, 0, 0}, t2[3] = {0, 0, 0};
+            for (int a = 0; a < nv; ++a)
+                for (int i = 0; i < 3; ++i) {
+                    xg[i] += N[a] * xyz[3 * (int64_t)fa[a] + i];
+                    xs[i] += N[a] * xyz[3 * (int64_t)ex[a] + i];
+                    us[i] += N[a] * u[3 * (int64_t)ex[a] + i];
+                    t1[i] += dN[a][0] * xyz[3 * (int64_t)fa[a] + i];
+                    t2[i] += dN[a][1] * xyz[3 * (int64_t)fa[a] + i];
+                }
+            const double nr[3] = {t1[1] * t2[2] - t1[2] * t2[1], t1[2] * t2[0] - t1[0] * t2[2],
+                                  t1[0] * t2[1] - t1[1] * t2[0]};
+            const double area = sqrt(nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2]);
+            if (!(area > 0.0)) return -3;
+            const double nh[3] = {nr[0] / area, nr[1] / area, nr[2] / area};   /* out of the fluid */
+            const double y = -((xs[0] - xg[0]) * nh[0] + (xs[1] - xg[1]) * nh[1] + (xs[2] - xg[2]) * nh[2]);
+            if (!(y > 0.0)) return -3;
+            const double un = us[0] * nh[0] + us[1] * nh[1] + us[2] * nh[2];
+            const double ut[3] = {us[0] - un * nh[0], us[1] - un * nh[1], us[2] - un * nh[2]};
+            const double U = sqrt(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
+            if (U == 0.0) continue;
+            double ut_;
+            const int st = orc_wall_utau(U, y, nu, kappa, c, &ut_, NULL);
+            if (st) return st;
+            const double s = -w[g] * area * ut_ * ut_ / U;
+            for (int a = 0; a < nv; ++a)
+                for (int i = 0; i < 3; ++i) rhs[3 * (int64_t)fa[a] + i] += s * N[a] * ut[i];
+        }
+    }
+    return 0;
+}
+
 /* One stage of the three-stage SSP Runge-Kutta momentum update (Shu-Osher):
  *   u^(k+1) = a_k u^n + b_k (u^(k) + dt M^-1 R(u^(k), p^n)),
  *   (a, b) = (0, 1), (3/4, 1/4), (1/3, 2/3);
  * R is folded over periodic pairs, M is the folded lumped mass, and nodes
- * with dirichlet != 0 keep u^n.  uk_out may alias uk.                      */
+ * with dirichlet != 0 keep u^n.  rhs_extra (optional, [n][3]) is added to
+ * the element RHS before the fold (the boundary assembly of Algorithm 1,
+ * evaluated by the caller at u^(k)).  uk_out may alias uk.                  */
 int orc_rk_stage(const orc_mesh *m, const int32_t *master, const uint8_t *dirichlet, const double *mass_folded,
                  const double *un, const double *uk, const double *p, const orc_params *prm, int stage, double dt,
-                 double *uk_out) {
+                 const double *rhs_extra, double *uk_out) {
     static const double A[3] = {0.0, 0.75, 1.0 / 3.0};
     static const double Bc[3] = {1.0, 0.25, 2.0 / 3.0};
     if (stage < 0 || stage > 2) return -2;
@@ -779,6 +924,8 @@ int orc_rk_stage(const orc_mesh *m, const int32_t *master, const uint8_t *dirich
         free(R);
         return st;
     }
+    if (rhs_extra)
+        for (int64_t k = 0; k < 3 * n; ++k) R[k] += rhs_extra[k];
     if (master) orc_periodic_fold(n, master, R, 3);
     for (int64_t i = 0; i < n; ++i)
         for (int c = 0; c < 3; ++c) {

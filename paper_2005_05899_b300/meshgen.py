@@ -49,6 +49,9 @@ class Mesh:
     fp64_flag: Dict[int, np.ndarray] = dataclasses.field(default_factory=dict)
     name: str = ""
     meta: dict = dataclasses.field(default_factory=dict)
+    # wall-model faces: {"tri": (F,3), "tri_exch": (F,3)[, "quad", "quad_exch"]}
+    # node ids, each face ordered so that its normal points out of the fluid
+    wall_faces: Optional[Dict[str, np.ndarray]] = None
 
     @property
     def n_nodes(self) -> int:
@@ -160,6 +163,27 @@ def orient_positive(etype: int, conn: np.ndarray, xyz: np.ndarray) -> np.ndarray
     return conn
 
 
+def prism_wall_faces(mesh: Mesh) -> Dict[str, np.ndarray]:
+    """Wall-model faces of a prism boundary layer: the triangle of every PEN06
+    whose three nodes are wall (Dirichlet) nodes, with the opposite triangle's
+    nodes as exchange nodes; faces are reordered so that their normal
+    (x1 - x0) x (x2 - x0) points away from the exchange nodes (out of the
+    fluid)."""
+    pen = mesh.conn.get(PEN06)
+    if pen is None or mesh.dirichlet is None:
+        return {"tri": np.zeros((0, 3), np.int32), "tri_exch": np.zeros((0, 3), np.int32)}
+    w = mesh.dirichlet.astype(bool)
+    bot, top = w[pen[:, :3]].all(axis=1), w[pen[:, 3:]].all(axis=1)
+    face = np.concatenate([pen[bot, :3], pen[top, 3:]]).astype(np.int32)
+    exch = np.concatenate([pen[bot, 3:], pen[top, :3]]).astype(np.int32)
+    X = mesh.xyz
+    nrm = np.cross(X[face[:, 1]] - X[face[:, 0]], X[face[:, 2]] - X[face[:, 0]])
+    into_fluid = np.einsum("ij,ij->i", nrm, X[exch].mean(axis=1) - X[face].mean(axis=1)) > 0
+    face[into_fluid] = face[into_fluid][:, [0, 2, 1]]
+    exch[into_fluid] = exch[into_fluid][:, [0, 2, 1]]
+    return {"tri": face, "tri_exch": exch}
+
+
 def morton_codes(xyz: np.ndarray, bits: int = 21) -> np.ndarray:
     """63-bit Morton (Z-order) keys of points quantised in their bounding box."""
     lo = xyz.min(axis=0)
@@ -188,9 +212,10 @@ def renumber_nodes(mesh: Mesh, perm: np.ndarray) -> Mesh:
     if mesh.periodic_master is not None:
         master = inv[mesh.periodic_master[perm]].astype(np.int32)
     dirichlet = None if mesh.dirichlet is None else mesh.dirichlet[perm].copy()
+    wall = None if mesh.wall_faces is None else {k: inv[v].astype(np.int32) for k, v in mesh.wall_faces.items()}
     out = dataclasses.replace(mesh, xyz=mesh.xyz[perm].copy(), conn=conn,
                               periodic_master=master, dirichlet=dirichlet,
-                              meta=dict(mesh.meta))
+                              meta=dict(mesh.meta), wall_faces=wall)
     out.meta["node_perm"] = perm
     return out
 
@@ -386,6 +411,7 @@ def channel_mesh(nx: int = 128, ny: int = 64, nz: int = 64, seed: int = 2,
                 meta={"nx": nx, "ny": ny, "nz": nz, "seed": seed, "n_layers": n_layers,
                       "ratio": ratio, "split_frac": split_frac, "jitter": jitter,
                       "volume": lx * 2.0 * lz, "first_cell": float(gy[1] - gy[0])})
+    mesh.wall_faces = prism_wall_faces(mesh)
     return sfc_sort_nodes(mesh) if sfc else mesh
 
 
@@ -595,6 +621,7 @@ def airplane_mesh(n_nodes_axis: int = 170, seed: int = 4, n_bl: int = 5, bl_rati
                       "rotation": rot.tolist(), "n_bl": n_bl, "bl_ratio": bl_ratio,
                       "n_wall_faces": int(wall.shape[0]), "h": h, "bl_total": bl_total,
                       "wall_nodes": wall_nodes, "inner_wall_faces": inner_faces})
+    mesh.wall_faces = prism_wall_faces(mesh)
     if sfc:
         mesh = sfc_sort_nodes(mesh)
         inv = np.empty_like(mesh.meta["node_perm"])
