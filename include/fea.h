@@ -205,8 +205,9 @@ fea_status fea_periodic_fold(fea_ctx *ctx, int32_t mesh, double *v, int32_t ncom
 /* One SSP-RK3 momentum-update stage (Algorithm 1, stage index 0..2) on the
  * library-owned state:  u^(k+1) = a_k u^n + b_k (u^(k) + dt M^-1 R(u^(k))),
  * (a, b) = (0, 1), (3/4, 1/4), (1/3, 2/3); R folded, M the folded lumped
- * mass, Dirichlet nodes hold u^n, pressure frozen at the uploaded p.  Stage 2
- * also makes the result the new u^n. */
+ * mass, Dirichlet nodes hold u^n, pressure frozen at the uploaded p.  R
+ * includes the wall-model term when the mesh has wall faces
+ * (fea_wall_setup).  Stage 2 also makes the result the new u^n. */
 fea_status fea_rk_stage(fea_ctx *ctx, int32_t mesh, int32_t stage, double dt, fea_prec prec, fea_closure closure,
                         void *stream);
 
@@ -279,6 +280,49 @@ fea_status fea_mlp_train_step(fea_ctx *ctx, const float *x, const float *y, int6
  * pipeline serves the defaults; other forms run in the generic kernels.
  * Drops a captured RK graph of the mesh.  Errors: FEA_EINVAL. */
 fea_status fea_set_model(fea_ctx *ctx, int32_t mesh, int32_t conv_form, int32_t delta_form);
+
+/* ---- boundary assembly: equilibrium wall model (Algorithm 1) -------------
+ * Algorithm 1's "boundary assembly" applies a law of the wall on the wall
+ * faces (section 2.1 and the test-case section: an equilibrium wall model on
+ * the aircraft walls; the formulation itself is in a reference the paper
+ * cites, so the one here is a reading):
+ *   u+ = f(y+) = ln(1 + kappa y+)/kappa + C (1 - e^(-y+/11) - (y+/11) e^(-y+/3))
+ * (Reichardt).  At each Gauss point of a wall face (triangles: 3-point
+ * rule; bilinear quadrilaterals: 2x2 Gauss) the velocity and position are
+ * interpolated from the face nodes' exchange nodes; y = normal distance of
+ * that point from the face, U = |tangential velocity|; u_tau solves
+ * U = u_tau f(y u_tau / nu) (Newton); the RHS receives the wall shear stress
+ * as a traction against the tangential velocity:
+ *   R_a += - sum_g w_g |x_xi x x_eta| N_a u_tau^2 u_t / U.
+ * Geometry, traction and sums in FP64; u_tau to FP64 accuracy under FEA_FP64
+ * (and in fea_wall_assemble), its FP32 Newton root under FEA_MIXED.  The
+ * term joins R in every fea_rk_stage / fea_rk_step_graph / noalloc stage of
+ * the mesh (added before the periodic fold). */
+typedef struct {
+    int64_t n_tri;              /* triangular wall faces */
+    const int32_t *tri;         /* host [n_tri][3] node ids, ordered so that
+                                   (x1 - x0) x (x2 - x0) points out of the fluid */
+    const int32_t *tri_exch;    /* host [n_tri][3] exchange node of each face node */
+    int64_t n_quad;             /* bilinear quadrilateral wall faces */
+    const int32_t *quad;        /* host [n_quad][4], counter-clockwise seen from
+                                   outside the fluid: (x1 - x0) x (x3 - x0) points out */
+    const int32_t *quad_exch;   /* host [n_quad][4] */
+    double kappa;               /* von Karman constant (0.41) */
+    double c_plus;              /* C of the law above (7.8) */
+} fea_wall_desc;
+
+/* Sets (or, with n_tri = n_quad = 0, clears) the wall faces of a mesh.  The
+ * arrays are copied.  Checks every index and, on the host in FP64, that every
+ * face Gauss point has a positive face area and its exchange point strictly
+ * on the fluid side (FEA_EMESH otherwise).  kappa > 0 and c_plus >= 0, else
+ * FEA_EINVAL.  Drops a captured RK graph of the mesh. */
+fea_status fea_wall_setup(fea_ctx *ctx, int32_t mesh, const fea_wall_desc *desc);
+
+/* Adds the wall-model term at the uploaded field (current u^(k)) to rhs
+ * [3][n_nodes] (device, not folded).  A Newton iteration that does not
+ * converge in 100 steps is reported by fea_sync_status (FEA_ENUMERIC).
+ * FEA_ESTATE without a field; a mesh without wall faces adds nothing. */
+fea_status fea_wall_assemble(fea_ctx *ctx, int32_t mesh, double *rhs, void *stream);
 
 /* ---- pressure projection (Algorithm 1) -----------------------------------
  * Algorithm 1 assembles the Laplacian matrix once, and each time step ends

@@ -785,7 +785,9 @@ void orc_periodic_fold(int64_t n, const int32_t *master, double *v, int ncomp) {
 double orc_reichardt(double yp, double kappa, double c, double *df) {
     const double e11 = exp(-yp / 11.0), e3 = exp(-yp / 3.0);
     if (df) *df = 1.0 / (1.0 + kappa * yp) + c * (e11 / 11.0 - e3 / 11.0 + yp * e3 / 33.0);
-    return log1p(kappa * yp) / kappa + c * (1.0 - e11 - (yp / 11.0) * e3);
+    /* 1 - e^(-y+/11) as -expm1: deep in the sublayer the bracket is O(y+^2)
+     * and 1 - exp() would leave it an absolute error of one ulp of 1 */
+    return log1p(kappa * yp) / kappa + c * (-expm1(-yp / 11.0) - (yp / 11.0) * e3);
 }
 
 /* u_tau from U = u_tau f(y u_tau / nu): Newton on g(v) = v f(y v / nu) - U,

@@ -213,6 +213,66 @@ def projection(n_axis: int = 170, dt: float = 2e-4, rtol: float = 1e-6, steps: i
                       "setup_s": setup_s, "dt": dt, "rtol": rtol, "steps": res}), flush=True)
 
 
+def wall(reps: int, n_axis: int = 170, dims=(269, 134, 135)):
+    """Boundary assembly (wall model, FP64) timed with CUDA events: on the
+    airplane-like mesh's wall (the innermost prism-layer triangles) against
+    its RK stage with and without the term, and on the walls of a large
+    channel (prism-layer triangles on both walls)."""
+    import torch
+    from . import fea
+    from . import meshgen as mg
+    ctx = fea.Context(0)
+    out = {}
+    m = mg.airplane_mesh(n_axis, seed=4)
+    f = mg.inflow_field(m, seed=5)
+    dm = ctx.upload_mesh(m)
+    dm.upload_field(f.u, f.p, f.nu, f.c_vreman)
+    rhs = torch.zeros((3, m.n_nodes), dtype=torch.float64, device="cuda")
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        e0, e1 = _events()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    stage_plain = timed(lambda: dm.rk_stage(0, 1e-6))
+    dm.wall_setup(**m.wall_faces)
+    wall_ms = timed(lambda: dm.wall_assemble(rhs))
+    stage_wall = timed(lambda: dm.rk_stage(0, 1e-6))
+    ctx.sync_status()
+    nf = int(m.wall_faces["tri"].shape[0])
+    stage_wall64 = timed(lambda: dm.rk_stage(0, 1e-6, prec="fp64"))
+    dm.wall_setup()
+    stage_plain64 = timed(lambda: dm.rk_stage(0, 1e-6, prec="fp64"))
+    ctx.sync_status()
+    out["airplane"] = {"faces": nf, "elements": m.n_elem_total, "wall_fp64_ms": wall_ms,
+                       "faces_per_s_fp64": nf / (wall_ms * 1e-3),
+                       "mixed": {"rk_stage_ms": stage_plain, "rk_stage_with_wall_ms": stage_wall,
+                                 "boundary_share": (stage_wall - stage_plain) / stage_wall},
+                       "fp64": {"rk_stage_ms": stage_plain64, "rk_stage_with_wall_ms": stage_wall64,
+                                "boundary_share": (stage_wall64 - stage_plain64) / stage_wall64}}
+    del dm
+    c = mg.channel_mesh(*dims, seed=2)
+    cf = mg.channel_field(c, seed=3)
+    dc = ctx.upload_mesh(c)
+    dc.upload_field(cf.u, cf.p, cf.nu, cf.c_vreman)
+    dc.wall_setup(**c.wall_faces)
+    rc = torch.zeros((3, c.n_nodes), dtype=torch.float64, device="cuda")
+    ms = timed(lambda: dc.wall_assemble(rc))
+    ctx.sync_status()
+    nf = int(c.wall_faces["tri"].shape[0])
+    out["channel"] = {"faces": nf, "wall_fp64_ms": ms, "faces_per_s_fp64": nf / (ms * 1e-3)}
+    print(json.dumps({"workload": "wall-model boundary assembly (Reichardt law, Newton for u_tau; "
+                                  "FP32 root in the mixed stage, FP64 otherwise)",
+                      **out}), flush=True)
+
+
 def part_times(ctx, mesh, field, parts, reps: int):
     """Assembly time of every part (mixed precision, Vreman, autotuned plan
     of the first call), parts uploaded as meshes of their own, timed one
@@ -261,10 +321,11 @@ def main(argv=None) -> int:
     ap.add_argument("--closure", action="store_true")
     ap.add_argument("--projection", action="store_true")
     ap.add_argument("--balance", action="store_true")
+    ap.add_argument("--wall", action="store_true")
     ap.add_argument("--n-f", type=int, default=256, help="fine Taylor-Green grid of the closure's training runs")
     ap.add_argument("--reps", type=int, default=20)
     a = ap.parse_args(argv)
-    if not (a.channel or a.batch or a.closure or a.projection or a.balance):
+    if not (a.channel or a.batch or a.closure or a.projection or a.balance or a.wall):
         a.channel = a.batch = True
     if a.channel:
         channel(a.reps)
@@ -276,6 +337,8 @@ def main(argv=None) -> int:
         projection()
     if a.balance:
         balance(a.reps)
+    if a.wall:
+        wall(a.reps)
     return 0
 
 

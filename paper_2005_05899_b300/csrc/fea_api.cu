@@ -259,6 +259,21 @@ struct Mesh {
     int conv_form = 0, delta_form = 0;  // model variants (fea_set_model)
     PoissonSystem *poisson = nullptr;   // pressure equation (fea_poisson_setup)
     DevBuf<double> proj_b, proj_dp, proj_g;
+    // wall-model faces (fea_wall_setup): [0] triangles, [1] quads, SoA [nv][n]
+    DevBuf<int32_t> wall_face[2], wall_exch[2];
+    int64_t wall_n[2] = {0, 0};
+    double wall_kappa = 0.41, wall_c = 7.8;
+    WallDev wall_dev(int k) const {
+        WallDev w;
+        w.n_faces = wall_n[k];
+        w.nv = k ? 4 : 3;
+        w.face = wall_face[k].p;
+        w.exch = wall_exch[k].p;
+        w.kappa = wall_kappa;
+        w.c_plus = wall_c;
+        return w;
+    }
+    int wall_launches() const { return (wall_n[0] > 0) + (wall_n[1] > 0); }
     ~Mesh() {
         if (graph.exec) cudaGraphExecDestroy(graph.exec);
         if (poisson) poisson_free(poisson);
@@ -516,12 +531,27 @@ fea_status check_args(fea_ctx *ctx, fea_prec prec, fea_closure closure, uint32_t
     return FEA_OK;
 }
 
+// boundary assembly (Algorithm 1): the wall-model term at velocity u64 added
+// to rhs; no-op without wall faces
+fea_status add_wall_term(fea_ctx *ctx, const Mesh &m, const double *u64, double nu, double *rhs, fea_prec prec,
+                         cudaStream_t s) {
+    if (!m.wall_launches()) return FEA_OK;
+    if (!(nu > 0.0)) return fail(ctx, FEA_EINVAL, "the wall model needs nu > 0");
+    for (int k = 0; k < 2; ++k) {
+        if (!m.wall_n[k]) continue;
+        CK(launch_wall(m.wall_dev(k), m.xyz64.p, u64, m.n, nu, rhs, ctx->d_err, prec == FEA_FP64, s));
+        ctx->launches++;
+    }
+    return FEA_OK;
+}
+
 fea_status rk_stage_impl(fea_ctx *ctx, Mesh &m, int stage, double dt, fea_prec prec, fea_closure closure,
                          cudaStream_t s) {
     static const double A[3] = {0.0, 0.75, 1.0 / 3.0};
     static const double B[3] = {1.0, 0.25, 2.0 / 3.0};
     fea_status st = assemble_into(ctx, m, prec, closure, FEA_TERM_ALL, FEA_SCATTER_AUTO, m.rhs.p, nullptr, s);
     if (st) return st;
+    if ((st = add_wall_term(ctx, m, m.uk.p, m.nu, m.rhs.p, prec, s))) return st;
     if (m.slaves.n) {
         CK(launch_fold(m.slaves.p, m.masters.p, (int64_t)m.slaves.n, m.rhs.p, 3, m.n, s));
         ctx->launches += 2;
@@ -609,6 +639,7 @@ fea_status stage_with_scratch(fea_ctx *ctx, int32_t mesh, int32_t stage, double 
         CK(cudaEventRecord(ctx->ev_join, ctx->side));
         CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
     }
+    if ((st = add_wall_term(ctx, *m, uk, nu, rhs, prec, s))) return st;
     if (m->slaves.n) {
         CK(launch_fold(m->slaves.p, m->masters.p, (int64_t)m->slaves.n, rhs, 3, n, s));
         ctx->launches += 2;
@@ -1057,8 +1088,8 @@ fea_status fea_rk_step_graph(fea_ctx *ctx, int32_t mesh, double dt, fea_prec pre
         g.closure = closure;
     }
     CK(cudaGraphLaunch(g.exec, (cudaStream_t)stream));
-    // kernels per step: 3 x (buckets + fold 2 + update 1)
-    int64_t per_stage = 1 + (m->slaves.n ? 2 : 0);
+    // kernels per step: 3 x (buckets + wall faces + fold 2 + update 1)
+    int64_t per_stage = 1 + (m->slaves.n ? 2 : 0) + m->wall_launches();
     for (auto &b : m->buckets) per_stage += b->count ? 1 : 0;
     ctx->launches += 3 * per_stage;
     return FEA_OK;
@@ -1260,6 +1291,102 @@ fea_status fea_set_model(fea_ctx *ctx, int32_t mesh, int32_t conv_form, int32_t 
         m->graph.exec = nullptr;
     }
     return FEA_OK;
+}
+
+// ---- boundary assembly: wall model ---------------------------------------------
+
+fea_status fea_wall_setup(fea_ctx *ctx, int32_t mesh, const fea_wall_desc *d) {
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    if (!d) return fail(ctx, FEA_EINVAL, "null wall descriptor");
+    if (d->n_tri < 0 || d->n_quad < 0 || (d->n_tri && (!d->tri || !d->tri_exch)) ||
+        (d->n_quad && (!d->quad || !d->quad_exch)))
+        return fail(ctx, FEA_EINVAL, "bad wall face arrays");
+    if (!(d->kappa > 0.0) || !(d->c_plus >= 0.0)) return fail(ctx, FEA_EINVAL, "need kappa > 0 and c_plus >= 0");
+    CK(cudaSetDevice(ctx->device));
+    const int64_t n = m->n;
+    const double *X = m->xyz_h.data();   // [3][n]
+    const int64_t cnt[2] = {d->n_tri, d->n_quad};
+    const int32_t *fs[2] = {d->tri, d->quad}, *xs[2] = {d->tri_exch, d->quad_exch};
+    std::vector<int32_t> soa_f[2], soa_x[2];
+    for (int k = 0; k < 2; ++k) {
+        const int nv = k ? 4 : 3;
+        soa_f[k].resize((size_t)nv * cnt[k]);
+        soa_x[k].resize((size_t)nv * cnt[k]);
+        // face Gauss points of the same rules as the kernel (geometry check only)
+        const double a6 = 1.0 / 6.0, b6 = 2.0 / 3.0, q = 1.0 / sqrt(3.0);
+        const double gp[4][2] = {{k ? -q : a6, k ? -q : a6}, {k ? q : b6, k ? -q : a6}, {k ? q : a6, k ? q : b6},
+                                 {-q, q}};
+        for (int64_t f = 0; f < cnt[k]; ++f) {
+            int32_t fa[4], ex[4];
+            for (int a = 0; a < nv; ++a) {
+                fa[a] = fs[k][f * nv + a];
+                ex[a] = xs[k][f * nv + a];
+                if (fa[a] < 0 || fa[a] >= n || ex[a] < 0 || ex[a] >= n)
+                    return fail(ctx, FEA_EMESH, "wall face %lld: node id out of range", (long long)f);
+                soa_f[k][(size_t)a * cnt[k] + f] = fa[a];
+                soa_x[k][(size_t)a * cnt[k] + f] = ex[a];
+            }
+            for (int g = 0; g < nv; ++g) {
+                double N[4], dN[4][2];
+                const double xi = gp[g][0], eta = gp[g][1];
+                if (nv == 3) {
+                    N[0] = 1 - xi - eta, N[1] = xi, N[2] = eta;
+                    dN[0][0] = -1, dN[0][1] = -1, dN[1][0] = 1, dN[1][1] = 0, dN[2][0] = 0, dN[2][1] = 1;
+                } else {
+                    const double sx[4] = {-1, 1, 1, -1}, sy[4] = {-1, -1, 1, 1};
+                    for (int a = 0; a < 4; ++a) {
+                        N[a] = 0.25 * (1 + sx[a] * xi) * (1 + sy[a] * eta);
+                        dN[a][0] = 0.25 * sx[a] * (1 + sy[a] * eta);
+                        dN[a][1] = 0.25 * sy[a] * (1 + sx[a] * xi);
+                    }
+                }
+                double t1[3] = {0, 0, 0}, t2[3] = {0, 0, 0}, dx[3] = {0, 0, 0};
+                for (int a = 0; a < nv; ++a)
+                    for (int i = 0; i < 3; ++i) {
+                        t1[i] += dN[a][0] * X[i * n + fa[a]];
+                        t2[i] += dN[a][1] * X[i * n + fa[a]];
+                        dx[i] += N[a] * (X[i * n + ex[a]] - X[i * n + fa[a]]);
+                    }
+                const double nr[3] = {t1[1] * t2[2] - t1[2] * t2[1], t1[2] * t2[0] - t1[0] * t2[2],
+                                      t1[0] * t2[1] - t1[1] * t2[0]};
+                const double y = -(dx[0] * nr[0] + dx[1] * nr[1] + dx[2] * nr[2]);   // times |nr|
+                const double area2 = nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2];
+                if (!(area2 > 0.0) || !(y > 0.0))
+                    return fail(ctx, FEA_EMESH,
+                                "wall face %lld: degenerate, or its exchange point is not on the fluid side "
+                                "(face normal must point out of the fluid)",
+                                (long long)f);
+            }
+        }
+    }
+    for (int k = 0; k < 2; ++k) {
+        m->wall_n[k] = 0;
+        CK(m->wall_face[k].alloc(soa_f[k].size()));
+        CK(m->wall_exch[k].alloc(soa_x[k].size()));
+        if (cnt[k]) {
+            CK(cudaMemcpy(m->wall_face[k].p, soa_f[k].data(), soa_f[k].size() * 4, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(m->wall_exch[k].p, soa_x[k].data(), soa_x[k].size() * 4, cudaMemcpyHostToDevice));
+        }
+        m->wall_n[k] = cnt[k];
+    }
+    m->wall_kappa = d->kappa;
+    m->wall_c = d->c_plus;
+    if (m->graph.exec) {   // a captured step lacks (or holds stale) wall launches
+        cudaGraphExecDestroy(m->graph.exec);
+        m->graph.exec = nullptr;
+    }
+    return FEA_OK;
+}
+
+fea_status fea_wall_assemble(fea_ctx *ctx, int32_t mesh, double *rhs, void *stream) {
+    Mesh *m;
+    fea_status st = get_mesh(ctx, mesh, &m);
+    if (st) return st;
+    if (!rhs) return fail(ctx, FEA_EINVAL, "null rhs");
+    if (!m->has_field) return fail(ctx, FEA_ESTATE, "no field uploaded for mesh %d", mesh);
+    return add_wall_term(ctx, *m, m->uk.p, m->nu, rhs, FEA_FP64, (cudaStream_t)stream);
 }
 
 // ---- pressure projection -----------------------------------------------------
@@ -1508,7 +1635,10 @@ fea_status fea_sync_status(fea_ctx *ctx, void *stream) {
     CK(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
     if (w & ERR_TIMEOUT) return fail(ctx, FEA_ETIMEOUT, "a bounded device wait gave up (word 0x%x)", w);
     if (w & (ERR_DETJ | ERR_INDEX)) return fail(ctx, FEA_EMESH, "device saw det J <= 0 or a bad index (word 0x%x)", w);
+    if (w & ERR_WALL_GEOM)
+        return fail(ctx, FEA_EMESH, "wall model: degenerate face or exchange point off the fluid side (word 0x%x)", w);
     if (w & ERR_NONFINITE) return fail(ctx, FEA_ENUMERIC, "non-finite element residual (word 0x%x)", w);
+    if (w & ERR_WALL_NEWTON) return fail(ctx, FEA_ENUMERIC, "wall model: u_tau iteration did not converge (word 0x%x)", w);
     return FEA_OK;
 }
 

@@ -21,7 +21,9 @@ enum : unsigned {
     ERR_DETJ = 1u,      // det J <= 0 at some Gauss point
     ERR_NONFINITE = 2u, // non-finite element residual
     ERR_TIMEOUT = 4u,   // a bounded device-side wait gave up
-    ERR_INDEX = 8u      // index out of range (checked builds and upload validation)
+    ERR_INDEX = 8u,     // index out of range (checked builds and upload validation)
+    ERR_WALL_GEOM = 16u,   // wall model: degenerate face or exchange point not on the fluid side
+    ERR_WALL_NEWTON = 32u  // wall model: the u_tau iteration did not converge
 };
 
 // Reference-element tables at the Gauss points of each type's rule.
@@ -117,6 +119,18 @@ cudaError_t launch_rk_update(int64_t n, const double *un, double *uk, double *un
                              const double *minv, const uint8_t *dirichlet, const double *p64, float4 *up32,
                              double a, double b, double dt, cudaStream_t s);
 cudaError_t launch_pack_field(int64_t n, const double *u64, const double *p64, float4 *up32, cudaStream_t s);
+// wall-model boundary term (fea_wall.cu): faces [nv][n_faces] and their
+// exchange nodes, FP64; adds into rhs [3][n]
+struct WallDev {
+    int64_t n_faces;
+    int nv;                 // 3 or 4
+    const int32_t *face;    // [nv][n_faces]
+    const int32_t *exch;    // [nv][n_faces]
+    double kappa, c_plus;
+};
+// fp64: u_tau to FP64 accuracy (else its FP32 root, for the mixed mode)
+cudaError_t launch_wall(const WallDev &w, const double *xyz64, const double *u64, int64_t n, double nu, double *rhs,
+                        unsigned *err, bool fp64, cudaStream_t s);
 cudaError_t launch_f32_to_f64(const float *src, double *dst, int64_t count, cudaStream_t s);
 cudaError_t launch_recip(const double *m, double *minv, int64_t n, cudaStream_t s);
 

@@ -34,7 +34,7 @@ EXPORTED = (
     "fea_mlp_load", "fea_mlp_get", "fea_mlp_forward", "fea_mlp_train_step", "fea_mlp_set_envelope",
     "fea_mlp_fallback_read", "fea_sfc_order", "fea_partition_sfc", "fea_interface_pack", "fea_interface_unpack",
     "fea_poisson_setup", "fea_poisson_solve", "fea_divergence", "fea_gradient", "fea_project",
-    "fea_balance_update", "fea_set_model",
+    "fea_balance_update", "fea_set_model", "fea_wall_setup", "fea_wall_assemble",
 )
 MLP_NPARAM = 8833
 NOALLOC_MAX_NODES = 262144
@@ -127,6 +127,12 @@ class MeshDesc(ctypes.Structure):
                 ("fp64_jac", ctypes.POINTER(ctypes.c_uint8) * 4)]
 
 
+class WallDesc(ctypes.Structure):
+    _fields_ = [("n_tri", ctypes.c_int64), ("tri", ctypes.c_void_p), ("tri_exch", ctypes.c_void_p),
+                ("n_quad", ctypes.c_int64), ("quad", ctypes.c_void_p), ("quad_exch", ctypes.c_void_p),
+                ("kappa", ctypes.c_double), ("c_plus", ctypes.c_double)]
+
+
 class Plan(ctypes.Structure):
     _fields_ = [("scatter", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
                 ("chunk_elems", ctypes.c_int32), ("chunk_acc", ctypes.c_int32)]
@@ -185,6 +191,8 @@ def lib() -> ctypes.CDLL:
         L.fea_partition_sfc.argtypes = [ctypes.POINTER(MeshDesc), i32, i32, vp, ctypes.c_void_p * 4]
         L.fea_balance_update.argtypes = [i32, i32, vp, vp, vp]
         L.fea_set_model.argtypes = [vp, i32, i32, i32]
+        L.fea_wall_setup.argtypes = [vp, i32, ctypes.POINTER(WallDesc)]
+        L.fea_wall_assemble.argtypes = [vp, i32, vp, vp]
         L.fea_interface_pack.argtypes = [vp, vp, i64, vp, vp, i64, vp, i64, vp]
         L.fea_interface_unpack.argtypes = [vp, vp, i64, vp, vp, i64, vp, i64, vp]
         L.fea_mlp_fallback_read.argtypes = [vp, ctypes.POINTER(i64), ctypes.c_int]
@@ -396,6 +404,34 @@ class DeviceMesh:
         """Convective form "gu" | "emac"; Vreman filter width "volume" | "axes"."""
         self.ctx.check(self._L().fea_set_model(self.ctx.handle, self.id, {"gu": 0, "emac": 1}[conv],
                                                {"volume": 0, "axes": 1}[delta]))
+
+    # ---- boundary assembly: wall model ----
+    def wall_setup(self, tri=None, tri_exch=None, quad=None, quad_exch=None, kappa=0.41, c_plus=7.8):
+        """Wall-model faces (host int arrays (F, 3) / (F, 4) of node ids and their
+        exchange nodes, normals out of the fluid); no faces clears them."""
+        keep = []
+
+        def arr(a, nv):
+            if a is None or len(a) == 0:
+                return 0, None
+            a = np.ascontiguousarray(a, dtype=np.int32)
+            assert a.ndim == 2 and a.shape[1] == nv
+            keep.append(a)
+            return a.shape[0], a.ctypes.data
+
+        d = WallDesc()
+        d.n_tri, d.tri = arr(tri, 3)
+        n2, d.tri_exch = arr(tri_exch, 3)
+        d.n_quad, d.quad = arr(quad, 4)
+        n4, d.quad_exch = arr(quad_exch, 4)
+        assert n2 == d.n_tri and n4 == d.n_quad, "faces and exchange nodes differ in length"
+        d.kappa, d.c_plus = float(kappa), float(c_plus)
+        self.ctx.check(self._L().fea_wall_setup(self.ctx.handle, self.id, ctypes.byref(d)))
+
+    def wall_assemble(self, rhs, stream=None):
+        """rhs [3][n] (device float64) += the wall-model term at the current field."""
+        self.ctx.check(self._L().fea_wall_assemble(self.ctx.handle, self.id, _ptr(rhs), _stream(stream)))
+        return rhs
 
     # ---- pressure projection ----
     def poisson_setup(self, pinned=None, stream=None):

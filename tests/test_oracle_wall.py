@@ -62,6 +62,18 @@ def test_newton_round_trip(yp_target):
     assert 0 < it <= 30
 
 
+def test_newton_converges_from_deep_sublayer_to_log_layer():
+    """U y / nu from 1e-14 to 1e10: Newton converges in a few steps (the
+    sublayer bracket is evaluated without cancellation) and the result
+    satisfies its equation."""
+    for nu in (1e-2, 1.0 / 5600, 1.0 / 1.93e6):
+        for y in np.logspace(-7, 0, 12):
+            for U in np.logspace(-10, 2, 16):
+                ut, it = O.wall_utau(U, y, nu)
+                assert it <= 8
+                assert ut * O.reichardt(y * ut / nu)[0] == pytest.approx(U, rel=1e-13)
+
+
 def test_newton_sublayer_closed_form_and_zero():
     nu, y, U = 1e-3, 1e-4, 1e-3          # y+ about 0.01
     ut, _ = O.wall_utau(U, y, nu)
