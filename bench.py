@@ -260,7 +260,12 @@ def run_ours(args):
     dm = ctx.upload_mesh(mesh)
     log(f"[bench] upload {time.time() - t:.1f}s")
     dm.upload_field(field.u, field.p, field.nu, field.c_vreman)
-    plan = dm.autotune(prec="mixed", closure="vreman") if args.autotune else dm.get_plan()
+    if args.plan:
+        sc, th, ch, acc = args.plan.split(":")
+        dm.set_plan(sc, int(th), int(ch), int(acc))
+        plan = dm.get_plan()
+    else:
+        plan = dm.autotune(prec="mixed", closure="vreman") if args.autotune else dm.get_plan()
     log(f"[bench] plan {plan.as_dict()}")
     E = mesh.n_elem_total
     stream = torch.cuda.current_stream()
@@ -428,6 +433,8 @@ def main():
     ap.add_argument("--n-axis", type=int, default=170, help="grid nodes per axis of the airplane-like mesh")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default launch plan instead of timing the candidates")
+    ap.add_argument("--plan", default="", help="fixed launch plan scatter:threads:chunk_elems:chunk_acc "
+                    "(e.g. chunk:128:256:0) instead of autotuning")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
