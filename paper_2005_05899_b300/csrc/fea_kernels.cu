@@ -1352,42 +1352,56 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
 }
 
 // u^(k+1) = a u^n + b (u^(k) + dt M^-1 R) = a u^n + b u^(k) + c R, c = b dt / M;
-// A0: a = 0 (first stage) reads no u^n except at held nodes
+// A0: a = 0 (first stage) reads no u^n except at held nodes.  One node per
+// thread, every load of the node issued before any is used (the hold flag
+// only selects), so that each warp has all its streams in flight at once.
 template <bool A0>
-__global__ void k_rk_update(int64_t n, const double *__restrict__ un, double *uk, double *un_out,
-                            const double *__restrict__ rhs, const double *__restrict__ minv,
-                            const uint8_t *__restrict__ dirichlet, const double *__restrict__ p64, float4 *up32,
-                            double a, double b, double bdt) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const bool hold = dirichlet && dirichlet[i];
-        const double c = bdt * minv[i];
-        double v[3];
+__global__ void __launch_bounds__(256) k_rk_update(int64_t n, const double *__restrict__ un, double *uk,
+                                                   double *un_out, const double *__restrict__ rhs,
+                                                   const double *__restrict__ minv,
+                                                   const uint8_t *__restrict__ dirichlet,
+                                                   const double *__restrict__ p64, float4 *up32, double a, double b,
+                                                   double bdt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool hold = dirichlet && __ldg(&dirichlet[i]);
+    const double c = bdt * __ldg(&minv[i]);
+    const double pi = __ldg(&p64[i]);
+    double r[3], k[3], o[3];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const int64_t k = (int64_t)q * n + i;
-            if (hold)
-                v[q] = un[k];
-            else if (A0)
-                v[q] = fma(c, rhs[k], uk[k]);
-            else
-                v[q] = fma(c, rhs[k], fma(a, un[k], b * uk[k]));
-            uk[k] = v[q];
-            if (un_out) un_out[k] = v[q];
-        }
-        up32[i] = make_float4(f64_to_f32_rn(v[0]), f64_to_f32_rn(v[1]), f64_to_f32_rn(v[2]), f64_to_f32_rn(p64[i]));
+    for (int q = 0; q < 3; ++q) {
+        r[q] = __ldg(&rhs[(int64_t)q * n + i]);
+        k[q] = uk[(int64_t)q * n + i];
+        o[q] = A0 ? 0.0 : __ldg(&un[(int64_t)q * n + i]);
     }
+    double v[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) v[q] = A0 ? fma(c, r[q], k[q]) : fma(c, r[q], fma(a, o[q], b * k[q]));
+    if (hold) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) v[q] = A0 ? __ldg(&un[(int64_t)q * n + i]) : o[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        uk[(int64_t)q * n + i] = v[q];
+        if (un_out) un_out[(int64_t)q * n + i] = v[q];
+    }
+    up32[i] = make_float4(f64_to_f32_rn(v[0]), f64_to_f32_rn(v[1]), f64_to_f32_rn(v[2]), f64_to_f32_rn(pi));
 }
 
 cudaError_t launch_rk_update(int64_t n, const double *un, double *uk, double *un_out, const double *rhs,
                              const double *minv, const uint8_t *dirichlet, const double *p64, float4 *up32, double a,
                              double b, double dt, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
     const int t = 256;
-    const int64_t want = (n + t - 1) / t;
-    const unsigned blocks = (unsigned)(want < 148 * 16 ? (want > 0 ? want : 1) : 148 * 16);
+    const int64_t blocks = (n + t - 1) / t;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (a == 0.0 && b == 1.0)
-        k_rk_update<true><<<blocks, t, 0, s>>>(n, un, uk, un_out, rhs, minv, dirichlet, p64, up32, a, b, b * dt);
+        k_rk_update<true><<<(unsigned)blocks, t, 0, s>>>(n, un, uk, un_out, rhs, minv, dirichlet, p64, up32, a, b,
+                                                         b * dt);
     else
-        k_rk_update<false><<<blocks, t, 0, s>>>(n, un, uk, un_out, rhs, minv, dirichlet, p64, up32, a, b, b * dt);
+        k_rk_update<false><<<(unsigned)blocks, t, 0, s>>>(n, un, uk, un_out, rhs, minv, dirichlet, p64, up32, a, b,
+                                                          b * dt);
     return cudaGetLastError();
 }
 
