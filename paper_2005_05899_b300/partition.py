@@ -68,6 +68,23 @@ def build_parts(mesh: Mesh, n_parts: int, level: int = 10,
     shared = np.flatnonzero(parts_per_class >= 2)
     shared_no = np.full(N, -1, np.int64)
     shared_no[shared] = np.arange(shared.size)
+    # wall-model faces: each goes to the lowest-numbered part that holds all
+    # of its nodes and exchange nodes (a prism-layer face goes with its prism
+    # or a lower part), so that every face is assembled exactly once
+    wall_owner = {}
+    if mesh.wall_faces:
+        member = np.zeros((n_parts, N), bool)
+        for p in range(n_parts):
+            member[p, used[p]] = True
+        for kind, nv in (("tri", 3), ("quad", 4)):
+            f = mesh.wall_faces.get(kind)
+            if f is None or len(f) == 0:
+                continue
+            x = mesh.wall_faces[kind + "_exch"]
+            ok = member[:, f].all(axis=2) & member[:, x].all(axis=2)      # (n_parts, F)
+            if not ok.any(axis=0).all():
+                raise ValueError(f"a wall face ({kind}) has nodes or exchange nodes in no single part")
+            wall_owner[kind] = np.argmax(ok, axis=0)
     out = []
     g2l = np.full(N, -1, np.int64)
     for p in range(n_parts):
@@ -91,10 +108,18 @@ def build_parts(mesh: Mesh, n_parts: int, level: int = 10,
         if np.any(local_master < 0):
             raise ValueError("a class local to one part lost its master")
         iface_loc = np.flatnonzero(is_shared).astype(np.int64)
+        wall = None
+        if wall_owner:
+            wall = {}
+            for kind, owner in wall_owner.items():
+                mine = owner == p
+                wall[kind] = g2l[mesh.wall_faces[kind][mine]].astype(np.int32)
+                wall[kind + "_exch"] = g2l[mesh.wall_faces[kind + "_exch"][mine]].astype(np.int32)
         sub = Mesh(xyz=mesh.xyz[nodes], conn=conn,
                    periodic_master=local_master.astype(np.int32) if mesh.periodic_master is not None else None,
                    dirichlet=mesh.dirichlet[nodes] if mesh.dirichlet is not None else None,
-                   fp64_flag=flags, name=f"{mesh.name}.part{p}of{n_parts}", meta=dict(mesh.meta))
+                   fp64_flag=flags, name=f"{mesh.name}.part{p}of{n_parts}", meta=dict(mesh.meta),
+                   wall_faces=wall)
         out.append(Part(index=p, mesh=sub, nodes=nodes, elems=elems, iface_loc=iface_loc,
                         iface_cls=shared_no[cls[iface_loc]], n_shared=int(shared.size)))
     return out

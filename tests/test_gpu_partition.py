@@ -82,3 +82,36 @@ def test_interface_kernels_flag_bad_indices(ctx):
     with pytest.raises(fea.FeaError):
         ctx.sync_status()
     ctx.sync_status()
+
+
+def test_parts_with_wall_faces_equal_the_whole_mesh(ctx):
+    """Wall faces split over the parts (each face with one owner) plus the
+    exchange give the whole mesh's folded element + wall-model RHS."""
+    m = mg.channel_mesh(nx=14, ny=12, nz=8, seed=3, n_layers=2, split_frac=0.3)
+    f = mg.channel_field(m, seed=4, nu=1e-3)
+    u = f.u + 0.1 * np.random.default_rng(6).standard_normal(f.u.shape)
+    parts = P.build_parts(m, 3)
+    rhs, ex = [], []
+    for part in parts:
+        dm = ctx.upload_mesh(part.mesh)
+        dm.upload_field(u[part.nodes], f.p[part.nodes], f.nu, f.c_vreman)
+        dm.wall_setup(**part.mesh.wall_faces)
+        r = torch.empty((3, dm.n_nodes), dtype=torch.float64, device="cuda")
+        dm.assemble(r, prec="fp64", scatter="atomic")
+        dm.wall_assemble(r)
+        dm.fold(r)
+        e = P.Exchange(ctx, part)
+        e.pack(r)
+        rhs.append(r)
+        ex.append(e)
+    total = sum(e.buf for e in ex)
+    for e, r in zip(ex, rhs):
+        e.buf.copy_(total)
+        e.unpack(r)
+    ctx.sync_status()
+    om = O.OracleMesh.of(m)
+    ref = O.periodic_fold(m.periodic_master, O.assemble_rhs(om, u, f.p, f.nu, f.c_vreman, "vreman")
+                          + O.wall_rhs(om, u, f.nu, **m.wall_faces))
+    scale = np.abs(ref).max()
+    for part, r in zip(parts, rhs):
+        assert np.abs(r.cpu().numpy().T - ref[part.nodes]).max() <= 1e-12 * scale

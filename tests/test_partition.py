@@ -87,6 +87,20 @@ def test_parts_cover_the_mesh_and_agree_on_shared_classes():
         assert p.mesh.periodic_master.max() < p.n_nodes
 
 
+def test_every_wall_face_goes_to_exactly_one_part():
+    m, _ = small_mixed()
+    assert m.wall_faces["tri"].shape[0] > 0
+    parts = P.build_parts(m, 3)
+    got = np.concatenate([p.nodes[p.mesh.wall_faces["tri"]] for p in parts])
+    gx = np.concatenate([p.nodes[p.mesh.wall_faces["tri_exch"]] for p in parts])
+    key = lambda f, x: np.sort([tuple(r) for r in np.concatenate([f, x], axis=1)], axis=0)
+    assert got.shape == m.wall_faces["tri"].shape
+    assert np.array_equal(key(got, gx), key(m.wall_faces["tri"], m.wall_faces["tri_exch"]))
+    # the node order (and so the face orientation) is kept
+    ref = {tuple(r) for r in np.concatenate([m.wall_faces["tri"], m.wall_faces["tri_exch"]], axis=1)}
+    assert {tuple(r) for r in np.concatenate([got, gx], axis=1)} == ref
+
+
 def _np_pack(v, loc, cls, out):
     out.zero_()
     for d in range(3):
