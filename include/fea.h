@@ -87,9 +87,16 @@ enum { FEA_TERM_CONV = 1, FEA_TERM_VISC = 2, FEA_TERM_SGS = 4, FEA_TERM_PRES = 8
 typedef enum {
     FEA_SCATTER_AUTO = 0,   /* the mesh's current plan (autotuned or default) */
     FEA_SCATTER_ATOMIC = 1, /* one FP64 atomic add per element node and component */
-    FEA_SCATTER_CHUNK = 2   /* CTA-local assembly of a chunk of elements in
+    FEA_SCATTER_CHUNK = 2,  /* CTA-local assembly of a chunk of elements in
                                shared memory; FP64 atomics only for nodes the
                                chunk shares with other chunks */
+    FEA_SCATTER_COLOUR = 3, /* greedy element colouring per category (no two
+                               elements of a colour share a node), one launch
+                               per colour, plain FP64 read-modify-write: the sum
+                               order is fixed, results are bitwise reproducible */
+    FEA_SCATTER_WARP = 4    /* FP64 atomics after a warp-level sum of the lanes
+                               whose element has the same node in the same local
+                               slot (match_any): fewer atomics on shared nodes */
 } fea_scatter;
 
 /* convective form (section 2.1 writes the EMAC bracket; see fea_set_model) */
@@ -121,7 +128,8 @@ typedef struct {
 
 /* Launch plan of one mesh (chosen by fea_autotune or set by hand). */
 typedef struct {
-    int32_t scatter;            /* fea_scatter (not AUTO); FEA_FP64 always uses ATOMIC */
+    int32_t scatter;            /* fea_scatter (not AUTO); under FEA_FP64 a CHUNK plan
+                                   runs ATOMIC (COLOUR and WARP apply to both) */
     int32_t threads_per_block;  /* element kernels: multiple of 32 in [32, 1024] (capped at 256) */
     int32_t chunk_elems;        /* elements per chunk for FEA_SCATTER_CHUNK: multiple of 32 in [32, 4096] */
     int32_t chunk_acc;          /* FEA_SCATTER_CHUNK nodal sums inside a chunk: 0 = FP32,

@@ -211,6 +211,10 @@ struct Bucket {
     DevBuf<int32_t> chunk_nodes;
     DevBuf<float4> chunk_rec;
     DevBuf<uint32_t> inc_range;
+    // colouring (FEA_SCATTER_COLOUR), built on first use
+    DevBuf<int32_t> col_conn, col_orig;
+    std::vector<int64_t> col_off;   // [n_colours + 1] element offsets per colour
+    int n_colours = 0;
     BucketDev dev() const {
         BucketDev b;
         b.etype = etype;
@@ -226,6 +230,8 @@ struct Bucket {
         b.chunk_rec = chunk_rec.p;
         b.inc_range = inc_range.p;
         b.max_chunk_nodes = max_chunk_nodes;
+        b.col_conn = col_conn.p;
+        b.col_orig = col_orig.p;
         return b;
     }
 };
@@ -454,6 +460,65 @@ fea_status build_chunks(fea_ctx *ctx, Mesh &m, Bucket &b, int C) {
     return FEA_OK;
 }
 
+// Greedy colouring of a category's elements in their (Morton) order: each
+// element takes the lowest colour that none of its nodes has seen yet, so no
+// two elements of a colour share a node.  Node colour sets are bit masks of
+// kColourWords x 64 colours.  The elements are then stored colour by colour
+// (Morton order kept within a colour).
+constexpr int kColourWords = 4;
+
+fea_status build_colours(fea_ctx *ctx, const Mesh &m, Bucket &b) {
+    const int nen = kNen[b.etype];
+    const int64_t cnt = b.count;
+    std::vector<uint64_t> seen((size_t)m.n * kColourWords, 0ull);
+    std::vector<int32_t> col((size_t)cnt);
+    int n_col = 0;
+    for (int64_t e = 0; e < cnt; ++e) {
+        uint64_t mask[kColourWords] = {0, 0, 0, 0};
+        for (int a = 0; a < nen; ++a) {
+            const uint64_t *w = &seen[(size_t)b.conn_h[(size_t)a * cnt + e] * kColourWords];
+            for (int k = 0; k < kColourWords; ++k) mask[k] |= w[k];
+        }
+        int c = -1;
+        for (int k = 0; k < kColourWords && c < 0; ++k)
+            if (~mask[k]) c = 64 * k + __builtin_ctzll(~mask[k]);
+        if (c < 0) return fail(ctx, FEA_EMESH, "colouring needs more than %d colours", 64 * kColourWords);
+        col[(size_t)e] = c;
+        n_col = std::max(n_col, c + 1);
+        for (int a = 0; a < nen; ++a)
+            seen[(size_t)b.conn_h[(size_t)a * cnt + e] * kColourWords + c / 64] |= 1ull << (c % 64);
+    }
+    std::vector<int64_t> off((size_t)n_col + 1, 0);
+    for (int64_t e = 0; e < cnt; ++e) off[(size_t)col[(size_t)e] + 1]++;
+    for (int c = 0; c < n_col; ++c) off[(size_t)c + 1] += off[(size_t)c];
+    std::vector<int64_t> pos(off.begin(), off.end() - 1);
+    std::vector<int32_t> perm((size_t)cnt);
+    for (int64_t e = 0; e < cnt; ++e) perm[(size_t)pos[(size_t)col[(size_t)e]]++] = (int32_t)e;
+    std::vector<int32_t> cc((size_t)nen * cnt), corig((size_t)cnt), orig_h((size_t)cnt);
+    CK(cudaMemcpy(orig_h.data(), b.orig.p, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < cnt; ++k) {
+        const int32_t e = perm[(size_t)k];
+        for (int a = 0; a < nen; ++a) cc[(size_t)a * cnt + k] = b.conn_h[(size_t)a * cnt + e];
+        corig[(size_t)k] = orig_h[(size_t)e];
+    }
+    CK(b.col_conn.alloc(cc.size()));
+    CK(b.col_orig.alloc(corig.size()));
+    CK(cudaMemcpy(b.col_conn.p, cc.data(), cc.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b.col_orig.p, corig.data(), corig.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    b.col_off = off;
+    b.n_colours = n_col;
+    return FEA_OK;
+}
+
+fea_status ensure_colours(fea_ctx *ctx, Mesh &m) {
+    for (auto &bp : m.buckets) {
+        if (bp->count == 0 || bp->col_conn.p) continue;
+        fea_status st = build_colours(ctx, m, *bp);
+        if (st) return st;
+    }
+    return FEA_OK;
+}
+
 fea_status ensure_chunks(fea_ctx *ctx, Mesh &m, int C) {
     for (auto &bp : m.buckets) {
         if (bp->count == 0 || (bp->lconn.p && bp->chunk_elems == C)) continue;
@@ -468,6 +533,13 @@ fea_status assemble_into(fea_ctx *ctx, Mesh &m, fea_prec prec, fea_closure closu
     CK(cudaMemsetAsync(rhs, 0, sizeof(double) * 3 * m.n, s));
     FieldDev f = m.field();
     if (scatter == FEA_SCATTER_AUTO) scatter = (fea_scatter)m.plan.scatter;
+    // the colour scatter's plain read-modify-writes need the categories one
+    // after the other on one stream (the MLP closure keeps atomics)
+    const bool colour = scatter == FEA_SCATTER_COLOUR && closure != FEA_CLOSURE_MLP;
+    if (colour) {
+        fea_status cs = ensure_colours(ctx, m);
+        if (cs) return cs;
+    }
     // FP64-Jacobian categories (FP64 pipe) go first, on a side stream, so
     // that they overlap the FP32-bound categories on the caller's stream.
     bool forked = false;
@@ -475,8 +547,9 @@ fea_status assemble_into(fea_ctx *ctx, Mesh &m, fea_prec prec, fea_closure closu
         for (auto &bp : m.buckets) {
             const Bucket &b = *bp;
             if (!b.count) continue;
-            const bool side = prec == FEA_MIXED && b.fp64j;
-            if (side != (pass == 0)) continue;
+            const bool first = prec == FEA_MIXED && b.fp64j;
+            if (first != (pass == 0)) continue;
+            const bool side = first && !colour;
             cudaStream_t ls = s;
             if (side) {
                 if (!forked) {
@@ -503,10 +576,16 @@ fea_status assemble_into(fea_ctx *ctx, Mesh &m, fea_prec prec, fea_closure closu
                 CK(cudaEventCreate(&pr.e1));
                 CK(cudaEventRecord(pr.e0, ls));
             }
-            if (prec == FEA_MIXED && scatter == FEA_SCATTER_CHUNK && b.lconn.p)
+            if (colour) {
+                CK(launch_assemble_colour(b.dev(), f, a, prec, m.plan.threads_per_block, b.col_off.data(),
+                                          b.n_colours, ls));
+                ctx->launches += b.n_colours - 1;
+            } else if (prec == FEA_MIXED && scatter == FEA_SCATTER_CHUNK && b.lconn.p)
                 CK(launch_assemble_chunk(b.dev(), f, a, m.plan.threads_per_block, m.plan.chunk_acc, ls));
             else
-                CK(launch_assemble_bucket(b.dev(), f, a, prec, FEA_SCATTER_ATOMIC, m.plan.threads_per_block, ls));
+                CK(launch_assemble_bucket(b.dev(), f, a, prec,
+                                          scatter == FEA_SCATTER_WARP ? FEA_SCATTER_WARP : FEA_SCATTER_ATOMIC,
+                                          m.plan.threads_per_block, ls));
             ctx->launches++;
             if (timed) {
                 CK(cudaEventRecord(pr.e1, ls));
@@ -604,13 +683,19 @@ fea_status stage_with_scratch(fea_ctx *ctx, int32_t mesh, int32_t stage, double 
     f.c_vreman = c_vreman;
     CK(cudaMemsetAsync(rhs, 0, sizeof(double) * 3 * n, s));
     const fea_scatter scatter = (fea_scatter)m->plan.scatter;
+    // colour tables are built by fea_set_plan / fea_autotune, never here
+    const bool colour = scatter == FEA_SCATTER_COLOUR && closure != FEA_CLOSURE_MLP;
+    if (colour)
+        for (auto &bp : m->buckets)
+            if (bp->count && !bp->col_conn.p) return fail(ctx, FEA_ESTATE, "colour tables missing (set the plan)");
     bool forked = false;
     for (int pass = 0; pass < 2; ++pass) {
         for (auto &bp : m->buckets) {
             const Bucket &b = *bp;
             if (!b.count) continue;
-            const bool side = prec == FEA_MIXED && b.fp64j;
-            if (side != (pass == 0)) continue;
+            const bool first = prec == FEA_MIXED && b.fp64j;
+            if (first != (pass == 0)) continue;
+            const bool side = first && !colour;
             cudaStream_t ls = s;
             if (side) {
                 if (!forked) {
@@ -628,10 +713,16 @@ fea_status stage_with_scratch(fea_ctx *ctx, int32_t mesh, int32_t stage, double 
             a.err = ctx->d_err;
             a.mlp = closure == FEA_CLOSURE_MLP ? mlp_fast_ptr(ctx->mlp_w.p) : nullptr;
             a.mlp_fb = closure == FEA_CLOSURE_MLP ? ctx->mlp_fb.p : nullptr;
-            if (prec == FEA_MIXED && scatter == FEA_SCATTER_CHUNK && b.lconn.p)
+            if (colour) {
+                CK(launch_assemble_colour(b.dev(), f, a, prec, m->plan.threads_per_block, b.col_off.data(),
+                                          b.n_colours, ls));
+                ctx->launches += b.n_colours - 1;
+            } else if (prec == FEA_MIXED && scatter == FEA_SCATTER_CHUNK && b.lconn.p)
                 CK(launch_assemble_chunk(b.dev(), f, a, m->plan.threads_per_block, m->plan.chunk_acc, ls));
             else
-                CK(launch_assemble_bucket(b.dev(), f, a, prec, FEA_SCATTER_ATOMIC, m->plan.threads_per_block, ls));
+                CK(launch_assemble_bucket(b.dev(), f, a, prec,
+                                          scatter == FEA_SCATTER_WARP ? FEA_SCATTER_WARP : FEA_SCATTER_ATOMIC,
+                                          m->plan.threads_per_block, ls));
             ctx->launches++;
         }
     }
@@ -931,7 +1022,7 @@ fea_status fea_assemble_rhs(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closu
     if (st) return st;
     if ((st = check_args(ctx, prec, closure, mask))) return st;
     if (!rhs_out) return fail(ctx, FEA_EINVAL, "null rhs_out");
-    if (scatter < FEA_SCATTER_AUTO || scatter > FEA_SCATTER_CHUNK) return fail(ctx, FEA_EINVAL, "bad scatter");
+    if (scatter < FEA_SCATTER_AUTO || scatter > FEA_SCATTER_WARP) return fail(ctx, FEA_EINVAL, "bad scatter");
     if (!m->has_field) return fail(ctx, FEA_ESTATE, "no field uploaded for mesh %d", mesh);
     return assemble_into(ctx, *m, prec, closure, mask, scatter, rhs_out, nut_out, (cudaStream_t)stream);
 }
@@ -1090,7 +1181,8 @@ fea_status fea_rk_step_graph(fea_ctx *ctx, int32_t mesh, double dt, fea_prec pre
     CK(cudaGraphLaunch(g.exec, (cudaStream_t)stream));
     // kernels per step: 3 x (buckets + wall faces + fold 2 + update 1)
     int64_t per_stage = 1 + (m->slaves.n ? 2 : 0) + m->wall_launches();
-    for (auto &b : m->buckets) per_stage += b->count ? 1 : 0;
+    const bool colour = m->plan.scatter == FEA_SCATTER_COLOUR && closure != FEA_CLOSURE_MLP;
+    for (auto &b : m->buckets) per_stage += b->count ? (colour ? b->n_colours : 1) : 0;
     ctx->launches += 3 * per_stage;
     return FEA_OK;
 }
@@ -1119,8 +1211,10 @@ fea_status fea_set_plan(fea_ctx *ctx, int32_t mesh, const fea_plan *plan) {
     fea_status st = get_mesh(ctx, mesh, &m);
     if (st) return st;
     if (!plan) return fail(ctx, FEA_EINVAL, "null plan");
-    if (plan->scatter != FEA_SCATTER_ATOMIC && plan->scatter != FEA_SCATTER_CHUNK)
-        return fail(ctx, FEA_EINVAL, "plan scatter must be ATOMIC or CHUNK");
+    if (plan->scatter != FEA_SCATTER_ATOMIC && plan->scatter != FEA_SCATTER_CHUNK &&
+        plan->scatter != FEA_SCATTER_COLOUR && plan->scatter != FEA_SCATTER_WARP)
+        return fail(ctx, FEA_EINVAL, "plan scatter must be ATOMIC, CHUNK, COLOUR or WARP");
+    if (plan->scatter == FEA_SCATTER_COLOUR && (st = ensure_colours(ctx, *m))) return st;
     if (plan->threads_per_block < 32 || plan->threads_per_block > 1024 || plan->threads_per_block % 32)
         return fail(ctx, FEA_EINVAL, "threads_per_block must be a multiple of 32 in [32, 1024]");
     if (plan->scatter == FEA_SCATTER_CHUNK) {
@@ -1185,6 +1279,11 @@ fea_status fea_autotune(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure c
     float best_ms = 1e30f;
     std::vector<fea_plan> cands;
     for (int t : {128, 256}) cands.push_back(fea_plan{FEA_SCATTER_ATOMIC, t, m->plan.chunk_elems, 0});
+    for (int t : {128, 256}) cands.push_back(fea_plan{FEA_SCATTER_WARP, t, m->plan.chunk_elems, 0});
+    if (closure != FEA_CLOSURE_MLP) {
+        if ((st = ensure_colours(ctx, *m))) return st;
+        for (int t : {128, 256}) cands.push_back(fea_plan{FEA_SCATTER_COLOUR, t, m->plan.chunk_elems, 0});
+    }
     if (prec == FEA_MIXED)
         for (int C : {256, 512, 1024})
             for (int t : {128, 256, 512})

@@ -60,6 +60,9 @@ struct BucketDev {
     const uint32_t *inc_range;      // per local node: first incidence | count << 16; local
                                     // nodes are ordered by decreasing incidence count
     int32_t max_chunk_nodes;        // max L_k
+    // colouring (FEA_SCATTER_COLOUR): the elements reordered colour by colour
+    const int32_t *col_conn;        // [nen][count] node ids in colour order
+    const int32_t *col_orig;        // [count] caller element index, colour order
 };
 
 // Per-mesh nodal data used by the kernels.
@@ -90,6 +93,10 @@ struct AsmArgs {
 cudaError_t upload_ref_tables(const RefTables &t);
 cudaError_t launch_assemble_bucket(const BucketDev &b, const FieldDev &f, const AsmArgs &a, fea_prec prec,
                                    fea_scatter scatter, int threads, cudaStream_t s);
+// colour scatter: one launch per colour over [col_off[k], col_off[k+1]) of the
+// colour-ordered connectivity (col_off on the host)
+cudaError_t launch_assemble_colour(const BucketDev &b, const FieldDev &f, const AsmArgs &a, fea_prec prec,
+                                   int threads, const int64_t *col_off, int n_colours, cudaStream_t s);
 cudaError_t launch_assemble_chunk(const BucketDev &b, const FieldDev &f, const AsmArgs &a, int threads,
                                   int compensated, cudaStream_t s);
 size_t chunk_smem_bytes(const BucketDev &b);

@@ -606,10 +606,38 @@ __device__ __forceinline__ void count_fallbacks(unsigned long long *counter, int
 // ---------------------------------------------------------------------------
 // ATOMIC scatter kernel: thread per element, FP64 atomic adds into rhs [3][n]
 
-template <int ET, typename R, bool J64, bool MLP = false>
+// Sum of v over the lanes of `peers` (lanes whose elements have the same node
+// in this local slot), left in the lowest of them; the others are added in
+// increasing lane order, one per round, so the sum order is fixed.  Every
+// lane of `act` calls it with its own peers (a partition of act).
+__device__ __forceinline__ void peer_sum3(unsigned act, unsigned peers, double &v0, double &v1, double &v2) {
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    unsigned rest = peers & ~(1u << leader);
+    double s0 = v0, s1 = v1, s2 = v2;
+    while (__any_sync(act, rest != 0u)) {
+        const int src = rest ? __ffs(rest) - 1 : lane;
+        const double t0 = __shfl_sync(act, v0, src), t1 = __shfl_sync(act, v1, src), t2 = __shfl_sync(act, v2, src);
+        if (rest) {
+            s0 += t0;
+            s1 += t1;
+            s2 += t2;
+            rest &= rest - 1u;
+        }
+    }
+    v0 = s0, v1 = s1, v2 = s2;
+}
+
+// AGG (FEA_SCATTER_WARP): before the FP64 atomics, the lanes of a warp whose
+// elements have the same node in the same local slot sum their contributions
+// (Morton-ordered neighbours often share a corner in the same slot); the
+// lowest such lane issues the atomics.
+template <int ET, typename R, bool J64, bool MLP = false, bool AGG = false>
 __global__ void __launch_bounds__(256) k_assemble_atomic(BucketDev b, FieldDev f, AsmArgs args) {
     constexpr int nen = kNen[ET], ng = kNg[ET];
     const int64_t e_raw = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // lanes with an element (blocks are whole warps); taken before any lane returns
+    const unsigned act = AGG ? __ballot_sync(0xffffffffu, e_raw < b.count) : 0u;
     // with the MLP the whole warp evaluates the network together: idle lanes
     // repeat the last element and store nothing
     if (!MLP && e_raw >= b.count) return;
@@ -646,15 +674,92 @@ __global__ void __launch_bounds__(256) k_assemble_atomic(BucketDev b, FieldDev f
     for (int a = 0; a < nen; ++a) chk += r[a][0] + r[a][1] + r[a][2];
     if (bad) set_err(args.err, ERR_DETJ);
     if (!isfinite(chk)) set_err(args.err, ERR_NONFINITE);
+    if constexpr (AGG) {
+        __syncwarp(act);
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int a = 0; a < nen; ++a) {
+            const unsigned peers = __match_any_sync(act, idx[a]);
+            double v0 = double(r[a][0]), v1 = double(r[a][1]), v2 = double(r[a][2]);
+            peer_sum3(act, peers, v0, v1, v2);
+            if (lane == __ffs(peers) - 1) {
+                atomicAdd(&args.rhs[idx[a]], v0);
+                atomicAdd(&args.rhs[f.n + idx[a]], v1);
+                atomicAdd(&args.rhs[2 * f.n + idx[a]], v2);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < nen; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) atomicAdd(&args.rhs[(int64_t)i * f.n + idx[a]], double(r[a][i]));
+    }
+}
+
+// COLOUR scatter: thread per element of one colour (elements [e0, e1) of the
+// colour-ordered connectivity); no two elements of a colour share a node, so
+// the FP64 sums are plain read-modify-writes, in launch (colour) order.
+template <int ET, typename R, bool J64>
+__global__ void __launch_bounds__(256) k_assemble_colour(BucketDev b, FieldDev f, AsmArgs args, int64_t e0,
+                                                         int64_t e1) {
+    constexpr int nen = kNen[ET], ng = kNg[ET];
+    const int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= e1) return;
+    int idx[nen];
+#pragma unroll
+    for (int a = 0; a < nen; ++a) idx[a] = __ldg(&b.col_conn[(int64_t)a * b.count + e]);
+    Gathered<R, J64> el;
+    gather<ET, R, J64>(f, idx, el);
+    R r[kMaxNen][3];
+    bool bad = false;
+    float *nut = args.nut ? args.nut + (int64_t)__ldg(&b.col_orig[e]) * ng : nullptr;
+    if constexpr (ET == FEA_TET04)
+        tet_residual<R, J64, false>(el, f, args, r, nut, bad);
+    else
+        element_residual<ET, R, J64, false>(el, f, args, r, nut, bad);
+    R chk = R(0);
+#pragma unroll
+    for (int a = 0; a < nen; ++a) chk += r[a][0] + r[a][1] + r[a][2];
+    if (bad) set_err(args.err, ERR_DETJ);
+    if (!isfinite(chk)) set_err(args.err, ERR_NONFINITE);
 #pragma unroll
     for (int a = 0; a < nen; ++a)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) atomicAdd(&args.rhs[(int64_t)i * f.n + idx[a]], double(r[a][i]));
+        for (int i = 0; i < 3; ++i) args.rhs[(int64_t)i * f.n + idx[a]] += double(r[a][i]);
+}
+
+template <int ET>
+static cudaError_t launch_colour_t(const BucketDev &b, const FieldDev &f, const AsmArgs &a, fea_prec prec, int threads,
+                                   const int64_t *col_off, int n_colours, cudaStream_t s) {
+    auto kern = prec == FEA_FP64 ? k_assemble_colour<ET, double, false>
+                                 : (b.fp64j ? k_assemble_colour<ET, float, true> : k_assemble_colour<ET, float, false>);
+    for (int c = 0; c < n_colours; ++c) {
+        const int64_t e0 = col_off[c], e1 = col_off[c + 1];
+        if (e1 <= e0) continue;
+        kern<<<(unsigned)((e1 - e0 + threads - 1) / threads), threads, 0, s>>>(b, f, a, e0, e1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_assemble_colour(const BucketDev &b, const FieldDev &f, const AsmArgs &a, fea_prec prec,
+                                   int threads, const int64_t *col_off, int n_colours, cudaStream_t s) {
+    if (b.count == 0) return cudaSuccess;
+    if (!b.col_conn || !b.col_orig || !col_off || a.closure == FEA_CLOSURE_MLP) return cudaErrorInvalidValue;
+    if (threads > 256) threads = 256;
+    switch (b.etype) {
+        case FEA_TET04: return launch_colour_t<FEA_TET04>(b, f, a, prec, threads, col_off, n_colours, s);
+        case FEA_PYR05: return launch_colour_t<FEA_PYR05>(b, f, a, prec, threads, col_off, n_colours, s);
+        case FEA_PEN06: return launch_colour_t<FEA_PEN06>(b, f, a, prec, threads, col_off, n_colours, s);
+        case FEA_HEX08: return launch_colour_t<FEA_HEX08>(b, f, a, prec, threads, col_off, n_colours, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <int ET>
 static cudaError_t launch_atomic_t(const BucketDev &b, const FieldDev &f, const AsmArgs &a, fea_prec prec,
-                                   int threads, cudaStream_t s) {
+                                   int threads, bool agg, cudaStream_t s) {
     const unsigned blocks = (unsigned)((b.count + threads - 1) / threads);
     if (a.closure == FEA_CLOSURE_MLP) {
         const size_t smem = mlp_smem_bytes(threads, mlp_rows_per_elem(ET));
@@ -664,6 +769,13 @@ static cudaError_t launch_atomic_t(const BucketDev &b, const FieldDev &f, const 
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         kern<<<blocks, threads, smem, s>>>(b, f, a);
+    } else if (agg) {
+        if (prec == FEA_FP64)
+            k_assemble_atomic<ET, double, false, false, true><<<blocks, threads, 0, s>>>(b, f, a);
+        else if (b.fp64j)
+            k_assemble_atomic<ET, float, true, false, true><<<blocks, threads, 0, s>>>(b, f, a);
+        else
+            k_assemble_atomic<ET, float, false, false, true><<<blocks, threads, 0, s>>>(b, f, a);
     } else if (prec == FEA_FP64)
         k_assemble_atomic<ET, double, false><<<blocks, threads, 0, s>>>(b, f, a);
     else if (b.fp64j)
@@ -677,12 +789,14 @@ cudaError_t launch_assemble_bucket(const BucketDev &b, const FieldDev &f, const 
                                    fea_scatter scatter, int threads, cudaStream_t s) {
     if (b.count == 0) return cudaSuccess;
     if (threads > 256) threads = 256;
-    (void)scatter;
+    // FEA_SCATTER_WARP: warp-aggregated atomics (not with the MLP, whose
+    // kernels keep plain atomics); anything else: plain atomics
+    const bool agg = scatter == FEA_SCATTER_WARP && a.closure != FEA_CLOSURE_MLP;
     switch (b.etype) {
-        case FEA_TET04: return launch_atomic_t<FEA_TET04>(b, f, a, prec, threads, s);
-        case FEA_PYR05: return launch_atomic_t<FEA_PYR05>(b, f, a, prec, threads, s);
-        case FEA_PEN06: return launch_atomic_t<FEA_PEN06>(b, f, a, prec, threads, s);
-        case FEA_HEX08: return launch_atomic_t<FEA_HEX08>(b, f, a, prec, threads, s);
+        case FEA_TET04: return launch_atomic_t<FEA_TET04>(b, f, a, prec, threads, agg, s);
+        case FEA_PYR05: return launch_atomic_t<FEA_PYR05>(b, f, a, prec, threads, agg, s);
+        case FEA_PEN06: return launch_atomic_t<FEA_PEN06>(b, f, a, prec, threads, agg, s);
+        case FEA_HEX08: return launch_atomic_t<FEA_HEX08>(b, f, a, prec, threads, agg, s);
     }
     return cudaErrorInvalidValue;
 }

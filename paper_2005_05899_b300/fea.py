@@ -23,7 +23,7 @@ NNODE = (4, 5, 6, 8)
 NGAUSS = (4, 8, 6, 8)
 PREC = {"fp64": 0, "mixed": 1}
 CLOSURE = {"none": 0, "vreman": 1, "mlp": 2}
-SCATTER = {"auto": 0, "atomic": 1, "chunk": 2}
+SCATTER = {"auto": 0, "atomic": 1, "chunk": 2, "colour": 3, "warp": 4}
 TERM_CONV, TERM_VISC, TERM_SGS, TERM_PRES, TERM_ALL = 1, 2, 4, 8, 15
 
 EXPORTED = (
