@@ -205,6 +205,17 @@ fea_status fea_assemble_rhs_batched(fea_ctx *ctx, const int32_t *meshes, int32_t
                                     fea_closure closure, uint32_t term_mask, double *const *rhs_out,
                                     void *stream);
 
+/* Autotuner of the batched form for these meshes (their fields uploaded):
+ * times the persistent launch over chunk tables of 128, 256 and 512 elements
+ * (FEA_MIXED) against per-mesh launches with the ATOMIC, WARP and COLOUR
+ * scatters, and keeps the fastest: every mesh's plan is set to it, and
+ * fea_assemble_rhs_batched of this context then uses the persistent launch
+ * (best_out->scatter == FEA_SCATTER_CHUNK) or per-mesh launches (otherwise).
+ * Synchronises the device; overwrites the meshes' library-owned RHS
+ * buffers.  best_out may be NULL. */
+fea_status fea_autotune_batched(fea_ctx *ctx, const int32_t *meshes, int32_t n, fea_prec prec, fea_closure closure,
+                                fea_plan *best_out);
+
 /* In-place periodic fold of v [ncomp][n_nodes] (device): every slave's value
  * is added to its master, then copied back to the slave.  No-op without a
  * periodic map. */

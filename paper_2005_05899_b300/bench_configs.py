@@ -86,6 +86,21 @@ def batch(reps: int, count: int = 64):
         ctx.sync_status()
         ms = e0.elapsed_time(e1) / reps
         res[mode] = {"ms": ms, "melem_s": E / ms / 1e3, "launches_per_call": (ctx.launch_count - l0) / reps}
+    # the batch autotuner's choice (persistent launch with its chunk size, or per-mesh scatter)
+    best = ctx.autotune_batched(dms)
+    for _ in range(3):
+        ctx.assemble_batched(dms, outs)
+    torch.cuda.synchronize()
+    l0 = ctx.launch_count
+    e0.record()
+    for _ in range(reps):
+        ctx.assemble_batched(dms, outs)
+    e1.record()
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    ms = e0.elapsed_time(e1) / reps
+    res["autotuned"] = {"plan": best.as_dict(), "ms": ms, "melem_s": E / ms / 1e3,
+                        "launches_per_call": (ctx.launch_count - l0) / reps}
     print(json.dumps({"workload": f"batch of {count} channel-like meshes, log-uniform 1e4-5e5 elements",
                       "elements": E, "generate_s": gen_s, **res}), flush=True)
 

@@ -323,6 +323,7 @@ struct fea_ctx {
     DevBuf<double *> batch_rhs;
     DevBuf<int64_t> batch_len;
     DevBuf<unsigned long long> batch_counter;
+    bool batch_per_mesh = false;   // fea_autotune_batched chose per-mesh launches over the persistent one
     // learned closure: FP32 master parameters, Adam moments, packed BF16 weights
     DevBuf<float> mlp_theta, mlp_m1, mlp_m2, mlp_grad, mlp_loss, mlp_norm;
     DevBuf<unsigned char> mlp_w;
@@ -1042,10 +1043,11 @@ fea_status fea_assemble_rhs_batched(fea_ctx *ctx, const int32_t *meshes, int32_t
             if (b->count && (!b->lconn.p || (b->fp64j && b->etype != FEA_PEN06))) tables = false;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    if (!tables) {  // FP64 path: per-mesh atomic launches
+    if (!tables || ctx->batch_per_mesh) {  // per-mesh launches (FP64 path, or the autotuner's choice)
         for (int32_t k = 0; k < n; ++k) {
             Mesh *m = ctx->meshes[meshes[k]].get();
-            st = assemble_into(ctx, *m, prec, closure, mask, FEA_SCATTER_ATOMIC, rhs_out[k], nullptr, s);
+            const fea_scatter sc = !tables ? FEA_SCATTER_ATOMIC : FEA_SCATTER_AUTO;
+            st = assemble_into(ctx, *m, prec, closure, mask, sc, rhs_out[k], nullptr, s);
             if (st) return st;
         }
         return FEA_OK;
@@ -1115,8 +1117,13 @@ fea_status fea_assemble_rhs_batched(fea_ctx *ctx, const int32_t *meshes, int32_t
         CK(cudaEventCreate(&pr.e1));
         CK(cudaEventRecord(pr.e0, s));
     }
+    bool variants = false;
+    for (int32_t k = 0; k < n; ++k) {
+        const Mesh *m = ctx->meshes[meshes[k]].get();
+        variants |= m->conv_form != 0 || m->delta_form != 0;
+    }
     CK(launch_assemble_batch(ctx->batch_bk.p, ctx->batch_fd.p, ctx->batch_ag.p, ctx->batch_items.p, n_items,
-                             ctx->batch_counter.p, smem, ctx->sms, closure == FEA_CLOSURE_MLP, s));
+                             ctx->batch_counter.p, smem, ctx->sms, closure == FEA_CLOSURE_MLP, variants, s));
     if (ctx->profiling) {
         CK(cudaEventRecord(pr.e1, s));
         ctx->prof.push_back(pr);
@@ -1332,6 +1339,71 @@ fea_status fea_autotune(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure c
         cudaGraphExecDestroy(m->graph.exec);
         m->graph.exec = nullptr;
     }
+    return FEA_OK;
+}
+
+fea_status fea_autotune_batched(fea_ctx *ctx, const int32_t *meshes, int32_t n, fea_prec prec, fea_closure closure,
+                                fea_plan *best_out) {
+    if (!ctx || !meshes || n <= 0) return fail(ctx, FEA_EINVAL, "bad batch arguments");
+    fea_status st = check_args(ctx, prec, closure, FEA_TERM_ALL);
+    if (st) return st;
+    std::vector<Mesh *> ms((size_t)n);
+    for (int32_t k = 0; k < n; ++k) {
+        if ((st = get_mesh(ctx, meshes[k], &ms[(size_t)k]))) return st;
+        if (!ms[(size_t)k]->has_field) return fail(ctx, FEA_ESTATE, "no field uploaded for mesh %d", meshes[k]);
+    }
+    // candidates: the persistent batched launch over chunk tables of C
+    // elements (CHUNK), or per-mesh launches with one of the other scatters
+    std::vector<fea_plan> cands;
+    if (prec == FEA_MIXED)
+        for (int C : {128, 256, 512}) cands.push_back(fea_plan{FEA_SCATTER_CHUNK, 256, C, 0});
+    cands.push_back(fea_plan{FEA_SCATTER_ATOMIC, 256, 256, 0});
+    cands.push_back(fea_plan{FEA_SCATTER_WARP, 256, 256, 0});
+    if (closure != FEA_CLOSURE_MLP) cands.push_back(fea_plan{FEA_SCATTER_COLOUR, 128, 256, 0});
+    std::vector<double *> rhs((size_t)n);
+    for (int32_t k = 0; k < n; ++k) rhs[(size_t)k] = ms[(size_t)k]->rhs.p;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    fea_plan best{};
+    float best_ms = 1e30f;
+    for (const fea_plan &cand : cands) {
+        bool ok = true;
+        for (int32_t k = 0; k < n; ++k) {
+            fea_plan p = ms[(size_t)k]->plan;
+            p.scatter = cand.scatter;
+            p.threads_per_block = cand.threads_per_block;
+            if (cand.scatter == FEA_SCATTER_CHUNK) p.chunk_elems = cand.chunk_elems;
+            if (fea_set_plan(ctx, meshes[k], &p) != FEA_OK) ok = false;   // e.g. a chunk too large for shared memory
+        }
+        if (!ok) continue;
+        ctx->batch_per_mesh = cand.scatter != FEA_SCATTER_CHUNK;
+        for (int rep = 0; rep < 2; ++rep)
+            if ((st = fea_assemble_rhs_batched(ctx, meshes, n, prec, closure, FEA_TERM_ALL, rhs.data(), 0))) return st;
+        CK(cudaEventRecord(e0, 0));
+        for (int rep = 0; rep < 5; ++rep)
+            if ((st = fea_assemble_rhs_batched(ctx, meshes, n, prec, closure, FEA_TERM_ALL, rhs.data(), 0))) return st;
+        CK(cudaEventRecord(e1, 0));
+        CK(cudaEventSynchronize(e1));
+        float ms_ = 0;
+        CK(cudaEventElapsedTime(&ms_, e0, e1));
+        if (ms_ < best_ms) {
+            best_ms = ms_;
+            best = cand;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_ms >= 1e30f) return fail(ctx, FEA_EINVAL, "no batch candidate fits");
+    for (int32_t k = 0; k < n; ++k) {
+        fea_plan p = ms[(size_t)k]->plan;
+        p.scatter = best.scatter;
+        p.threads_per_block = best.threads_per_block;
+        if (best.scatter == FEA_SCATTER_CHUNK) p.chunk_elems = best.chunk_elems;
+        if ((st = fea_set_plan(ctx, meshes[k], &p))) return st;
+    }
+    ctx->batch_per_mesh = best.scatter != FEA_SCATTER_CHUNK;
+    if (best_out) *best_out = best;
     return FEA_OK;
 }
 

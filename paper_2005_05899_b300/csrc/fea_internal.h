@@ -111,6 +111,7 @@ constexpr size_t kChunkSmemLimit = 200 * 1024;
 // batched persistent launch over (category, chunk) items of many meshes
 cudaError_t launch_assemble_batch(const void *buckets, const void *fields, const void *args, const void *items,
                                   int64_t n_items, unsigned long long *counter, size_t smem, int sms, bool mlp,
+                                  bool variants,
                                   cudaStream_t s);
 size_t batch_item_bytes();
 cudaError_t launch_zero_batch(double *const *rhs_dev, const int64_t *len_dev, int n_meshes, cudaStream_t s);

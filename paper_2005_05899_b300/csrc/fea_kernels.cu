@@ -253,7 +253,7 @@ __device__ __forceinline__ JR prism_or_generic_jacobian(const JR X[][3], const P
 
 // Returns the number of Gauss points whose nu_t fell back from the MLP to
 // Vreman (outside the training envelope); 0 without the MLP.
-template <int ET, typename R, bool J64, bool MLP = false>
+template <int ET, typename R, bool J64, bool MLP = false, bool VAR = true>
 __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, const AsmArgs &args, R r[][3],
                                 float *nut_out, bool &bad, const MlpUse &mu = MlpUse{nullptr, nullptr}) {
     using JR = typename std::conditional<J64, double, R>::type;
@@ -261,8 +261,9 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
     const uint32_t mask = args.mask;
     const bool want_q = !MLP && args.closure == FEA_CLOSURE_VREMAN && ((mask & FEA_TERM_SGS) || nut_out);
     // model variants: EMAC needs |u_a|^2 at the nodes, anisotropic Vreman the extents
-    const bool emac = f.conv_form == 1 && (mask & FEA_TERM_CONV);
-    const bool aniso = f.delta_form == 1;
+    // VAR = false: the default forms only (no variant code, fewer registers)
+    const bool emac = VAR && f.conv_form == 1 && (mask & FEA_TERM_CONV);
+    const bool aniso = VAR && f.delta_form == 1;
     R q2[kMaxNen];
     if (emac) {
 #pragma unroll
@@ -467,7 +468,7 @@ __device__ __forceinline__ JR prism_or_generic_jacobian(const JR X[][3], const P
 // TET04: affine map, constant gradients; the 4-point rule is exact for the
 // degree-2 integrands, so the Gauss sums take their closed forms:
 //   sum_g W N_a N_b = V (1 + delta_ab) / 20,  sum_g W N_a = V / 4.
-template <typename R, bool J64, bool MLP = false>
+template <typename R, bool J64, bool MLP = false, bool VAR = true>
 __device__ int tet_residual(const Gathered<R, J64> &el, const FieldDev &f, const AsmArgs &args, R r[][3],
                             float *nut_out, bool &bad, const MlpUse &mu = MlpUse{nullptr, nullptr}) {
     using JR = typename std::conditional<J64, double, R>::type;
@@ -529,7 +530,7 @@ __device__ int tet_residual(const Gathered<R, J64> &el, const FieldDev &f, const
             nut = R(ntile[lane]);
         } else {
             const R delta = cbrt_r(V);
-            if (f.delta_form == 1) {
+            if (VAR && f.delta_form == 1) {
                 R dmx[3];
                 element_extents<4, R>(el.X, dmx);
                 nut = vreman_aniso(G, dmx, R(f.c_vreman));
@@ -540,7 +541,7 @@ __device__ int tet_residual(const Gathered<R, J64> &el, const FieldDev &f, const
         }
         __syncwarp();
     } else if (args.closure == FEA_CLOSURE_VREMAN && ((mask & FEA_TERM_SGS) || nut_out)) {
-        if (f.delta_form == 1) {
+        if (VAR && f.delta_form == 1) {
             R dmx[3];
             element_extents<4, R>(el.X, dmx);
             nut = vreman_aniso(G, dmx, R(f.c_vreman));
@@ -568,7 +569,7 @@ __device__ int tet_residual(const Gathered<R, J64> &el, const FieldDev &f, const
     const R v20 = V * R(0.05), v4 = V * R(0.25);
     // EMAC: + G^T u (same closed form as G u) and -1/2 grad (|u|^2)_h, constant
     // on the element, whose integral against N_a is V/4
-    const bool emac = f.conv_form == 1 && (mask & FEA_TERM_CONV);
+    const bool emac = VAR && f.conv_form == 1 && (mask & FEA_TERM_CONV);
     R kq[3] = {R(0), R(0), R(0)};
     if (emac) {
 #pragma unroll
@@ -827,7 +828,7 @@ __device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
     s = t;
 }
 
-template <int ET, bool J64, bool COMP, bool MLP = false>
+template <int ET, bool J64, bool COMP, bool MLP = false, bool VAR = true>
 __device__ __forceinline__ void chunk_body(const BucketDev &b, const FieldDev &f, const AsmArgs &args, int64_t k,
                                            float4 *smem4, const MlpUse &mu = MlpUse{nullptr, nullptr}) {
     constexpr int nen = kNen[ET], ng = kNg[ET];
@@ -895,9 +896,9 @@ __device__ __forceinline__ void chunk_body(const BucketDev &b, const FieldDev &f
         float *nut = args.nut ? (active ? args.nut + (int64_t)__ldg(&b.orig[e]) * ng : nut_tmp) : nullptr;
         int fb;
         if constexpr (ET == FEA_TET04)
-            fb = tet_residual<float, J64, MLP>(g, f, args, r, nut, bad, mu);
+            fb = tet_residual<float, J64, MLP, VAR>(g, f, args, r, nut, bad, mu);
         else
-            fb = element_residual<ET, float, J64, MLP>(g, f, args, r, nut, bad, mu);
+            fb = element_residual<ET, float, J64, MLP, VAR>(g, f, args, r, nut, bad, mu);
         if (active) fallbacks += fb;
         if (!active) continue;
 #pragma unroll
@@ -951,7 +952,7 @@ __device__ __forceinline__ void chunk_body(const BucketDev &b, const FieldDev &f
 // CTA then takes the register share of one TET04 CTA, so that these kernels
 // find room beside the persistent TET04 kernel (the side stream overlaps
 // them); the few spills cost less than the overlap gains.
-template <int ET, bool J64, bool COMP, bool MLP = false>
+template <int ET, bool J64, bool COMP, bool MLP = false, bool VAR = true>
 __global__ void __launch_bounds__(256, (J64 && !MLP ? 2 : 1)) k_assemble_chunk(BucketDev b, FieldDev f, AsmArgs args) {
     extern __shared__ float4 smem4[];
     MlpUse mu{nullptr, nullptr};
@@ -963,7 +964,7 @@ __global__ void __launch_bounds__(256, (J64 && !MLP ? 2 : 1)) k_assemble_chunk(B
         mu.w = w;
         mu.scratch = tail + sizeof(MlpFast) + (threadIdx.x >> 5) * mlp_warp_scratch_bytes(mlp_rows_per_elem(ET));
     }
-    chunk_body<ET, J64, COMP, MLP>(b, f, args, blockIdx.x, smem4, mu);
+    chunk_body<ET, J64, COMP, MLP, VAR>(b, f, args, blockIdx.x, smem4, mu);
 }
 
 // ---------------------------------------------------------------------------
@@ -977,7 +978,7 @@ struct BatchItem {
     int32_t chunk;    // chunk index within the bucket
 };
 
-template <bool MLP>
+template <bool MLP, bool VAR = true>
 __global__ void __launch_bounds__(256, 2) k_assemble_batch(const BucketDev *__restrict__ bk,
                                                         const FieldDev *__restrict__ fd,
                                                         const AsmArgs *__restrict__ ag,
@@ -1005,11 +1006,11 @@ __global__ void __launch_bounds__(256, 2) k_assemble_batch(const BucketDev *__re
         const FieldDev f = fd[it.bucket];
         const AsmArgs a = ag[it.bucket];
         switch (b.etype * 2 + b.fp64j) {
-            case 0: chunk_body<FEA_TET04, false, false, MLP>(b, f, a, it.chunk, smem4, mu); break;
-            case 2: chunk_body<FEA_PYR05, false, false, MLP>(b, f, a, it.chunk, smem4, mu); break;
-            case 4: chunk_body<FEA_PEN06, false, false, MLP>(b, f, a, it.chunk, smem4, mu); break;
-            case 5: chunk_body<FEA_PEN06, true, false, MLP>(b, f, a, it.chunk, smem4, mu); break;
-            case 6: chunk_body<FEA_HEX08, false, false, MLP>(b, f, a, it.chunk, smem4, mu); break;
+            case 0: chunk_body<FEA_TET04, false, false, MLP, VAR>(b, f, a, it.chunk, smem4, mu); break;
+            case 2: chunk_body<FEA_PYR05, false, false, MLP, VAR>(b, f, a, it.chunk, smem4, mu); break;
+            case 4: chunk_body<FEA_PEN06, false, false, MLP, VAR>(b, f, a, it.chunk, smem4, mu); break;
+            case 5: chunk_body<FEA_PEN06, true, false, MLP, VAR>(b, f, a, it.chunk, smem4, mu); break;
+            case 6: chunk_body<FEA_HEX08, false, false, MLP, VAR>(b, f, a, it.chunk, smem4, mu); break;
             default: break;   // FP64-Jacobian TET04/PYR05/HEX08: not batched (host falls back)
         }
         __syncthreads();   // shared memory is reused by the next item
@@ -1018,12 +1019,12 @@ __global__ void __launch_bounds__(256, 2) k_assemble_batch(const BucketDev *__re
 
 cudaError_t launch_assemble_batch(const void *buckets, const void *fields, const void *args, const void *items,
                                   int64_t n_items, unsigned long long *counter, size_t smem, int sms, bool mlp,
-                                  cudaStream_t s) {
+                                  bool variants, cudaStream_t s) {
     if (n_items == 0) return cudaSuccess;
     const size_t chunk_bytes = smem;
     if (mlp) smem += mlp_smem_bytes(256, kMaxNg);
     if (smem > kMaxBlockSmem) return cudaErrorInvalidConfiguration;
-    auto kern = mlp ? k_assemble_batch<true> : k_assemble_batch<false>;
+    auto kern = mlp ? k_assemble_batch<true> : (variants ? k_assemble_batch<false, true> : k_assemble_batch<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -1325,7 +1326,9 @@ static cudaError_t launch_chunk_v(const BucketDev &b, const FieldDev &f, const A
     const bool mlp = a.closure == FEA_CLOSURE_MLP;
     const size_t smem = chunk_smem_bytes(b) + (mlp ? mlp_smem_bytes(threads, mlp_rows_per_elem(ET)) : 0);
     if (smem > kMaxBlockSmem) return cudaErrorInvalidConfiguration;
-    auto kern = mlp ? k_assemble_chunk<ET, J64, COMP, true> : k_assemble_chunk<ET, J64, COMP, false>;
+    const bool var = f.conv_form != 0 || f.delta_form != 0;
+    auto kern = mlp ? k_assemble_chunk<ET, J64, COMP, true>
+                    : (var ? k_assemble_chunk<ET, J64, COMP, false, true> : k_assemble_chunk<ET, J64, COMP, false, false>);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -34,7 +34,7 @@ EXPORTED = (
     "fea_mlp_load", "fea_mlp_get", "fea_mlp_forward", "fea_mlp_train_step", "fea_mlp_set_envelope",
     "fea_mlp_fallback_read", "fea_sfc_order", "fea_partition_sfc", "fea_interface_pack", "fea_interface_unpack",
     "fea_poisson_setup", "fea_poisson_solve", "fea_divergence", "fea_gradient", "fea_project",
-    "fea_balance_update", "fea_set_model", "fea_wall_setup", "fea_wall_assemble",
+    "fea_balance_update", "fea_set_model", "fea_wall_setup", "fea_wall_assemble", "fea_autotune_batched",
 )
 MLP_NPARAM = 8833
 NOALLOC_MAX_NODES = 262144
@@ -193,6 +193,8 @@ def lib() -> ctypes.CDLL:
         L.fea_set_model.argtypes = [vp, i32, i32, i32]
         L.fea_wall_setup.argtypes = [vp, i32, ctypes.POINTER(WallDesc)]
         L.fea_wall_assemble.argtypes = [vp, i32, vp, vp]
+        L.fea_autotune_batched.argtypes = [vp, ctypes.POINTER(i32), i32, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(Plan)]
         L.fea_interface_pack.argtypes = [vp, vp, i64, vp, vp, i64, vp, i64, vp]
         L.fea_interface_unpack.argtypes = [vp, vp, i64, vp, vp, i64, vp, i64, vp]
         L.fea_mlp_fallback_read.argtypes = [vp, ctypes.POINTER(i64), ctypes.c_int]
@@ -346,6 +348,16 @@ class Context:
         ptrs = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
         self.check(self._lib.fea_assemble_rhs_batched(self.handle, ids, n, PREC[prec], CLOSURE[closure], mask,
                                                       ptrs, _stream(stream)))
+
+
+    def autotune_batched(self, meshes: Sequence["DeviceMesh"], prec="mixed", closure="vreman") -> Plan:
+        """Chooses between the persistent batched launch (chunk size) and
+        per-mesh launches (atomic / warp / colour) for assemble_batched."""
+        n = len(meshes)
+        ids = (ctypes.c_int32 * n)(*[m.id for m in meshes])
+        p = Plan()
+        self.check(self._lib.fea_autotune_batched(self.handle, ids, n, PREC[prec], CLOSURE[closure], ctypes.byref(p)))
+        return p
 
 
 class DeviceMesh:

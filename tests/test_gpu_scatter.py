@@ -105,3 +105,27 @@ def test_noalloc_stage_under_a_colour_plan(ctx, mixed_small):
     mass = O.periodic_fold(m.periodic_master, O.lumped_mass(om))
     ref = O.rk_stage(om, m.periodic_master, m.dirichlet, mass, f.u, f.u, f.p, f.nu, f.c_vreman, "vreman", 0, 2e-3)
     assert np.abs(out.cpu().numpy().T - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_batch_autotuner_picks_a_valid_mode(ctx):
+    """fea_autotune_batched times the persistent launch (three chunk sizes)
+    against per-mesh atomic / warp / colour launches; whatever it keeps, the
+    batched assembly still matches the oracle."""
+    batch = mg.batch_meshes(count=5, seed=9, e_min=2e3, e_max=2e4)
+    dms, outs = [], []
+    for m, f in batch:
+        dm = ctx.upload_mesh(m)
+        dm.upload_field(f.u, f.p, f.nu, f.c_vreman)
+        dms.append(dm)
+        outs.append(torch.full((3, dm.n_nodes), 7.0, dtype=torch.float64, device="cuda"))
+    best = ctx.autotune_batched(dms, prec="mixed", closure="vreman")
+    assert best.scatter in (1, 2, 3, 4)
+    if best.scatter == 2:
+        assert best.chunk_elems in (128, 256, 512)
+    for dm in dms:
+        assert dm.get_plan().scatter == best.scatter
+    ctx.assemble_batched(dms, outs, prec="mixed", closure="vreman")
+    ctx.sync_status()
+    for (m, f), o in zip(batch, outs):
+        l2, mx = errors(o.cpu().numpy().T, oracle_rhs(m, f))
+        assert l2 < MIXED_L2 and mx < MIXED_MAX, (best.as_dict(), l2, mx)
