@@ -23,7 +23,54 @@ namespace fea {
 
 __constant__ RefTables c_ref;
 
-cudaError_t upload_ref_tables(const RefTables &t) { return cudaMemcpyToSymbol(c_ref, &t, sizeof(RefTables)); }
+// The same tables rounded to FP32 for the FP32 element arithmetic: reading
+// the FP64 table and converting at every use put a conversion per shape
+// function value on the FP64 pipe (1/64 of the FP32 rate on this part).
+struct RefTables32 {
+    float xi[4][kMaxNg][3];
+    float N[4][kMaxNg][kMaxNen];
+    float dN[4][kMaxNg][kMaxNen][3];
+    float w[4][kMaxNg];
+};
+__constant__ RefTables32 c_ref32;
+
+cudaError_t upload_ref_tables(const RefTables &t) {
+    RefTables32 t32;
+    for (int e = 0; e < 4; ++e)
+        for (int g = 0; g < kMaxNg; ++g) {
+            t32.w[e][g] = (float)t.w[e][g];
+            for (int k = 0; k < 3; ++k) t32.xi[e][g][k] = (float)t.xi[e][g][k];
+            for (int a = 0; a < kMaxNen; ++a) {
+                t32.N[e][g][a] = (float)t.N[e][g][a];
+                for (int k = 0; k < 3; ++k) t32.dN[e][g][a][k] = (float)t.dN[e][g][a][k];
+            }
+        }
+    cudaError_t e = cudaMemcpyToSymbol(c_ref, &t, sizeof(RefTables));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(c_ref32, &t32, sizeof(RefTables32));
+}
+
+// reference-table entries in the arithmetic type R (the FP32 copy for float)
+template <typename R>
+__device__ __forceinline__ R ref_N(int et, int g, int a) {
+    if constexpr (sizeof(R) == 4) return c_ref32.N[et][g][a];
+    else return c_ref.N[et][g][a];
+}
+template <typename R>
+__device__ __forceinline__ R ref_dN(int et, int g, int a, int k) {
+    if constexpr (sizeof(R) == 4) return c_ref32.dN[et][g][a][k];
+    else return c_ref.dN[et][g][a][k];
+}
+template <typename R>
+__device__ __forceinline__ R ref_w(int et, int g) {
+    if constexpr (sizeof(R) == 4) return c_ref32.w[et][g];
+    else return c_ref.w[et][g];
+}
+template <typename R>
+__device__ __forceinline__ R ref_xi(int et, int g, int k) {
+    if constexpr (sizeof(R) == 4) return c_ref32.xi[et][g][k];
+    else return c_ref.xi[et][g][k];
+}
 
 template <typename R>
 struct Mat3 {
@@ -183,7 +230,7 @@ __device__ __forceinline__ JR jacobian_at(const JR X[][3], int g, JR J[3][3]) {
     for (int a = 0; a < nen; ++a)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            const JR d = JR(c_ref.dN[ET][g][a][j]);
+            const JR d = ref_dN<JR>(ET, g, a, j);
 #pragma unroll
             for (int i = 0; i < 3; ++i) J[i][j] += X[a][i] * d;
         }
@@ -298,7 +345,7 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
         JR A[3][3];
         const JR detj = adjugate(J, A);
         if (!(detj > JR(0))) bad = true;
-        const JR wdet = JR(c_ref.w[ET][g]) * detj;
+        const JR wdet = ref_w<JR>(ET, g) * detj;
         V += wdet;
         const R rdet = R(1) / R(detj);
         R Ji[3][3];
@@ -311,10 +358,10 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
         R Gx[3][3] = {}, px[3] = {}, ug[3] = {};
 #pragma unroll
         for (int a = 0; a < nen; ++a) {
-            const R Na = R(c_ref.N[ET][g][a]);
+            const R Na = ref_N<R>(ET, g, a);
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const R d = R(c_ref.dN[ET][g][a][k]);
+                const R d = ref_dN<R>(ET, g, a, k);
                 px[k] += el.P[a] * d;
 #pragma unroll
                 for (int i = 0; i < 3; ++i) Gx[i][k] += el.U[a][i] * d;
@@ -362,7 +409,7 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
 #pragma unroll
             for (int a = 0; a < nen; ++a)
 #pragma unroll
-                for (int j = 0; j < 3; ++j) kr[j] += q2[a] * R(c_ref.dN[ET][g][a][j]);
+                for (int j = 0; j < 3; ++j) kr[j] += q2[a] * ref_dN<R>(ET, g, a, j);
 #pragma unroll
             for (int j = 0; j < 3; ++j) kx[j] = kr[0] * Ji[0][j] + kr[1] * Ji[1][j] + kr[2] * Ji[2][j];
         }
@@ -390,8 +437,8 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
         }
 #pragma unroll
         for (int a = 0; a < nen; ++a) {
-            const R Na = R(c_ref.N[ET][g][a]);
-            const R d0 = R(c_ref.dN[ET][g][a][0]), d1 = R(c_ref.dN[ET][g][a][1]), d2 = R(c_ref.dN[ET][g][a][2]);
+            const R Na = ref_N<R>(ET, g, a);
+            const R d0 = ref_dN<R>(ET, g, a, 0), d1 = ref_dN<R>(ET, g, a, 1), d2 = ref_dN<R>(ET, g, a, 2);
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 const R t = S[i][0] * d0 + S[i][1] * d1 + S[i][2] * d2;
@@ -428,8 +475,7 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
                     for (int k = 0; k < 3; ++k) Sg[i][k] = R(Stile[(g * 9 + 3 * i + k) * 32 + lane]);
 #pragma unroll
                 for (int a = 0; a < nen; ++a) {
-                    const R d0 = R(c_ref.dN[ET][g][a][0]), d1 = R(c_ref.dN[ET][g][a][1]),
-                            d2 = R(c_ref.dN[ET][g][a][2]);
+                    const R d0 = ref_dN<R>(ET, g, a, 0), d1 = ref_dN<R>(ET, g, a, 1), d2 = ref_dN<R>(ET, g, a, 2);
 #pragma unroll
                     for (int i = 0; i < 3; ++i) r[a][i] -= nt * (Sg[i][0] * d0 + Sg[i][1] * d1 + Sg[i][2] * d2);
                 }
@@ -452,7 +498,7 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
 template <int ET, typename R, typename JR>
 __device__ __forceinline__ JR prism_or_generic_jacobian(const JR X[][3], const PrismGeom<JR> &pg, int g, JR J[3][3]) {
     if constexpr (ET == FEA_PEN06) {
-        const JR pr = JR(c_ref.xi[ET][g][0]), ps = JR(c_ref.xi[ET][g][1]), pz = JR(c_ref.xi[ET][g][2]);
+        const JR pr = ref_xi<JR>(ET, g, 0), ps = ref_xi<JR>(ET, g, 1), pz = ref_xi<JR>(ET, g, 2);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             J[i][0] = pg.Ar[i] + pz * pg.Br[i];
