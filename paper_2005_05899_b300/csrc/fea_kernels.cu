@@ -50,6 +50,31 @@ cudaError_t upload_ref_tables(const RefTables &t) {
     return cudaMemcpyToSymbol(c_ref32, &t32, sizeof(RefTables32));
 }
 
+// FP64 -> FP32, round to nearest even, by integer operations for results in
+// the normal FP32 range (B300's FP64 pipe runs at 1/64 of the FP32 rate and
+// the stage update is otherwise bound by it); zero, subnormal, overflowing,
+// infinite and NaN inputs take the hardware conversion.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    if (e < 897u || e > 1150u) return __double2float_rn(x);
+    const unsigned long long m = b & 0x000FFFFFFFFFFFFFull;
+    const unsigned long long rem = m & 0x1FFFFFFFull;   // the 29 bits dropped
+    unsigned r = (unsigned)(m >> 29);
+    r += (rem > 0x10000000ull || (rem == 0x10000000ull && (r & 1u))) ? 1u : 0u;
+    // a carry out of the 23-bit fraction moves into the exponent, as it must
+    return __uint_as_float(((hi & 0x80000000u) | ((e - 896u) << 23)) + r);
+}
+
+// an FP64 value in the arithmetic type R: FP64 -> FP32 by the integer
+// rounding above (a hardware conversion is an FP64-pipe instruction)
+template <typename R, typename JR>
+__device__ __forceinline__ R to_r(JR x) {
+    if constexpr (sizeof(R) == 4 && sizeof(JR) == 8) return f64_to_f32_rn(x);
+    else return R(x);
+}
+
 // reference-table entries in the arithmetic type R (the FP32 copy for float)
 template <typename R>
 __device__ __forceinline__ R ref_N(int et, int g, int a) {
@@ -347,13 +372,13 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
         if (!(detj > JR(0))) bad = true;
         const JR wdet = ref_w<JR>(ET, g) * detj;
         V += wdet;
-        const R rdet = R(1) / R(detj);
+        const R rdet = R(1) / to_r<R>(detj);
         R Ji[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int j = 0; j < 3; ++j) Ji[i][j] = R(A[i][j]) * rdet;
-        const R W = R(wdet);
+            for (int j = 0; j < 3; ++j) Ji[i][j] = to_r<R>(A[i][j]) * rdet;
+        const R W = to_r<R>(wdet);
         // reference-coordinate gradients and the Gauss-point velocity
         R Gx[3][3] = {}, px[3] = {}, ug[3] = {};
 #pragma unroll
@@ -450,7 +475,7 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
     int fallbacks = 0;
     if constexpr (MLP) {
         // Delta = V^(1/3) completes every row (column 5)
-        const R delta = cbrt_r(R(V));
+        const R delta = cbrt_r(to_r<R>(V));
         const R d2 = delta * delta;
         bool delta_inside;
         const uint16_t db = mlp_delta_bits(float(delta), *mu.w, &delta_inside);
@@ -483,7 +508,7 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
         }
         __syncwarp();   // the scratch is rewritten for the warp's next elements
     } else {
-        const R delta = cbrt_r(R(V));
+        const R delta = cbrt_r(to_r<R>(V));
         const R d2 = aniso ? R(1) : delta * delta;
 #pragma unroll
         for (int a = 0; a < nen; ++a)
@@ -1497,22 +1522,6 @@ cudaError_t launch_fold(const int32_t *slaves, const int32_t *masters, int64_t n
 // RK stage update (streaming): u^(k+1) = a u^n + b (u^(k) + dt R / M), Dirichlet
 // nodes keep u^n; also refreshes the FP32 packed copy (u, v, w, p).
 
-// FP64 -> FP32, round to nearest even, by integer operations for results in
-// the normal FP32 range (B300's FP64 pipe runs at 1/64 of the FP32 rate and
-// the stage update is otherwise bound by it); zero, subnormal, overflowing,
-// infinite and NaN inputs take the hardware conversion.
-__device__ __forceinline__ float f64_to_f32_rn(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned hi = (unsigned)(b >> 32);
-    const unsigned e = (hi >> 20) & 0x7ffu;
-    if (e < 897u || e > 1150u) return __double2float_rn(x);
-    const unsigned long long m = b & 0x000FFFFFFFFFFFFFull;
-    const unsigned long long rem = m & 0x1FFFFFFFull;   // the 29 bits dropped
-    unsigned r = (unsigned)(m >> 29);
-    r += (rem > 0x10000000ull || (rem == 0x10000000ull && (r & 1u))) ? 1u : 0u;
-    // a carry out of the 23-bit fraction moves into the exponent, as it must
-    return __uint_as_float(((hi & 0x80000000u) | ((e - 896u) << 23)) + r);
-}
 
 // u^(k+1) = a u^n + b (u^(k) + dt M^-1 R) = a u^n + b u^(k) + c R, c = b dt / M;
 // A0: a = 0 (first stage) reads no u^n except at held nodes.  One node per
