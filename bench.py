@@ -109,12 +109,16 @@ def ncu_traffic(kernel_key: str, plan: dict):
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    rec = d.get(kernel_key)
-    if not rec or rec.get("source_hash") != kernel_source_hash():
-        return None
-    if any(rec.get("plan", {}).get(k) != plan.get(k) for k in ("scatter", "threads_per_block", "chunk_elems")):
-        return None
-    return float(rec["dram_bytes_per_launch"])
+    recs = d.get(kernel_key) or []
+    if isinstance(recs, dict):
+        recs = [recs]
+    for rec in recs:   # one record per launch plan measured
+        if rec.get("source_hash") != kernel_source_hash():
+            continue
+        if any(rec.get("plan", {}).get(k) != plan.get(k) for k in ("scatter", "threads_per_block", "chunk_elems")):
+            continue
+        return float(rec["dram_bytes_per_launch"])
+    return None
 
 
 class ClockSampler:
