@@ -475,7 +475,11 @@ fea_status fea_get_plan(fea_ctx *ctx, int32_t mesh, fea_plan *plan);
 fea_status fea_set_plan(fea_ctx *ctx, int32_t mesh, const fea_plan *plan);
 
 /* Times the candidate plans of one mesh (after a field upload) with CUDA
- * events and keeps the fastest.  With cache_path != NULL, a text file of
+ * events and keeps the fastest: ATOMIC, WARP and COLOUR (not with the MLP
+ * closure) at 128 and 256 threads and, under FEA_MIXED, CHUNK plans of 256,
+ * 512 and 1024 elements; a CHUNK plan within 5 % of the fastest is kept
+ * instead (its chunk-relative FP32 coordinates are the more accurate
+ * mixed-precision path).  With cache_path != NULL, a text file of
  * lines "key scatter threads chunk_elems chunk_acc ms" keyed by device name,
  * node and element counts, precision and closure: a matching line (the last
  * one) is applied through fea_set_plan instead of timing; otherwise the

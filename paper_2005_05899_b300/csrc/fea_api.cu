@@ -1282,8 +1282,8 @@ fea_status fea_autotune(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure c
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    fea_plan best = m->plan;
-    float best_ms = 1e30f;
+    fea_plan best = m->plan, best_chunk{};
+    float best_ms = 1e30f, best_chunk_ms = 1e30f;
     std::vector<fea_plan> cands;
     for (int t : {128, 256}) cands.push_back(fea_plan{FEA_SCATTER_ATOMIC, t, m->plan.chunk_elems, 0});
     for (int t : {128, 256}) cands.push_back(fea_plan{FEA_SCATTER_WARP, t, m->plan.chunk_elems, 0});
@@ -1323,6 +1323,17 @@ fea_status fea_autotune(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure c
             best_ms = ms;
             best = cand;
         }
+        if (cand.scatter == FEA_SCATTER_CHUNK && ms < best_chunk_ms) {
+            best_chunk_ms = ms;
+            best_chunk = cand;
+        }
+    }
+    // near-ties go to the chunk scatter: its chunk-relative FP32 coordinates
+    // keep edge vectors at full FP32 precision (about 3x smaller mixed-
+    // precision error than the global FP32 coordinates of the other paths)
+    if (best.scatter != FEA_SCATTER_CHUNK && best_chunk_ms <= 1.05f * best_ms) {
+        best = best_chunk;
+        best_ms = best_chunk_ms;
     }
     if (best.scatter == FEA_SCATTER_CHUNK && (st = ensure_chunks(ctx, *m, best.chunk_elems))) return st;
     cudaEventDestroy(e0);
