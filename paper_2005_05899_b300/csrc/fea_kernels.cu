@@ -67,6 +67,25 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
     return __uint_as_float(((hi & 0x80000000u) | ((e - 896u) << 23)) + r);
 }
 
+// FP32 -> FP64 (exact) by integer operations for normal numbers: the
+// hardware conversion is an FP64-pipe instruction (1/64 of the FP32 rate on
+// this part), one per scattered component otherwise; zero, subnormals,
+// infinities and NaN take the hardware conversion.
+__device__ __forceinline__ double f32_to_f64_exact(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)x;
+    const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+// an R value as FP64 for the nodal sums
+template <typename R>
+__device__ __forceinline__ double to_f64(R x) {
+    if constexpr (sizeof(R) == 4) return f32_to_f64_exact(x);
+    else return x;
+}
+
 // an FP64 value in the arithmetic type R: FP64 -> FP32 by the integer
 // rounding above (a hardware conversion is an FP64-pipe instruction)
 template <typename R, typename JR>
@@ -343,8 +362,8 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
     }
     R dm[3] = {R(0), R(0), R(0)};
     if (aniso) element_extents<nen, R>(el.X, dm);
-    const R nu = (mask & FEA_TERM_VISC) ? R(f.nu) : R(0);
-    const R cv = R(f.c_vreman);
+    const R nu = (mask & FEA_TERM_VISC) ? to_r<R>(f.nu) : R(0);
+    const R cv = to_r<R>(f.c_vreman);
     R rs[kMaxNen][3];
 #pragma unroll
     for (int a = 0; a < nen; ++a)
@@ -604,9 +623,9 @@ __device__ int tet_residual(const Gathered<R, J64> &el, const FieldDev &f, const
             if (VAR && f.delta_form == 1) {
                 R dmx[3];
                 element_extents<4, R>(el.X, dmx);
-                nut = vreman_aniso(G, dmx, R(f.c_vreman));
+                nut = vreman_aniso(G, dmx, to_r<R>(f.c_vreman));
             } else {
-                nut = vreman(G, delta * delta, R(f.c_vreman));
+                nut = vreman(G, delta * delta, to_r<R>(f.c_vreman));
             }
             fallbacks = 4;   // all four Gauss points
         }
@@ -615,10 +634,10 @@ __device__ int tet_residual(const Gathered<R, J64> &el, const FieldDev &f, const
         if (VAR && f.delta_form == 1) {
             R dmx[3];
             element_extents<4, R>(el.X, dmx);
-            nut = vreman_aniso(G, dmx, R(f.c_vreman));
+            nut = vreman_aniso(G, dmx, to_r<R>(f.c_vreman));
         } else {
             const R delta = cbrt_r(V);
-            nut = vreman(G, delta * delta, R(f.c_vreman));
+            nut = vreman(G, delta * delta, to_r<R>(f.c_vreman));
         }
     }
     if (nut_out) {
@@ -627,7 +646,7 @@ __device__ int tet_residual(const Gathered<R, J64> &el, const FieldDev &f, const
     }
     const R trG = G[0][0] + G[1][1] + G[2][2];
     R visc = R(0);
-    if (mask & FEA_TERM_VISC) visc += R(f.nu);
+    if (mask & FEA_TERM_VISC) visc += to_r<R>(f.nu);
     if (mask & FEA_TERM_SGS) visc += nut;
     const R s2 = R(2) * visc * V;
     R sig[3][3];
@@ -752,7 +771,7 @@ __global__ void __launch_bounds__(256) k_assemble_atomic(BucketDev b, FieldDev f
 #pragma unroll
         for (int a = 0; a < nen; ++a) {
             const unsigned peers = __match_any_sync(act, idx[a]);
-            double v0 = double(r[a][0]), v1 = double(r[a][1]), v2 = double(r[a][2]);
+            double v0 = to_f64(r[a][0]), v1 = to_f64(r[a][1]), v2 = to_f64(r[a][2]);
             peer_sum3(act, peers, v0, v1, v2);
             if (lane == __ffs(peers) - 1) {
                 atomicAdd(&args.rhs[idx[a]], v0);
@@ -764,7 +783,7 @@ __global__ void __launch_bounds__(256) k_assemble_atomic(BucketDev b, FieldDev f
 #pragma unroll
         for (int a = 0; a < nen; ++a)
 #pragma unroll
-            for (int i = 0; i < 3; ++i) atomicAdd(&args.rhs[(int64_t)i * f.n + idx[a]], double(r[a][i]));
+            for (int i = 0; i < 3; ++i) atomicAdd(&args.rhs[(int64_t)i * f.n + idx[a]], to_f64(r[a][i]));
     }
 }
 
@@ -797,7 +816,7 @@ __global__ void __launch_bounds__(256) k_assemble_colour(BucketDev b, FieldDev f
 #pragma unroll
     for (int a = 0; a < nen; ++a)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) args.rhs[(int64_t)i * f.n + idx[a]] += double(r[a][i]);
+        for (int i = 0; i < 3; ++i) args.rhs[(int64_t)i * f.n + idx[a]] += to_f64(r[a][i]);
 }
 
 template <int ET>
@@ -1000,11 +1019,11 @@ __device__ __forceinline__ void chunk_body(const BucketDev &b, const FieldDev &f
         }
         const int bits = __float_as_int(sX[j].w);
         const int64_t id = bits & 0x7fffffff;
-        double v0 = double(s0), v1 = double(s1), v2 = double(s2);
+        double v0 = f32_to_f64_exact(s0), v1 = f32_to_f64_exact(s1), v2 = f32_to_f64_exact(s2);
         if constexpr (COMP) {
-            v0 += double(c0);
-            v1 += double(c1);
-            v2 += double(c2);
+            v0 += f32_to_f64_exact(c0);
+            v1 += f32_to_f64_exact(c1);
+            v2 += f32_to_f64_exact(c2);
         }
         double *r0 = args.rhs + id, *r1 = args.rhs + f.n + id, *r2 = args.rhs + 2 * f.n + id;
         if (bits < 0) {
