@@ -1598,7 +1598,8 @@ cudaError_t launch_rk_update(int64_t n, const double *un, double *uk, double *un
 
 __global__ void k_pack_field(int64_t n, const double *u64, const double *p64, float4 *up32) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        up32[i] = make_float4(float(u64[i]), float(u64[n + i]), float(u64[2 * n + i]), float(p64[i]));
+        up32[i] = make_float4(f64_to_f32_rn(u64[i]), f64_to_f32_rn(u64[n + i]), f64_to_f32_rn(u64[2 * n + i]),
+                              f64_to_f32_rn(p64[i]));
 }
 
 cudaError_t launch_pack_field(int64_t n, const double *u64, const double *p64, float4 *up32, cudaStream_t s) {
