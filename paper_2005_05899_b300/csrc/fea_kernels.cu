@@ -382,12 +382,48 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
     float *qtile = ntile + ng * 32;
     uint32_t inside_mask = 0;   // bit g: point g inside the training envelope
     JR V = JR(0);
+    // PEN06: the rule's points are 3 triangle points at each of 2 levels zeta
+    // (level-major); the r- and s-columns of J and their cross product (the
+    // adjugate's last row) depend on zeta only, so they are formed once per
+    // level; per point only the zeta-column, two cross products and the
+    // determinant c2 . (c0 x c1) remain
+    JR c0[3], c1[3], a2[3];
 #pragma unroll 1
     for (int g = 0; g < ng; ++g) {
         JR J[3][3];
-        prism_or_generic_jacobian<ET, R, JR>(el.X, pg, g, J);
         JR A[3][3];
-        const JR detj = adjugate(J, A);
+        JR detj;
+        if constexpr (ET == FEA_PEN06) {
+            if (g % 3 == 0) {
+                const JR pz = ref_xi<JR>(ET, g, 2);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    c0[i] = pg.Ar[i] + pz * pg.Br[i];
+                    c1[i] = pg.As[i] + pz * pg.Bs[i];
+                }
+                a2[0] = c0[1] * c1[2] - c0[2] * c1[1];
+                a2[1] = c0[2] * c1[0] - c0[0] * c1[2];
+                a2[2] = c0[0] * c1[1] - c0[1] * c1[0];
+            }
+            const JR pr = ref_xi<JR>(ET, g, 0), ps = ref_xi<JR>(ET, g, 1);
+            JR c2[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) c2[i] = pg.C0[i] + pr * pg.Dr[i] + ps * pg.Ds[i];
+            // A row 0 = c1 x c2, row 1 = c2 x c0, row 2 = c0 x c1 (J^-1 = A / det)
+            A[0][0] = c1[1] * c2[2] - c1[2] * c2[1];
+            A[0][1] = c1[2] * c2[0] - c1[0] * c2[2];
+            A[0][2] = c1[0] * c2[1] - c1[1] * c2[0];
+            A[1][0] = c2[1] * c0[2] - c2[2] * c0[1];
+            A[1][1] = c2[2] * c0[0] - c2[0] * c0[2];
+            A[1][2] = c2[0] * c0[1] - c2[1] * c0[0];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) A[2][j] = a2[j];
+            detj = c2[0] * a2[0] + c2[1] * a2[1] + c2[2] * a2[2];
+            (void)J;
+        } else {
+            prism_or_generic_jacobian<ET, R, JR>(el.X, pg, g, J);
+            detj = adjugate(J, A);
+        }
         if (!(detj > JR(0))) bad = true;
         const JR wdet = ref_w<JR>(ET, g) * detj;
         V += wdet;
