@@ -299,6 +299,10 @@ def test_airplane_full_size_sampled_parity(ctx):
         l2, mx = sampled_parity(ctx, m, f, plan=plan)
         print(f"airplane 170^3 sampled mixed {plan}: rel-L2 {l2:.3e} max {mx:.3e}")
         assert l2 < MIXED_L2 and mx < MIXED_MAX, plan
+    # the FP64 path at full size, to the FP64 tolerance
+    l2, mx = sampled_parity(ctx, m, f, prec="fp64", seed=1)
+    print(f"airplane 170^3 sampled fp64: rel-L2 {l2:.3e} max {mx:.3e}")
+    assert l2 < FP64_TOL and mx < FP64_TOL
 
 
 # ---------------------------------------------------------------------------
