@@ -529,6 +529,31 @@ fea_status ensure_chunks(fea_ctx *ctx, Mesh &m, int C) {
     return FEA_OK;
 }
 
+// Whether the FP64-Jacobian PEN06 category runs as a programmatic dependent
+// of the persistent TET04 kernel on the caller's stream (it starts as that
+// kernel's CTAs retire and fills its tail) instead of on a side stream: a
+// mesh of exactly one TET04 category on the pipeline and one FP64-Jacobian
+// PEN06 category, mixed precision, chunk plan, default forms, no MLP, no
+// nu_t output.  Both orders overlap the two; only this one survives graph
+// capture (a graph's branches were launched one after the other).
+bool tail_order(const Mesh &m, fea_prec prec, fea_closure closure, fea_scatter scatter, bool want_nut) {
+    if (prec != FEA_MIXED || scatter != FEA_SCATTER_CHUNK || closure == FEA_CLOSURE_MLP || want_nut ||
+        m.conv_form != 0 || m.delta_form != 0 || m.plan.chunk_acc != 0)
+        return false;
+    int n_tet = 0, n_pen64 = 0, other = 0;
+    for (auto &bp : m.buckets) {
+        if (!bp->count) continue;
+        if (bp->fp64j && bp->etype == FEA_PEN06 && bp->lconn.p)
+            ++n_pen64;
+        else if (!bp->fp64j && bp->etype == FEA_TET04 && bp->lconn.p &&
+                 tet_pipe_smem_bytes(bp->dev()) <= kChunkSmemLimit)
+            ++n_tet;
+        else
+            ++other;
+    }
+    return n_tet == 1 && n_pen64 == 1 && other == 0;
+}
+
 fea_status assemble_into(fea_ctx *ctx, Mesh &m, fea_prec prec, fea_closure closure, uint32_t mask,
                          fea_scatter scatter, double *rhs, float *nut, cudaStream_t s) {
     CK(cudaMemsetAsync(rhs, 0, sizeof(double) * 3 * m.n, s));
@@ -542,15 +567,18 @@ fea_status assemble_into(fea_ctx *ctx, Mesh &m, fea_prec prec, fea_closure closu
         if (cs) return cs;
     }
     // FP64-Jacobian categories (FP64 pipe) go first, on a side stream, so
-    // that they overlap the FP32-bound categories on the caller's stream.
+    // that they overlap the FP32-bound categories on the caller's stream;
+    // or, in the tail order (tail_order; not while profiling per category),
+    // after the TET04 kernel on the same stream as its programmatic dependent.
+    const bool tail = !ctx->profiling && tail_order(m, prec, closure, scatter, nut != nullptr);
     bool forked = false;
     for (int pass = 0; pass < 2; ++pass) {
         for (auto &bp : m.buckets) {
             const Bucket &b = *bp;
             if (!b.count) continue;
-            const bool first = prec == FEA_MIXED && b.fp64j;
+            const bool first = tail ? !b.fp64j : (prec == FEA_MIXED && b.fp64j);
             if (first != (pass == 0)) continue;
-            const bool side = first && !colour;
+            const bool side = !tail && first && !colour;
             cudaStream_t ls = s;
             if (side) {
                 if (!forked) {
@@ -568,6 +596,7 @@ fea_status assemble_into(fea_ctx *ctx, Mesh &m, fea_prec prec, fea_closure closu
             a.err = ctx->d_err;
             a.mlp = closure == FEA_CLOSURE_MLP ? mlp_fast_ptr(ctx->mlp_w.p) : nullptr;
             a.mlp_fb = closure == FEA_CLOSURE_MLP ? ctx->mlp_fb.p : nullptr;
+            a.pdl = tail && b.fp64j;
             cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
             if (ctx->profiling) CK(cudaStreamIsCapturing(s, &cap));
             ProfRec pr{b.etype, b.fp64j, nullptr, nullptr};
@@ -689,14 +718,15 @@ fea_status stage_with_scratch(fea_ctx *ctx, int32_t mesh, int32_t stage, double 
     if (colour)
         for (auto &bp : m->buckets)
             if (bp->count && !bp->col_conn.p) return fail(ctx, FEA_ESTATE, "colour tables missing (set the plan)");
+    const bool tail = tail_order(*m, prec, closure, scatter, false);   // as in assemble_into
     bool forked = false;
     for (int pass = 0; pass < 2; ++pass) {
         for (auto &bp : m->buckets) {
             const Bucket &b = *bp;
             if (!b.count) continue;
-            const bool first = prec == FEA_MIXED && b.fp64j;
+            const bool first = tail ? !b.fp64j : (prec == FEA_MIXED && b.fp64j);
             if (first != (pass == 0)) continue;
-            const bool side = first && !colour;
+            const bool side = !tail && first && !colour;
             cudaStream_t ls = s;
             if (side) {
                 if (!forked) {
@@ -714,6 +744,7 @@ fea_status stage_with_scratch(fea_ctx *ctx, int32_t mesh, int32_t stage, double 
             a.err = ctx->d_err;
             a.mlp = closure == FEA_CLOSURE_MLP ? mlp_fast_ptr(ctx->mlp_w.p) : nullptr;
             a.mlp_fb = closure == FEA_CLOSURE_MLP ? ctx->mlp_fb.p : nullptr;
+            a.pdl = tail && b.fp64j;
             if (colour) {
                 CK(launch_assemble_colour(b.dev(), f, a, prec, m->plan.threads_per_block, b.col_off.data(),
                                           b.n_colours, ls));

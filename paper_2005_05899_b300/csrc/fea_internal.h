@@ -87,6 +87,10 @@ struct AsmArgs {
     unsigned *err;        // device error word
     const void *mlp;      // MLP closure weights (device MlpFast) when closure == FEA_CLOSURE_MLP
     unsigned long long *mlp_fb = nullptr;   // count of Gauss points that fell back to Vreman (MLP only)
+    // chunk kernels: launched as a programmatic dependent of the kernel before
+    // it on the stream (starts while that one drains; waits for it to
+    // complete before it ends itself)
+    int pdl = 0;
 };
 
 // launchers (fea_kernels.cu); all return cudaGetLastError() of the launch

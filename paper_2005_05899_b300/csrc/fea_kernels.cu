@@ -1094,6 +1094,10 @@ __global__ void __launch_bounds__(256, ((J64 || ET == FEA_HEX08 || ET == FEA_PYR
         mu.scratch = tail + sizeof(MlpFast) + (threadIdx.x >> 5) * mlp_warp_scratch_bytes(mlp_rows_per_elem(ET));
     }
     chunk_body<ET, J64, COMP, MLP, VAR>(b, f, args, blockIdx.x, smem4, mu);
+    // as a programmatic dependent: the grid it overlapped has completed (and
+    // its writes are visible) before this one does, so whatever the stream
+    // runs next sees both; a no-op for an ordinary launch
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -1462,8 +1466,21 @@ static cudaError_t launch_chunk_v(const BucketDev &b, const FieldDev &f, const A
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<(unsigned)b.n_chunks, threads, smem, s>>>(b, f, a);
-    return cudaGetLastError();
+    if (!a.pdl) {
+        kern<<<(unsigned)b.n_chunks, threads, smem, s>>>(b, f, a);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)b.n_chunks);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, b, f, a);
 }
 
 template <int ET>

@@ -344,6 +344,10 @@ __global__ void __launch_bounds__(T) k_tet_pipe(BucketDev b, FieldDev f, AsmArgs
     const uint4 *elem_g = reinterpret_cast<const uint4 *>(b.lconn);
     const int tid = threadIdx.x;
     const int64_t G = gridDim.x, c0 = blockIdx.x, nch = b.n_chunks;
+    // a kernel launched after this one as a programmatic dependent (the
+    // FP64-Jacobian PEN06 category) may start as soon as CTAs of this one
+    // retire: it fills the SMs of this kernel's tail
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (tid == 0) {
         for (int q = 0; q < 3; ++q) mbar_init(&mbar[q], 1);
         *abort_flag = 0;
