@@ -497,7 +497,9 @@ int64_t fea_launch_count(const fea_ctx *ctx);
 
 /* Kernel timing (profiling aid).  While enabled, every element-assembly
  * kernel launched outside a CUDA graph is bracketed by two CUDA events
- * recorded on its launch stream.  fea_profile_read synchronises those
+ * recorded on its launch stream, and the categories of an assembly run one
+ * after the other on the caller's stream (no overlap), so that each time is
+ * that kernel's alone.  fea_profile_read synchronises those
  * events and returns, for the category (etype, fp64_jac), the summed kernel
  * time in milliseconds and the number of launches; reset != 0 clears the
  * records.  Errors: FEA_EINVAL, FEA_ECUDA. */

@@ -578,7 +578,9 @@ fea_status assemble_into(fea_ctx *ctx, Mesh &m, fea_prec prec, fea_closure closu
             if (!b.count) continue;
             const bool first = tail ? !b.fp64j : (prec == FEA_MIXED && b.fp64j);
             if (first != (pass == 0)) continue;
-            const bool side = !tail && first && !colour;
+            // while profiling per category every kernel runs alone on the
+            // caller's stream, so its events time that kernel, not a share
+            const bool side = !tail && first && !colour && !ctx->profiling;
             cudaStream_t ls = s;
             if (side) {
                 if (!forked) {
