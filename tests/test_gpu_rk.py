@@ -131,3 +131,13 @@ def test_tail_order_mesh_graph_and_stages(ctx):
     upd = np.abs(ref - f.u).max()
     assert np.abs(g - st).max() <= 1e-6 * upd
     assert np.abs(g - ref).max() < 2e-4 * upd
+    # the allocation-free stage takes the same order
+    un = torch.tensor(np.ascontiguousarray(f.u.T), dtype=torch.float64, device="cuda")
+    p = torch.tensor(f.p, dtype=torch.float64, device="cuda")
+    o1 = torch.empty_like(un)
+    dm.rk_stage_noalloc(0, dt, un, un, p, o1, f.nu, f.c_vreman)
+    dm.upload_field(f.u, f.p, f.nu, f.c_vreman)
+    dm.rk_stage(0, dt)
+    ctx.sync_status()
+    s0 = state(dm)
+    assert np.abs(o1.cpu().numpy().T - s0).max() <= 1e-6 * upd
