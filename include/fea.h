@@ -401,6 +401,16 @@ fea_status fea_project(fea_ctx *ctx, int32_t mesh, double dt, double rtol, int32
  * Errors: FEA_EINVAL. */
 fea_status fea_sfc_order(int64_t n, const double *xyz, int32_t level, int64_t *order);
 
+/* Greedy element colouring, the one FEA_SCATTER_COLOUR uses (host only, no
+ * device): elements in the given order take the lowest colour that none of
+ * their nodes has seen yet, so no two elements of one colour share a node.
+ * conn: host [count][n_en] node ids in [0, n_nodes); colour: host [count]
+ * output; *n_colours: the number of colours used.  Errors: FEA_EINVAL,
+ * FEA_EMESH (a node id out of range), FEA_ENUMERIC (more than 256 colours
+ * would be needed). */
+fea_status fea_colour_elements(int64_t n_nodes, int32_t n_en, int64_t count, const int32_t *conn, int32_t *colour,
+                               int32_t *n_colours);
+
 /* SFC partition of a mesh's elements into nparts parts (section 5, the
  * partitioner's steps): element location = centroid, weight = Gauss points
  * of the element's rule (TET04 4, PYR05 8, PEN06 6, HEX08 8), bins of a

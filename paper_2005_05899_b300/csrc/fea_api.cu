@@ -461,34 +461,17 @@ fea_status build_chunks(fea_ctx *ctx, Mesh &m, Bucket &b, int C) {
     return FEA_OK;
 }
 
-// Greedy colouring of a category's elements in their (Morton) order: each
-// element takes the lowest colour that none of its nodes has seen yet, so no
-// two elements of a colour share a node.  Node colour sets are bit masks of
-// kColourWords x 64 colours.  The elements are then stored colour by colour
-// (Morton order kept within a colour).
-constexpr int kColourWords = 4;
-
+// Greedy colouring of a category's elements in their (Morton) order
+// (greedy_colour: each element takes the lowest colour that none of its
+// nodes has seen yet, so no two elements of a colour share a node); the
+// elements are then stored colour by colour (Morton order kept within a
+// colour).
 fea_status build_colours(fea_ctx *ctx, const Mesh &m, Bucket &b) {
     const int nen = kNen[b.etype];
     const int64_t cnt = b.count;
-    std::vector<uint64_t> seen((size_t)m.n * kColourWords, 0ull);
     std::vector<int32_t> col((size_t)cnt);
-    int n_col = 0;
-    for (int64_t e = 0; e < cnt; ++e) {
-        uint64_t mask[kColourWords] = {0, 0, 0, 0};
-        for (int a = 0; a < nen; ++a) {
-            const uint64_t *w = &seen[(size_t)b.conn_h[(size_t)a * cnt + e] * kColourWords];
-            for (int k = 0; k < kColourWords; ++k) mask[k] |= w[k];
-        }
-        int c = -1;
-        for (int k = 0; k < kColourWords && c < 0; ++k)
-            if (~mask[k]) c = 64 * k + __builtin_ctzll(~mask[k]);
-        if (c < 0) return fail(ctx, FEA_EMESH, "colouring needs more than %d colours", 64 * kColourWords);
-        col[(size_t)e] = c;
-        n_col = std::max(n_col, c + 1);
-        for (int a = 0; a < nen; ++a)
-            seen[(size_t)b.conn_h[(size_t)a * cnt + e] * kColourWords + c / 64] |= 1ull << (c % 64);
-    }
+    const int n_col = greedy_colour(m.n, nen, cnt, b.conn_h.data(), 1, cnt, col.data());
+    if (n_col < 0) return fail(ctx, FEA_EMESH, "colouring needs more than %d colours", kColourMax);
     std::vector<int64_t> off((size_t)n_col + 1, 0);
     for (int64_t e = 0; e < cnt; ++e) off[(size_t)col[(size_t)e] + 1]++;
     for (int c = 0; c < n_col; ++c) off[(size_t)c + 1] += off[(size_t)c];

@@ -185,7 +185,15 @@ cudaError_t launch_iface_unpack(const double *in, int64_t nc, const int64_t *loc
                                 double *v, int64_t n, unsigned *err, int sms, cudaStream_t s);
 
 // space-filling curves (fea_partition.cu)
-uint64_t morton_spread3(uint64_t v);                              // 21 bits -> every third bit
+uint64_t morton_spread3(uint64_t v);
+// Greedy element colouring (fea_partition.cu): elements in the given order
+// take the lowest colour none of their nodes has seen (no two elements of a
+// colour share a node); node a of element e is conn[e * elem_stride + a *
+// node_stride].  Returns the number of colours, -1 above kColourMax, -2 for
+// a node id outside [0, n_nodes).
+constexpr int kColourMax = 256;
+int greedy_colour(int64_t n_nodes, int nen, int64_t count, const int32_t *conn, int64_t elem_stride,
+                  int64_t node_stride, int32_t *col);                              // 21 bits -> every third bit
 uint64_t hilbert_key3(uint32_t x0, uint32_t x1, uint32_t x2, int bits);   // Hilbert index in a 2^bits grid
 
 // MLP closure (fea_mlp.cu)

@@ -88,11 +88,47 @@ void bin_keys(int64_t n, const double *xyz, int64_t stride, int level, std::vect
 }
 
 }  // namespace
+
+int greedy_colour(int64_t n_nodes, int nen, int64_t count, const int32_t *conn, int64_t elem_stride,
+                  int64_t node_stride, int32_t *col) {
+    constexpr int W = kColourMax / 64;
+    std::vector<uint64_t> seen((size_t)n_nodes * W, 0ull);
+    int n_col = 0;
+    for (int64_t e = 0; e < count; ++e) {
+        uint64_t mask[W] = {};
+        for (int a = 0; a < nen; ++a) {
+            const int64_t v = conn[e * elem_stride + a * node_stride];
+            if (v < 0 || v >= n_nodes) return -2;
+            for (int k = 0; k < W; ++k) mask[k] |= seen[(size_t)v * W + k];
+        }
+        int c = -1;
+        for (int k = 0; k < W && c < 0; ++k)
+            if (~mask[k]) c = 64 * k + __builtin_ctzll(~mask[k]);
+        if (c < 0) return -1;
+        col[e] = c;
+        n_col = std::max(n_col, c + 1);
+        for (int a = 0; a < nen; ++a)
+            seen[(size_t)conn[e * elem_stride + a * node_stride] * W + c / 64] |= 1ull << (c % 64);
+    }
+    return n_col;
+}
+
 }  // namespace fea
 
 using namespace fea;
 
 extern "C" {
+
+fea_status fea_colour_elements(int64_t n_nodes, int32_t n_en, int64_t count, const int32_t *conn, int32_t *colour,
+                               int32_t *n_colours) {
+    if (n_nodes < 0 || n_en < 1 || n_en > kMaxNen || count < 0 || (count > 0 && (!conn || !colour)) || !n_colours)
+        return FEA_EINVAL;
+    const int nc = greedy_colour(n_nodes, n_en, count, conn, n_en, 1, colour);
+    if (nc == -2) return FEA_EMESH;
+    if (nc < 0) return FEA_ENUMERIC;
+    *n_colours = nc;
+    return FEA_OK;
+}
 
 fea_status fea_sfc_order(int64_t n, const double *xyz, int32_t level, int64_t *order) {
     if (n < 0 || (n > 0 && (!xyz || !order)) || level < 1 || level > 21) return FEA_EINVAL;

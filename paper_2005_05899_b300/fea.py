@@ -35,6 +35,7 @@ EXPORTED = (
     "fea_mlp_fallback_read", "fea_sfc_order", "fea_partition_sfc", "fea_interface_pack", "fea_interface_unpack",
     "fea_poisson_setup", "fea_poisson_solve", "fea_divergence", "fea_gradient", "fea_project",
     "fea_balance_update", "fea_set_model", "fea_wall_setup", "fea_wall_assemble", "fea_autotune_batched",
+    "fea_colour_elements",
 )
 MLP_NPARAM = 8833
 NOALLOC_MAX_NODES = 262144
@@ -98,6 +99,18 @@ def sfc_order(xyz, level: int = 10) -> np.ndarray:
         raise FeaError(st, "fea_sfc_order failed")
     return out
 
+
+def colour_elements(conn, n_nodes: int):
+    """Greedy colouring of the elements conn (E, n_en) (host, no device):
+    returns (colour per element (E,) int32, number of colours)."""
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    col = np.zeros(conn.shape[0], np.int32)
+    nc = ctypes.c_int32(0)
+    st = lib().fea_colour_elements(int(n_nodes), int(conn.shape[1]), int(conn.shape[0]), conn.ctypes.data,
+                                   col.ctypes.data, ctypes.byref(nc))
+    if st:
+        raise FeaError(st, "fea_colour_elements failed")
+    return col, nc.value
 
 def partition_sfc(mesh, nparts: int, level: int = 10, lam=None) -> dict:
     """SFC partition of the elements: {etype: part id per element} (host);
@@ -183,6 +196,7 @@ def lib() -> ctypes.CDLL:
         L.fea_mlp_train_step.argtypes = [vp, vp, vp, i64, ctypes.c_float, vp, vp, vp]
         L.fea_mlp_set_envelope.argtypes = [vp, vp, vp, vp]
         L.fea_sfc_order.argtypes = [i64, vp, i32, vp]
+        L.fea_colour_elements.argtypes = [i64, i32, i64, vp, vp, ctypes.POINTER(i32)]
         L.fea_poisson_setup.argtypes = [vp, i32, vp, vp]
         L.fea_poisson_solve.argtypes = [vp, i32, vp, dbl, vp, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl), vp]
         L.fea_divergence.argtypes = [vp, i32, vp, vp, vp]
