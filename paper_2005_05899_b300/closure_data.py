@@ -6,11 +6,11 @@ learned model, so this module defines the data pipeline:
 1. **Fine runs of the plain method.**  A Taylor-Green vortex (nu = 1/1600) on
    an n_f^3 periodic Kuhn tet mesh, advanced by the three RK3 stages of
    Algorithm 1 with the library's element assembly (mixed precision, Vreman
-   closure) for the momentum RHS.  The pressure Poisson/CG solve of
-   Algorithm 1 is not part of this build's hot path; in its place the
-   velocity is made divergence-free after every stage by a spectral (Leray)
-   projection on the periodic node grid (a fractional-step method:
-   momentum without the pressure gradient, then projection).
+   closure) for the momentum RHS.  In place of the pressure Poisson / CG
+   solve of Algorithm 1 the velocity is made divergence-free after every
+   stage by a spectral (Leray) projection on the periodic node grid (a
+   fractional-step method: momentum without the pressure gradient, then
+   projection), which on a periodic grid needs no iteration.
 2. **Box filter** of the fine nodal velocity to a coarse grid of n_f / r
    cells per direction (trapezoidal top-hat of width r fine cells, periodic),
    for r in `ratios` (several filter widths give the network the range of
