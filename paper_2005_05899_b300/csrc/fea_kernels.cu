@@ -283,25 +283,43 @@ __device__ __forceinline__ JR jacobian_at(const JR X[][3], int g, JR J[3][3]) {
 
 // Jacobian of a PEN06 at (r, s, zeta) from per-element edge combinations:
 // the r- and s-columns are linear in zeta, the zeta-column linear in (r, s).
+// The combinations are kept at twice their value (the shape functions' 1/2
+// factors left out): every column is then 2x the true one, the adjugate 4x
+// and the determinant 8x, all exactly (power-of-two scalings), and the
+// callers rescale J^-1 and the weight instead of paying 21 FP64 multiplies
+// per element.
 template <typename JR>
 struct PrismGeom {
     JR Ar[3], Br[3], As[3], Bs[3], C0[3], Dr[3], Ds[3];
 };
 
 template <typename JR>
-__device__ __forceinline__ void prism_geom(const JR X[][3], PrismGeom<JR> &p) {
+__device__ __forceinline__ void prism_geom2(const JR X[][3], PrismGeom<JR> &p) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const JR e1 = X[1][i] - X[0][i], e2 = X[2][i] - X[0][i];
         const JR f1 = X[4][i] - X[3][i], f2 = X[5][i] - X[3][i];
         const JR h0 = X[3][i] - X[0][i], h1 = X[4][i] - X[1][i], h2 = X[5][i] - X[2][i];
-        p.Ar[i] = JR(0.5) * (e1 + f1);
-        p.Br[i] = JR(0.5) * (f1 - e1);
-        p.As[i] = JR(0.5) * (e2 + f2);
-        p.Bs[i] = JR(0.5) * (f2 - e2);
-        p.C0[i] = JR(0.5) * h0;
-        p.Dr[i] = JR(0.5) * (h1 - h0);
-        p.Ds[i] = JR(0.5) * (h2 - h0);
+        p.Ar[i] = e1 + f1;
+        p.Br[i] = f1 - e1;
+        p.As[i] = e2 + f2;
+        p.Bs[i] = f2 - e2;
+        p.C0[i] = h0;
+        p.Dr[i] = h1 - h0;
+        p.Ds[i] = h2 - h0;
+    }
+}
+
+// detJ > 0 (and finite, for FP64): an FP64 comparison is an FP64-pipe
+// instruction, so the double's bits are tested on the integer pipe instead
+// (a positive finite double has sign bit 0 and a biased exponent below 0x7ff)
+template <typename JR>
+__device__ __forceinline__ bool det_positive(JR d) {
+    if constexpr (sizeof(JR) == 8) {
+        const long long b = __double_as_longlong(d);
+        return b > 0 && b < 0x7ff0000000000000LL;
+    } else {
+        return d > JR(0);
     }
 }
 
@@ -339,9 +357,6 @@ __host__ __device__ constexpr int mlp_rows_per_elem(int et) {
     return et == FEA_TET04 ? 1 : (et == FEA_PYR05 ? 8 : (et == FEA_PEN06 ? 6 : 8));
 }
 
-template <int ET, typename R, typename JR>
-__device__ __forceinline__ JR prism_or_generic_jacobian(const JR X[][3], const PrismGeom<JR> &pg, int g, JR J[3][3]);
-
 // Returns the number of Gauss points whose nu_t fell back from the MLP to
 // Vreman (outside the training envelope); 0 without the MLP.
 template <int ET, typename R, bool J64, bool MLP = false, bool VAR = true>
@@ -370,7 +385,7 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
 #pragma unroll
         for (int i = 0; i < 3; ++i) r[a][i] = rs[a][i] = R(0);
     PrismGeom<JR> pg;
-    if constexpr (ET == FEA_PEN06) prism_geom<JR>(el.X, pg);
+    if constexpr (ET == FEA_PEN06) prism_geom2<JR>(el.X, pg);
     // MLP: phase 1 (this loop) stores each Gauss point's features and its
     // matrix S in the warp's scratch and assembles everything but the
     // subgrid term; phase 2 runs the network over the warp's 32 x ng rows;
@@ -381,12 +396,15 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
     float *ntile = Stile + ng * 9 * 32;
     float *qtile = ntile + ng * 32;
     uint32_t inside_mask = 0;   // bit g: point g inside the training envelope
-    JR V = JR(0);
+    // element volume (sum of the weights W, in R: it only sets Delta)
+    R V = R(0);
     // PEN06: the rule's points are 3 triangle points at each of 2 levels zeta
     // (level-major); the r- and s-columns of J and their cross product (the
     // adjugate's last row) depend on zeta only, so they are formed once per
     // level; per point only the zeta-column, two cross products and the
-    // determinant c2 . (c0 x c1) remain
+    // determinant c2 . (c0 x c1) remain.  Columns at twice their value
+    // (prism_geom2): A = 4 adj J, detj = 8 det J, so J^-1 = 2 A / detj and
+    // W = (w / 8) detj.
     JR c0[3], c1[3], a2[3];
 #pragma unroll 1
     for (int g = 0; g < ng; ++g) {
@@ -421,19 +439,20 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
             detj = c2[0] * a2[0] + c2[1] * a2[1] + c2[2] * a2[2];
             (void)J;
         } else {
-            prism_or_generic_jacobian<ET, R, JR>(el.X, pg, g, J);
+            jacobian_at<ET, R, JR>(el.X, g, J);
             detj = adjugate(J, A);
         }
-        if (!(detj > JR(0))) bad = true;
-        const JR wdet = ref_w<JR>(ET, g) * detj;
-        V += wdet;
-        const R rdet = R(1) / to_r<R>(detj);
+        if (!det_positive(detj)) bad = true;
+        constexpr bool scaled = ET == FEA_PEN06;
+        const R detr = to_r<R>(detj);
+        const R rdet = (scaled ? R(2) : R(1)) / detr;
         R Ji[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int j = 0; j < 3; ++j) Ji[i][j] = to_r<R>(A[i][j]) * rdet;
-        const R W = to_r<R>(wdet);
+        const R W = detr * (scaled ? ref_w<R>(ET, g) * R(0.125) : ref_w<R>(ET, g));
+        V += W;
         // reference-coordinate gradients and the Gauss-point velocity
         R Gx[3][3] = {}, px[3] = {}, ug[3] = {};
 #pragma unroll
@@ -530,7 +549,7 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
     int fallbacks = 0;
     if constexpr (MLP) {
         // Delta = V^(1/3) completes every row (column 5)
-        const R delta = cbrt_r(to_r<R>(V));
+        const R delta = cbrt_r(V);
         const R d2 = delta * delta;
         bool delta_inside;
         const uint16_t db = mlp_delta_bits(float(delta), *mu.w, &delta_inside);
@@ -563,7 +582,7 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
         }
         __syncwarp();   // the scratch is rewritten for the warp's next elements
     } else {
-        const R delta = cbrt_r(to_r<R>(V));
+        const R delta = cbrt_r(V);
         const R d2 = aniso ? R(1) : delta * delta;
 #pragma unroll
         for (int a = 0; a < nen; ++a)
@@ -573,22 +592,6 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
             for (int g = 0; g < ng; ++g) nut_out[g] = float(R(nut_out[g]) * d2);
     }
     return fallbacks;
-}
-
-template <int ET, typename R, typename JR>
-__device__ __forceinline__ JR prism_or_generic_jacobian(const JR X[][3], const PrismGeom<JR> &pg, int g, JR J[3][3]) {
-    if constexpr (ET == FEA_PEN06) {
-        const JR pr = ref_xi<JR>(ET, g, 0), ps = ref_xi<JR>(ET, g, 1), pz = ref_xi<JR>(ET, g, 2);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            J[i][0] = pg.Ar[i] + pz * pg.Br[i];
-            J[i][1] = pg.As[i] + pz * pg.Bs[i];
-            J[i][2] = pg.C0[i] + pr * pg.Dr[i] + ps * pg.Ds[i];
-        }
-        return det3(J);
-    } else {
-        return jacobian_at<ET, R, JR>(X, g, J);
-    }
 }
 
 // TET04: affine map, constant gradients; the 4-point rule is exact for the
