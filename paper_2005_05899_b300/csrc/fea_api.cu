@@ -48,6 +48,8 @@ int rule(int et, double pts[][3], double w[]) {
             return n;
         }
         case FEA_PEN06: {
+            // level-major, and these triangle points in this order: the prism
+            // Jacobian of the element kernels (PrismGeom) relies on both
             const double tri[3][2] = {{1.0 / 6.0, 1.0 / 6.0}, {2.0 / 3.0, 1.0 / 6.0}, {1.0 / 6.0, 2.0 / 3.0}};
             for (int kz = 0; kz < 2; ++kz)
                 for (int q = 0; q < 3; ++q) {

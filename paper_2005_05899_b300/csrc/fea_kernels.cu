@@ -287,10 +287,12 @@ __device__ __forceinline__ JR jacobian_at(const JR X[][3], int g, JR J[3][3]) {
 // factors left out): every column is then 2x the true one, the adjugate 4x
 // and the determinant 8x, all exactly (power-of-two scalings), and the
 // callers rescale J^-1 and the weight instead of paying 21 FP64 multiplies
-// per element.
+// per element.  Q is the zeta-column at the rule's first triangle point
+// (1/6, 1/6); at the other two, (2/3, 1/6) and (1/6, 2/3), it is Q + Dr / 2
+// and Q + Ds / 2.
 template <typename JR>
 struct PrismGeom {
-    JR Ar[3], Br[3], As[3], Bs[3], C0[3], Dr[3], Ds[3];
+    JR Ar[3], Br[3], As[3], Bs[3], Q[3], Dr[3], Ds[3];
 };
 
 template <typename JR>
@@ -304,9 +306,9 @@ __device__ __forceinline__ void prism_geom2(const JR X[][3], PrismGeom<JR> &p) {
         p.Br[i] = f1 - e1;
         p.As[i] = e2 + f2;
         p.Bs[i] = f2 - e2;
-        p.C0[i] = h0;
         p.Dr[i] = h1 - h0;
         p.Ds[i] = h2 - h0;
+        p.Q[i] = h0 + JR(1.0 / 6.0) * (p.Dr[i] + p.Ds[i]);
     }
 }
 
@@ -423,10 +425,16 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
                 a2[1] = c0[2] * c1[0] - c0[0] * c1[2];
                 a2[2] = c0[0] * c1[1] - c0[1] * c1[0];
             }
-            const JR pr = ref_xi<JR>(ET, g, 0), ps = ref_xi<JR>(ET, g, 1);
+            // the zeta-column at triangle point q of the level (see PrismGeom)
+            const int q = g % 3;
             JR c2[3];
+            if (q == 0) {
 #pragma unroll
-            for (int i = 0; i < 3; ++i) c2[i] = pg.C0[i] + pr * pg.Dr[i] + ps * pg.Ds[i];
+                for (int i = 0; i < 3; ++i) c2[i] = pg.Q[i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) c2[i] = pg.Q[i] + JR(0.5) * (q == 1 ? pg.Dr[i] : pg.Ds[i]);
+            }
             // A row 0 = c1 x c2, row 1 = c2 x c0, row 2 = c0 x c1 (J^-1 = A / det)
             A[0][0] = c1[1] * c2[2] - c1[2] * c2[1];
             A[0][1] = c1[2] * c2[0] - c1[0] * c2[2];
