@@ -287,12 +287,17 @@ __device__ __forceinline__ JR jacobian_at(const JR X[][3], int g, JR J[3][3]) {
 // factors left out): every column is then 2x the true one, the adjugate 4x
 // and the determinant 8x, all exactly (power-of-two scalings), and the
 // callers rescale J^-1 and the weight instead of paying 21 FP64 multiplies
-// per element.  Q is the zeta-column at the rule's first triangle point
-// (1/6, 1/6); at the other two, (2/3, 1/6) and (1/6, 2/3), it is Q + Dr / 2
-// and Q + Ds / 2.
+// per element.  With e, f the bottom and top edges from node 0 / 3 and h the
+// vertical edges, the r-column is (e1 + f1) + zeta (f1 - e1) and the
+// zeta-column h0 + r (h1 - h0) + s (h2 - h0); the twist f1 - e1 equals
+// h1 - h0 (both are X4 - X3 - X1 + X0), so one difference Dr serves both and
+// is formed from the short vertical edges (the more accurate rounding for a
+// thin prism), and e1 + f1 = 2 e1 + Dr (likewise Ds for the s-column).  Q is
+// the zeta-column at the rule's first triangle point (1/6, 1/6); at the
+// other two, (2/3, 1/6) and (1/6, 2/3), it is Q + Dr / 2 and Q + Ds / 2.
 template <typename JR>
 struct PrismGeom {
-    JR Ar[3], Br[3], As[3], Bs[3], Q[3], Dr[3], Ds[3];
+    JR Ar[3], As[3], Dr[3], Ds[3], Q[3];
 };
 
 template <typename JR>
@@ -300,14 +305,11 @@ __device__ __forceinline__ void prism_geom2(const JR X[][3], PrismGeom<JR> &p) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const JR e1 = X[1][i] - X[0][i], e2 = X[2][i] - X[0][i];
-        const JR f1 = X[4][i] - X[3][i], f2 = X[5][i] - X[3][i];
         const JR h0 = X[3][i] - X[0][i], h1 = X[4][i] - X[1][i], h2 = X[5][i] - X[2][i];
-        p.Ar[i] = e1 + f1;
-        p.Br[i] = f1 - e1;
-        p.As[i] = e2 + f2;
-        p.Bs[i] = f2 - e2;
         p.Dr[i] = h1 - h0;
         p.Ds[i] = h2 - h0;
+        p.Ar[i] = JR(2) * e1 + p.Dr[i];
+        p.As[i] = JR(2) * e2 + p.Ds[i];
         p.Q[i] = h0 + JR(1.0 / 6.0) * (p.Dr[i] + p.Ds[i]);
     }
 }
@@ -418,8 +420,8 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
                 const JR pz = ref_xi<JR>(ET, g, 2);
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    c0[i] = pg.Ar[i] + pz * pg.Br[i];
-                    c1[i] = pg.As[i] + pz * pg.Bs[i];
+                    c0[i] = pg.Ar[i] + pz * pg.Dr[i];
+                    c1[i] = pg.As[i] + pz * pg.Ds[i];
                 }
                 a2[0] = c0[1] * c1[2] - c0[2] * c1[1];
                 a2[1] = c0[2] * c1[0] - c0[0] * c1[2];
