@@ -12,7 +12,11 @@ Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 lumped-mass volume, rotation invariance, linear-pressure identity, Vreman
 closed forms, Taylor-Green analytic RHS with O(h^2) convergence, tetrahedron
 closed-form integrals, NumPy brute force on single elements, finite-difference
-MLP gradients).
+MLP gradients, the wall law's limits and a flat plate's total force, the
+projection's symmetry / null space / exact discrete integration by parts,
+the balance iteration's fixed point and convergence, the model variants'
+closed forms).  tests/golden/ holds regression fixtures of its results,
+written by tests/golden/make_golden.py from this package alone.
 """
 from __future__ import annotations
 
