@@ -1089,8 +1089,9 @@ __device__ __forceinline__ void chunk_body(const BucketDev &b, const FieldDev &f
 
 // FP64-Jacobian categories are held to 128 registers a thread: a 128-thread
 // CTA then takes the register share of one TET04 CTA, so that these kernels
-// find room beside the persistent TET04 kernel (the side stream overlaps
-// them); the few spills cost less than the overlap gains.  HEX08 and PYR05
+// find room beside the persistent TET04 kernel (on a side stream, or as
+// its programmatic dependent filling its tail, they overlap it); the few
+// spills cost less than the overlap gains.  HEX08 and PYR05
 // (216 and 150 registers unbounded) are held there too: with 256 threads
 // the channel mesh assembles 5 % faster (measured).
 template <int ET, bool J64, bool COMP, bool MLP = false, bool VAR = true>
