@@ -1,0 +1,82 @@
+"""Host logic of bench.py, without a GPU: the algorithmic bytes of the
+roofline, the matching of a committed ncu traffic record to the kernel
+sources and launch plan, the clock-record summary and the FLOP count."""
+import importlib.util
+import os
+import re
+import types
+
+import numpy as np
+import pytest
+
+from paper_2005_05899_b300 import meshgen as mg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_algorithmic_bytes_count_each_referenced_node_once(bench):
+    m = mg.tgv_mesh(3)
+    conn = m.conn[0]
+    b, e, n = bench.tet_algorithmic_bytes(m)
+    assert e == conn.shape[0] == 6 * 27
+    assert n == np.unique(conn).size
+    assert b == 16 * e + 52 * n
+    # a mesh whose elements reference only some of the nodes
+    sub = mg.Mesh(xyz=m.xyz, conn={0: conn[:5]})
+    b5, e5, n5 = bench.tet_algorithmic_bytes(sub)
+    assert (e5, n5) == (5, np.unique(conn[:5]).size) and b5 == 16 * 5 + 52 * n5
+
+
+def test_traffic_record_needs_matching_sources_and_plan(bench, monkeypatch):
+    import json
+    recs = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))["tet04_mixed_assembly"]
+    rec = recs[0]
+    plan = dict(rec["plan"])
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: rec["source_hash"])
+    assert bench.ncu_traffic("tet04_mixed_assembly", plan) == rec["dram_bytes_per_launch"]
+    # every recorded plan finds its own record
+    for r in recs:
+        assert bench.ncu_traffic("tet04_mixed_assembly", dict(r["plan"])) == r["dram_bytes_per_launch"]
+    # a plan that was not captured, another kernel key, changed sources: no traffic figure
+    assert bench.ncu_traffic("tet04_mixed_assembly", dict(plan, chunk_elems=96)) is None
+    assert bench.ncu_traffic("no_such_kernel", plan) is None
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    assert bench.ncu_traffic("tet04_mixed_assembly", plan) is None
+
+
+def test_clock_summary(bench, tmp_path, monkeypatch):
+    monkeypatch.setenv("FEA_BENCH_CLOCKS_DIR", str(tmp_path))
+    cs = bench.ClockSampler(0)
+    rows = [
+        "0, 2032, 2032, 800.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1990, 2032, 1100.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2010, 2032, 1050.3, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "0, [N/A], 2032, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    with open(cs.path, "w") as fh:
+        fh.write("\n".join(rows) + "\n")
+    # stand-ins for the sampling process and its output file
+    cs.proc = types.SimpleNamespace(terminate=lambda: None, wait=lambda timeout=None: 0, kill=lambda: None)
+    cs.f = open(os.devnull, "w")
+    s = cs.stop()
+    assert s == {"sm_mhz": 2010.0, "sm_max_mhz": 2032.0, "reasons": ["sw_power_cap"], "samples": 3}
+    # without a sampling process there is no record
+    assert bench.ClockSampler(0).stop() is None
+
+
+def test_tet_flop_count_matches_its_itemisation(bench):
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    block = src[src.index("# FP32 operations of one TET04"):src.index("TET_FLOPS =")]
+    # each part's count ends its item (before a comma, a period or the line's end)
+    items = [int(x) for x in re.findall(r"\b(\d+)(?:,|\.|\s*$)", block, flags=re.M)]
+    assert len(items) == 14
+    assert sum(items) == bench.TET_FLOPS == 411
