@@ -235,6 +235,42 @@ def _ptr(t) -> int:
     return t.data_ptr()
 
 
+def _on_device(t) -> bool:
+    return bool(t.is_cuda)
+
+
+_NP_DT = {"f64": np.float64, "f32": np.float32, "i64": np.int64}
+
+
+def _buf(t, name: str, dtype: str, numel: int, device: bool = True, optional: bool = False):
+    """Checks a buffer before its address goes to the C ABI, which cannot see
+    its size: a contiguous torch tensor (a CUDA tensor where the entry point
+    takes device memory) or, where host memory is allowed, also a numpy
+    array, of the given element type ("f64", "f32", "i64") and exactly
+    `numel` elements.  Raises ValueError, so that a wrong buffer never reaches
+    a kernel."""
+    if t is None:
+        if optional:
+            return
+        raise ValueError(f"{name}: a buffer is required")
+    if isinstance(t, np.ndarray):
+        if device:
+            raise ValueError(f"{name}: device memory required, got a numpy array")
+        ok, contiguous, n = t.dtype == np.dtype(_NP_DT[dtype]), t.flags.c_contiguous, t.size
+    else:
+        import torch
+        if device and not _on_device(t):
+            raise ValueError(f"{name}: device memory required, got a tensor on {t.device}")
+        want = {"f64": torch.float64, "f32": torch.float32, "i64": torch.int64}[dtype]
+        ok, contiguous, n = t.dtype == want, t.is_contiguous(), t.numel()
+    if not ok:
+        raise ValueError(f"{name}: element type {dtype} required, got {t.dtype}")
+    if not contiguous:
+        raise ValueError(f"{name}: must be contiguous")
+    if n != numel:
+        raise ValueError(f"{name}: {numel} elements required, got {n}")
+
+
 def _stream(stream) -> int:
     if stream is None:
         import torch
@@ -242,6 +278,27 @@ def _stream(stream) -> int:
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def _rows6(x) -> int:
+    """Rows of a float32 device feature array [B][6]."""
+    if getattr(x, "dim", lambda: -1)() != 2 or x.shape[1] != 6:
+        raise ValueError("x: a [B][6] array of raw features required")
+    B = int(x.shape[0])
+    _buf(x, "x", "f32", 6 * B)
+    return B
+
+
+def _iface_check(v, loc, cls, packed, vname: str, pname: str):
+    """Interface buffers: v [3][n] and the packed [3][n_class] float64, loc /
+    cls int64 [m], all device; the sizes handed on are read from them."""
+    for t, name in ((v, vname), (packed, pname)):
+        if getattr(t, "dim", lambda: -1)() != 2 or t.shape[0] != 3:
+            raise ValueError(f"{name}: a [3][n] array required")
+        _buf(t, name, "f64", 3 * int(t.shape[1]))
+    m = int(loc.numel()) if hasattr(loc, "numel") else -1
+    _buf(loc, "loc", "i64", m)
+    _buf(cls, "cls", "i64", m)
 
 
 class Context:
@@ -291,6 +348,8 @@ class Context:
         """theta [8833], feat_mean [6], feat_std [6]: float32 numpy (host) or torch tensors."""
         arrs = [np.ascontiguousarray(a, dtype=np.float32) if not hasattr(a, "data_ptr") else a
                 for a in (theta, feat_mean, feat_std)]
+        for a, name, n in zip(arrs, ("theta", "feat_mean", "feat_std"), (MLP_NPARAM, 6, 6)):
+            _buf(a, name, "f32", n, device=False)
         self._mlp_keep = arrs
         self.check(self._lib.fea_mlp_load(self.handle, _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]),
                                           float(out_scale), _stream(stream)))
@@ -299,12 +358,14 @@ class Context:
     def interface_pack(self, v, loc, cls, out, stream=None):
         """v: float64 device [3][n]; loc, cls: int64 device [m]; out: float64
         device [3][n_class] (zeroed, then the class sums of this part)."""
+        _iface_check(v, loc, cls, out, "v", "out")
         self.check(self._lib.fea_interface_pack(self.handle, _ptr(v), int(v.shape[1]), _ptr(loc), _ptr(cls),
                                                 int(loc.shape[0]), _ptr(out), int(out.shape[1]), _stream(stream)))
         return out
 
     def interface_unpack(self, buf, loc, cls, v, stream=None):
         """v[:, loc[k]] = buf[:, cls[k]] (all device)."""
+        _iface_check(v, loc, cls, buf, "v", "buf")
         self.check(self._lib.fea_interface_unpack(self.handle, _ptr(buf), int(buf.shape[1]), _ptr(loc), _ptr(cls),
                                                   int(loc.shape[0]), _ptr(v), int(v.shape[1]), _stream(stream)))
         return v
@@ -336,10 +397,18 @@ class Context:
 
     def mlp_forward(self, x, out, stream=None):
         """x: float32 device tensor [B][6] of raw features; out: float32 device [B]."""
+        B = _rows6(x)
+        _buf(out, "out", "f32", B)
         self.check(self._lib.fea_mlp_forward(self.handle, _ptr(x), int(x.shape[0]), _ptr(out), _stream(stream)))
         return out
 
     def mlp_train_step(self, x, y, lr: float, loss_out=None, grad_out=None, stream=None):
+        """x: float32 device [B][6]; y: float32 device [B]; loss_out (1) and
+        grad_out (MLP_NPARAM): optional float32, host or device."""
+        B = _rows6(x)
+        _buf(y, "y", "f32", B)
+        _buf(loss_out, "loss_out", "f32", 1, device=False, optional=True)
+        _buf(grad_out, "grad_out", "f32", MLP_NPARAM, device=False, optional=True)
         self.check(self._lib.fea_mlp_train_step(self.handle, _ptr(x), _ptr(y), int(x.shape[0]), float(lr),
                                                 _ptr(loss_out), _ptr(grad_out), _stream(stream)))
 
@@ -358,6 +427,10 @@ class Context:
     def assemble_batched(self, meshes: Sequence["DeviceMesh"], outs, prec="mixed", closure="vreman",
                          mask=TERM_ALL, stream=None):
         n = len(meshes)
+        if len(outs) != n:
+            raise ValueError(f"{n} meshes but {len(outs)} output buffers")
+        for k, (m, o) in enumerate(zip(meshes, outs)):
+            _buf(o, f"outs[{k}]", "f64", 3 * m.n_nodes)
         ids = (ctypes.c_int32 * n)(*[m.id for m in meshes])
         ptrs = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
         self.check(self._lib.fea_assemble_rhs_batched(self.handle, ids, n, PREC[prec], CLOSURE[closure], mask,
@@ -399,12 +472,17 @@ class DeviceMesh:
             u = np.ascontiguousarray(u.T)
         dtype = 0
         if isinstance(u, np.ndarray):
-            dtype = 0 if u.dtype == np.float64 else 1
-            u = np.ascontiguousarray(u)
+            u = np.ascontiguousarray(u, dtype=np.float32 if u.dtype == np.float32 else np.float64)
             p = np.ascontiguousarray(p, dtype=u.dtype)
+            dtype = 0 if u.dtype == np.float64 else 1
         else:
             import torch
+            if u.dtype not in (torch.float64, torch.float32):
+                raise ValueError(f"u: float64 or float32 required, got {u.dtype}")
             dtype = 0 if u.dtype == torch.float64 else 1
+        kind = "f64" if dtype == 0 else "f32"
+        _buf(u, "u", kind, 3 * self.n_nodes, device=False)
+        _buf(p, "p", kind, self.n_nodes, device=False)
         self._keep = (u, p)
         self.ctx.check(self._L().fea_field_upload(self.ctx.handle, self.id, _ptr(u), _ptr(p), dtype, float(nu),
                                                   float(c_vreman), _stream(stream)))
@@ -413,16 +491,20 @@ class DeviceMesh:
                  stream=None):
         """out: float64 device tensor [3][n] (overwritten); nut_out: optional
         float32 device tensor [n_gauss_total]."""
+        _buf(out, "out", "f64", 3 * self.n_nodes)
+        _buf(nut_out, "nut_out", "f32", self.n_gauss_total, optional=True)
         self.ctx.check(self._L().fea_assemble_rhs(self.ctx.handle, self.id, PREC[prec], CLOSURE[closure], mask,
                                                   SCATTER[scatter], _ptr(out), _ptr(nut_out), _stream(stream)))
         return out
 
     def lumped_mass(self, out, stream=None):
+        _buf(out, "out", "f64", self.n_nodes)
         self.ctx.check(self._L().fea_lumped_mass(self.ctx.handle, self.id, _ptr(out), _stream(stream)))
         return out
 
     def fold(self, v, stream=None):
         ncomp = 1 if v.dim() == 1 else v.shape[0]
+        _buf(v, "v", "f64", ncomp * self.n_nodes)
         self.ctx.check(self._L().fea_periodic_fold(self.ctx.handle, self.id, _ptr(v), ncomp, _stream(stream)))
         return v
 
@@ -456,6 +538,7 @@ class DeviceMesh:
 
     def wall_assemble(self, rhs, stream=None):
         """rhs [3][n] (device float64) += the wall-model term at the current field."""
+        _buf(rhs, "rhs", "f64", 3 * self.n_nodes)
         self.ctx.check(self._L().fea_wall_assemble(self.ctx.handle, self.id, _ptr(rhs), _stream(stream)))
         return rhs
 
@@ -468,6 +551,8 @@ class DeviceMesh:
     def poisson_solve(self, b, x, scale=1.0, rtol=1e-10, max_iter=2000, stream=None):
         """K x = scale fold(b) (device float64 [n]); x: initial guess / solution.
         Returns (iterations, ||r|| / ||b||)."""
+        _buf(b, "b", "f64", self.n_nodes)
+        _buf(x, "x", "f64", self.n_nodes)
         it, rr = ctypes.c_int32(0), ctypes.c_double(0.0)
         self.ctx.check(self._L().fea_poisson_solve(self.ctx.handle, self.id, _ptr(b), float(scale), _ptr(x),
                                                    float(rtol), int(max_iter), ctypes.byref(it), ctypes.byref(rr),
@@ -475,10 +560,14 @@ class DeviceMesh:
         return it.value, rr.value
 
     def divergence(self, u, out, stream=None):
+        _buf(u, "u", "f64", 3 * self.n_nodes)
+        _buf(out, "out", "f64", self.n_nodes)
         self.ctx.check(self._L().fea_divergence(self.ctx.handle, self.id, _ptr(u), _ptr(out), _stream(stream)))
         return out
 
     def gradient(self, p, out, stream=None):
+        _buf(p, "p", "f64", self.n_nodes)
+        _buf(out, "out", "f64", 3 * self.n_nodes)
         self.ctx.check(self._L().fea_gradient(self.ctx.handle, self.id, _ptr(p), _ptr(out), _stream(stream)))
         return out
 
@@ -497,6 +586,9 @@ class DeviceMesh:
                          prec="mixed", closure="vreman", stream=None):
         """One RK stage from caller arrays (device, [3][n] / [n] FP64) into `out`,
         through the entry point that allocates nothing (static device scratch)."""
+        for t, name in ((un, "un"), (uk, "uk"), (out, "out")):
+            _buf(t, name, "f64", 3 * self.n_nodes)
+        _buf(p, "p", "f64", self.n_nodes)
         self.ctx.check(self._L().fea_rk_stage_noalloc(self.ctx.handle, self.id, stage, float(dt), PREC[prec],
                                                       CLOSURE[closure], float(nu), float(c_vreman), _ptr(un),
                                                       _ptr(uk), _ptr(p), _ptr(out), _stream(stream)))
@@ -507,6 +599,8 @@ class DeviceMesh:
                                                    CLOSURE[closure], _stream(stream)))
 
     def state(self, out, stream=None):
+        """out: float64 [3][n], host (numpy, pinned or pageable torch) or device."""
+        _buf(out, "out", "f64", 3 * self.n_nodes, device=False)
         self.ctx.check(self._L().fea_state_download(self.ctx.handle, self.id, _ptr(out), _stream(stream)))
         return out
 
