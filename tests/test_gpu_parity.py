@@ -8,7 +8,6 @@ the difference over the max-norm of the oracle's RHS):
                size sets the error: gates 2e-5 / 2e-4 here, the measured
                values are printed by the benchmark.
 """
-import math
 
 import numpy as np
 import pytest

@@ -11,7 +11,6 @@
 import math
 
 import numpy as np
-import pytest
 import torch
 
 import oracle as O
