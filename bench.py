@@ -80,6 +80,16 @@ def tet_algorithmic_bytes(mesh) -> tuple:
 TET_FLOPS = 411
 
 
+def max_over_ranks(values, ws: int, device: str = "cuda"):
+    """Element-wise maximum of `values` over the ranks (the slowest rank sets
+    the time of a weak-scaling run); the values themselves when ws == 1."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -311,10 +321,7 @@ def run_ours(args):
     tet_ms, tet_n = ctx.profile_read(0, 0, reset=True)
     ctx.profile(False)
     clk = clocks.stop()
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks([ms], ws)[0]
     ms_step = ms_max / args.steps
     value = ws * 3 * E * args.steps / (ms_max / 1e3) / 1e6
     # end to end through the public API with pinned host buffers: every step
@@ -386,6 +393,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
     ctx.sync_status()
+    e2e_ms, e2e_serial_ms = max_over_ranks([e2e_ms, e2e_serial_ms], ws)
     last = (e2e_steps - 1) % 2
     assert torch.equal(out_host[last], r_dev[last].cpu()), "the last result read back differs from the device copy"
     e2e_val = ws * 3 * E * e2e_steps / (e2e_ms / 1e3) / 1e6

@@ -80,3 +80,35 @@ def test_tet_flop_count_matches_its_itemisation(bench):
     items = [int(x) for x in re.findall(r"\b(\d+)(?:,|\.|\s*$)", block, flags=re.M)]
     assert len(items) == 14
     assert sum(items) == bench.TET_FLOPS == 411
+
+
+def _max_rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        spec = importlib.util.spec_from_file_location("bench_rank", os.path.join(ROOT, "bench.py"))
+        bench = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(bench)
+        # each rank's step time and end-to-end times; the slowest rank differs per entry
+        got = bench.max_over_ranks([10.0 + rank, 5.0 - rank, 7.0 * (rank == 1)], world, device="cpu")
+        q.put((rank, got))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_times_are_the_maximum_over_two_gloo_ranks(bench):
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    q = mp.get_context("spawn").SimpleQueue()
+    mp.start_processes(_max_rank_main, args=(2, port, q), nprocs=2, join=True, start_method="spawn")
+    res = sorted(q.get() for _ in range(2))
+    assert [r for r, _ in res] == [0, 1]
+    for _, got in res:
+        assert got == [11.0, 5.0, 7.0]
+    # one rank: the values unchanged
+    assert bench.max_over_ranks([3.5, 1.0], 1, device="cpu") == [3.5, 1.0]
