@@ -15,8 +15,8 @@ det of those columns.
   rational arithmetic from the same FP64 coordinates and rule points.  The
   edge-difference form stays within a few ulps of it on thin prisms far from
   the origin, where the plain sum over nodes (the oracle's definition)
-  loses digits to cancellation: 5e-13 / 6e-11 / 5e-9 relative at thicknesses
-  1e-2 / 1e-4 / 1e-6 at a distance of 50.
+  loses digits to cancellation: about 5e-13 / 6e-11 / 5e-9 relative at
+  thicknesses 1e-2 / 1e-4 / 1e-6 at a distance of 50.
 * Oracle: on distorted prisms of unit size both agree to 1e-12.
 """
 from fractions import Fraction
@@ -31,7 +31,7 @@ TRI = [(1 / 6, 1 / 6), (2 / 3, 1 / 6), (1 / 6, 2 / 3)]
 
 
 def kernel_form(X, q, zeta, w):
-    """Cartesian derivatives (6, 3), det J and W at triangle point q, level zeta."""
+    """det J, W and J^-1 at triangle point q, level zeta."""
     e1, e2 = X[1] - X[0], X[2] - X[0]
     h0, h1, h2 = X[3] - X[0], X[4] - X[1], X[5] - X[2]
     Dr, Ds = h1 - h0, h2 - h0
@@ -41,7 +41,7 @@ def kernel_form(X, q, zeta, w):
     c2 = Q if q == 0 else Q + 0.5 * (Dr if q == 1 else Ds)
     A = np.stack([np.cross(c1, c2), np.cross(c2, c0), np.cross(c0, c1)])   # rows: adjugate of the columns
     d8 = c2 @ np.cross(c0, c1)
-    return None, d8 / 8, (w / 8) * d8, 2 * A / d8
+    return d8 / 8, (w / 8) * d8, 2 * A / d8
 
 
 def exact_form(X, xi, w):
@@ -75,7 +75,7 @@ def points():
 def check_against_exact(X, tol):
     for q, xi, wg in points():
         _, dNxi = O.shape(O.PEN06, xi)
-        _, det_k, W_k, Jinv_k = kernel_form(X, q, xi[2], wg)
+        det_k, W_k, Jinv_k = kernel_form(X, q, xi[2], wg)
         grad_e, det_e, W_e = exact_form(X, xi, wg)
         grad_k = dNxi @ Jinv_k
         assert det_k == pytest.approx(det_e, rel=tol)
@@ -91,7 +91,7 @@ def test_distorted_prisms_exact_and_oracle(seed):
     _, dNx, W, det = O.element_geometry(O.PEN06, X)
     for g, (q, xi, wg) in enumerate(points()):
         _, dNxi = O.shape(O.PEN06, xi)
-        _, det_k, W_k, Jinv_k = kernel_form(X, q, xi[2], wg)
+        det_k, W_k, Jinv_k = kernel_form(X, q, xi[2], wg)
         assert det_k == pytest.approx(det[g], rel=1e-12)
         assert W_k == pytest.approx(W[g], rel=1e-12)
         assert np.abs(dNxi @ Jinv_k - dNx[g]).max() <= 1e-12 * np.abs(dNx[g]).max()
