@@ -2,6 +2,7 @@
 
     python -m paper_2005_05899_b300.profile_case --mesh airplane --n 100 \
         --plan chunk --threads 256 --chunk 512 --reps 3
+    python -m paper_2005_05899_b300.profile_case --mesh channel --cells 269,134,135
 
 Builds the seeded mesh and field, uploads them, sets the launch plan and runs
 `--reps` mixed-precision assemblies (or RK3 graph steps with --rk3) with the
@@ -19,6 +20,8 @@ def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--mesh", choices=["airplane", "channel", "tgv"], default="airplane")
     ap.add_argument("--n", type=int, default=100, help="grid nodes per axis (airplane) or cells (tgv)")
+    ap.add_argument("--cells", default="128,64,64",
+                    help="channel cells nx,ny,nz (e.g. 269,134,135 for the 8M-element channel, inputs above L2)")
     ap.add_argument("--plan", choices=["chunk", "atomic"], default="chunk")
     ap.add_argument("--threads", type=int, default=256)
     ap.add_argument("--chunk", type=int, default=512)
@@ -38,7 +41,8 @@ def main(argv=None) -> int:
         m = mg.airplane_mesh(a.n, seed=4)
         f = mg.inflow_field(m, seed=5)
     elif a.mesh == "channel":
-        m = mg.channel_mesh()
+        nx, ny, nz = (int(v) for v in a.cells.split(","))
+        m = mg.channel_mesh(nx, ny, nz)
         f = mg.channel_field(m)
     else:
         m = mg.tgv_mesh(a.n)
