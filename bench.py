@@ -200,13 +200,24 @@ class OracleSampler:
         self._assemble(ne)
         self.rate = ne / max(time.time() - t, 1e-6)
 
+    def _build(self, ne):
+        sub = self.conn[:ne]
+        nodes, inv = np.unique(sub, return_inverse=True)
+        om = self.O.OracleMesh(self.mesh.xyz[nodes], {0: inv.reshape(sub.shape).astype(np.int32)})
+        return om, self.field.u[nodes], self.field.p[nodes]
+
     def _sample(self, ne):
         if self._cached is None or self._cached[0] != ne:
-            sub = self.conn[:ne]
-            nodes, inv = np.unique(sub, return_inverse=True)
-            om = self.O.OracleMesh(self.mesh.xyz[nodes], {0: inv.reshape(sub.shape).astype(np.int32)})
-            self._cached = (ne, om, self.field.u[nodes], self.field.p[nodes])
+            self._cached = (ne, *self._build(ne))
         return self._cached[1:]
+
+    def serial(self, ne: int = 200_000) -> float:
+        """The serial oracle (one thread) on a contiguous sample: Melem/s."""
+        ne = min(ne, self.conn.shape[0])
+        om, u, p = self._build(ne)
+        t = time.time()
+        self.O.assemble_rhs(om, u, p, self.field.nu, self.field.c_vreman, "vreman")
+        return ne / max(time.time() - t, 1e-9) / 1e6
 
     def _assemble(self, ne):
         om, u, p = self._sample(ne)
@@ -229,8 +240,25 @@ class OracleSampler:
         return ne * steps / dt / 1e6, self.threads, desc, dt
 
 
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or "unknown"
+
+
 def cpu_baseline(mesh, field, target_s: float = 12.0):
-    return OracleSampler(mesh, field).run(target_s)
+    """The oracle's rate on all host threads (a bounded sample of the
+    workload) as the cpu_baseline object, with its serial rate and the CPU."""
+    sampler = OracleSampler(mesh, field)
+    v, cores, desc, _ = sampler.run(target_s)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+            "serial_value": sampler.serial(), "cpu_model": cpu_model()}
 
 
 def run_reference(args):
@@ -256,7 +284,8 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "elements": mesh.n_elem_total, "nodes": mesh.n_nodes},
             "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+                             "serial_value": sampler.serial(), "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -428,8 +457,7 @@ def run_ours(args):
                     "serial_value": e2e_serial},
             "gpu_launches": launches, "clocks": clk}
     if rank == 0 and ws == 1 and not args.no_cpu:
-        v, cores, desc, _ = cpu_baseline(mesh, field, target_s=args.cpu_seconds)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        line["cpu_baseline"] = cpu_baseline(mesh, field, target_s=args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -112,3 +112,24 @@ def test_times_are_the_maximum_over_two_gloo_ranks(bench):
         assert got == [11.0, 5.0, 7.0]
     # one rank: the values unchanged
     assert bench.max_over_ranks([3.5, 1.0], 1, device="cpu") == [3.5, 1.0]
+
+
+def test_reference_arm_prints_its_json_line():
+    """`bench.py --impl reference` (the oracle on the host cores, no GPU) on
+    a small airplane-like mesh: one JSON line with the contract's keys."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3", "--n-axis", "40"], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "RHS assembly Melem/s" and d["unit"] == "Melem/s"
+    assert d["higher_is_better"] is True and d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 3
+    assert d["value"] > 0 and d["e2e"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
+    assert cb["serial_value"] > 0 and cb["cpu_model"] and "TET04" in cb["sample"]
