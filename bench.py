@@ -108,7 +108,7 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
 def kernel_source_hash() -> str:
     """Hash of the TET04 kernel's translation unit (the kernel and its launcher)."""
     h = hashlib.sha256()
-    h.update(open(os.path.join(ROOT, "paper_2005_05899_b300", "csrc", "fea_tet.cu"), "rb").read())
+    h.update(open(os.path.join(ROOT, "paper_2005_05899_b300", "csrc", "fea_tet_ws.cu"), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -130,8 +130,11 @@ typedef struct {
 typedef struct {
     int32_t scatter;            /* fea_scatter (not AUTO); under FEA_FP64 a CHUNK plan
                                    runs ATOMIC (COLOUR and WARP apply to both) */
-    int32_t threads_per_block;  /* element kernels: multiple of 32 in [32, 1024] (capped at 256) */
-    int32_t chunk_elems;        /* elements per chunk for FEA_SCATTER_CHUNK: multiple of 32 in [32, 4096] */
+    int32_t threads_per_block;  /* element kernels: multiple of 32 in [32, 1024] (capped at 256);
+                                   the TET04 chunk kernel (FEA_MIXED) takes from it its
+                                   compute warps: 12 from 384 threads, 8 from 256, else 4 */
+    int32_t chunk_elems;        /* elements per chunk for FEA_SCATTER_CHUNK: multiple of 32 in [32, 4096]
+                                   (the TET04 chunk kernel uses 64 per compute warp) */
     int32_t chunk_acc;          /* FEA_SCATTER_CHUNK nodal sums inside a chunk: 0 = FP32,
                                    1 = compensated two-float sums (about 48 significant bits);
                                    sums across chunks are FP64 atomics in both cases */
@@ -465,12 +468,14 @@ fea_status fea_interface_unpack(fea_ctx *ctx, const double *in, int64_t n_class,
  * p, 40 bytes per node) is one static device array, reserved on every GPU
  * that loads the library and held until the process exits.
  *   un, uk, p: device, [3][n_nodes], [3][n_nodes], [n_nodes] FP64 (inputs);
- *   uk_out: device [3][n_nodes] FP64 (output; may equal uk);
+ *   uk_out: device [3][n_nodes] FP64 (output; may be the same array as uk
+ *           or as un, e.g. the last stage writing u^(n+1) over u^n);
  *   nu, c_vreman: viscosity and Vreman constant for this call.
  * The mesh must have been uploaded (fea_mesh_upload allocates as usual) and
- * have at most FEA_NOALLOC_MAX_NODES nodes, else FEA_EINVAL.  The first call
- * on a device looks up the array's device address (with that device made
- * current, then restored); make that first call before any stream capture.
+ * have at most FEA_NOALLOC_MAX_NODES nodes, else FEA_EINVAL.  fea_create
+ * looks up the array's device address on its device (this loads the
+ * library's device module there and reserves the array), so no call of this
+ * entry point loads or reserves anything.
  * Every call on a device shares the array and it keeps the last call's
  * contents: each call clears the RHS part itself, and calls that overlap on
  * the GPU (e.g. on two streams at once) race on the shared scratch. */
@@ -501,6 +506,18 @@ fea_status fea_autotune(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure c
  * FEA_EMESH (det J <= 0 seen), FEA_ENUMERIC (non-finite residual),
  * FEA_ETIMEOUT (bounded wait gave up), or FEA_OK. */
 fea_status fea_sync_status(fea_ctx *ctx, void *stream);
+
+/* Poll limit of the bounded device-side waits of the TET04 assembly kernel
+ * (mixed precision, chunk scatter), which otherwise give up after about four
+ * million polls of an mbarrier phase, each of which may suspend the warp for
+ * a hardware-chosen time: polls > 0 sets the limit and makes every poll a
+ * non-suspending test, 0 restores the default.  A wait that gives up makes
+ * its CTA stop assembling, lets
+ * the copies it has in flight land, and sets the device error word
+ * (FEA_ETIMEOUT at the next fea_sync_status); the RHS of that assembly is
+ * then incomplete.  A small limit is how a test drives that path without a
+ * fault.  Host only; drops every captured RK graph of the context. */
+fea_status fea_set_wait_limit(fea_ctx *ctx, uint32_t polls);
 
 /* Number of kernels this context has launched so far (host counter). */
 int64_t fea_launch_count(const fea_ctx *ctx);

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <memory>
 #include <string>
 #include <vector>
@@ -213,6 +214,17 @@ struct Bucket {
     DevBuf<int32_t> chunk_nodes;
     DevBuf<float4> chunk_rec;
     DevBuf<uint32_t> inc_range;
+    // tables of the warp-specialised TET04 kernel (mixed precision, chunk scatter)
+    int ws_nw = 0, ws_want = 0;
+    int32_t ws_lmp = 0;
+    int64_t ws_nch = 0;
+    DevBuf<int64_t> ws_off;
+    DevBuf<int32_t> ws_nodes;
+    DevBuf<float4> ws_rec;
+    DevBuf<uint32_t> ws_ids;
+    DevBuf<int32_t> ws_nfp, ws_eorig;
+    DevBuf<uint32_t> ws_toff;
+    DevBuf<uint4> ws_elem;
     // colouring (FEA_SCATTER_COLOUR), built on first use
     DevBuf<int32_t> col_conn, col_orig;
     std::vector<int64_t> col_off;   // [n_colours + 1] element offsets per colour
@@ -234,6 +246,17 @@ struct Bucket {
         b.max_chunk_nodes = max_chunk_nodes;
         b.col_conn = col_conn.p;
         b.col_orig = col_orig.p;
+        b.ws_nw = ws_nw;
+        b.ws_lmp = ws_lmp;
+        b.ws_nch = ws_nch;
+        b.ws_off = ws_off.p;
+        b.ws_nodes = ws_nodes.p;
+        b.ws_rec = ws_rec.p;
+        b.ws_ids = ws_ids.p;
+        b.ws_elem = ws_elem.p;
+        b.ws_nfp = ws_nfp.p;
+        b.ws_eorig = ws_eorig.p;
+        b.ws_toff = ws_toff.p;
         return b;
     }
 };
@@ -335,6 +358,7 @@ struct fea_ctx {
     bool mlp_ready = false;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t launches = 0;
+    uint32_t wait_polls = 0;   // fea_set_wait_limit (0: kernels' default)
 };
 
 namespace {
@@ -463,6 +487,251 @@ fea_status build_chunks(fea_ctx *ctx, Mesh &m, Bucket &b, int C) {
     return FEA_OK;
 }
 
+// Compute warps of the warp-specialised TET04 kernel for a plan's
+// threads_per_block: 12 from 384 threads, 8 from 256, else 4.
+int ws_warps_for(int threads) { return threads >= 384 ? 12 : threads >= 256 ? 8 : 4; }
+
+// Tables of the warp-specialised TET04 kernel (see BucketDev::ws_*): chunks
+// of C = 64 NW elements, NW = want (12, 8 or 4) or, if its chunks do not
+// keep below 1024 nodes and 64 slots per node or its shared memory does not
+// fit one CTA, the next smaller.  No tables (the kernel is not used) when
+// none fits.
+//
+// Within a chunk the elements are matched greedily (Morton order) into
+// pairs that share a face.  A pair is stored as A = (f0, f1, f2, a) with
+// det > 0 and B's fourth node b; B = (f1, f0, f2, b) then has det > 0 as
+// well (b lies across the face), so the kernel loads five nodes instead of
+// eight and writes one slot per face node for both elements.  Unmatched
+// elements follow as plain pairs in their own node order.
+fea_status build_ws_tables(fea_ctx *ctx, Mesh &m, Bucket &b, int want) {
+    if (b.etype != FEA_TET04 || b.fp64j || b.count == 0) return FEA_OK;
+    if (b.ws_want == want) return FEA_OK;
+    b.ws_want = want;
+    const int64_t cnt = b.count, n = m.n;
+    std::vector<int32_t> orig_h((size_t)cnt);
+    CK(cudaMemcpy(orig_h.data(), b.orig.p, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost));
+    const double *X = m.xyz_h.data();
+    auto det4 = [&](const int32_t v[4]) {
+        double d[3][3];
+        for (int q = 0; q < 3; ++q)
+            for (int k = 0; k < 3; ++k) d[q][k] = X[(size_t)k * n + v[q + 1]] - X[(size_t)k * n + v[0]];
+        return d[0][0] * (d[1][1] * d[2][2] - d[1][2] * d[2][1]) - d[0][1] * (d[1][0] * d[2][2] - d[1][2] * d[2][0]) +
+               d[0][2] * (d[1][0] * d[2][1] - d[1][1] * d[2][0]);
+    };
+    for (int nw : {12, 8, 4}) {
+        if (nw > want) continue;
+        const int C = 64 * nw, R = C / 2;
+        const int64_t nch = (cnt + C - 1) / C;
+        std::vector<int64_t> off((size_t)nch + 1, 0);
+        std::vector<int32_t> nodes_n((size_t)nch, 0), nfp((size_t)nch, 0), eorig((size_t)nch * C, -1);
+        std::vector<uint32_t> toff((size_t)nch * 68, 0u);
+        std::vector<float4> recs;
+        std::vector<uint32_t> idv;
+        std::vector<uint4> elem((size_t)nch * R, make_uint4(0u, 0u, 0u, 0u));
+        recs.reserve((size_t)(cnt / 2 + 64));
+        idv.reserve((size_t)(cnt / 2 + 64));
+        // per chunk: the incidences (node ids) of each record in slot order,
+        // with the record each belongs to
+        std::vector<int32_t> inc, uniq, lcount, order, lrank, lstart, fill, mate, tri;
+        std::vector<std::array<int32_t, 5>> fkey;   // (n0, n1, n2, element, opposite local node)
+        std::vector<int> nbn;
+        std::vector<std::pair<int, int>> nbv;
+        int32_t lmp = 0;
+        bool fits = true;
+        for (int64_t k = 0; k < nch && fits; ++k) {
+            const int64_t e0 = k * C;
+            const int ne = (int)std::min<int64_t>(C, cnt - e0);
+            auto node = [&](int el, int a) { return b.conn_h[(size_t)a * cnt + e0 + el]; };
+            // face adjacency inside the chunk
+            fkey.clear();
+            for (int el = 0; el < ne; ++el)
+                for (int o = 0; o < 4; ++o) {
+                    int32_t f[3], j = 0;
+                    for (int a = 0; a < 4; ++a)
+                        if (a != o) f[j++] = node(el, a);
+                    std::sort(f, f + 3);
+                    fkey.push_back({f[0], f[1], f[2], el, o});
+                }
+            std::sort(fkey.begin(), fkey.end());
+            // face neighbours inside the chunk: (neighbour, my opposite node), at most 4
+            nbn.assign(ne, 0);
+            nbv.resize((size_t)4 * ne);
+            for (size_t i = 0; i + 1 < fkey.size(); ++i)
+                if (fkey[i][0] == fkey[i + 1][0] && fkey[i][1] == fkey[i + 1][1] && fkey[i][2] == fkey[i + 1][2]) {
+                    const int x = fkey[i][3], y = fkey[i + 1][3];
+                    if (nbn[x] < 4) nbv[(size_t)4 * x + nbn[x]++] = {y, fkey[i][4]};
+                    if (nbn[y] < 4) nbv[(size_t)4 * y + nbn[y]++] = {x, fkey[i + 1][4]};
+                }
+            mate.assign(ne, -1);
+            tri.assign(ne, -1);   // opposite local node of the shared face
+            for (int el = 0; el < ne; ++el) {
+                if (mate[el] >= 0) continue;
+                for (int h = 0; h < nbn[el]; ++h) {
+                    const auto &pr = nbv[(size_t)4 * el + h];
+                    if (mate[pr.first] < 0) {
+                        mate[el] = pr.first;
+                        mate[pr.first] = el;
+                        tri[el] = pr.second;
+                        for (int h2 = 0; h2 < nbn[pr.first]; ++h2)
+                            if (nbv[(size_t)4 * pr.first + h2].first == el) tri[pr.first] = nbv[(size_t)4 * pr.first + h2].second;
+                        break;
+                    }
+                }
+            }
+            // records: face pairs first, then the others two by two
+            inc.clear();
+            std::vector<int> rest;
+            int n_fp = 0;
+            std::vector<std::pair<int, int>> pairs;
+            for (int el = 0; el < ne; ++el) {
+                if (mate[el] < 0)
+                    rest.push_back(el);
+                else if (mate[el] > el) {
+                    // B = (f1, f0, f2, b) must be positive too (b across the face from a)
+                    int32_t f[3], j = 0;
+                    for (int a = 0; a < 4; ++a)
+                        if (a != tri[el]) f[j++] = node(el, a);
+                    int32_t v[4] = {f[0], f[1], f[2], node(el, tri[el])};
+                    if (!(det4(v) > 0.0)) std::swap(v[0], v[1]);
+                    const int32_t w[4] = {v[1], v[0], v[2], node(mate[el], tri[mate[el]])};
+                    if (det4(w) > 0.0) {
+                        pairs.push_back({el, mate[el]});
+                    } else {
+                        rest.push_back(el);
+                        rest.push_back(mate[el]);
+                    }
+                }
+            }
+            std::sort(rest.begin(), rest.end());
+            n_fp = (int)pairs.size();
+            std::vector<int32_t> recnodes;   // 8 node ids per record (-1 unused)
+            int pos = 0;
+            for (auto &pr : pairs) {
+                const int A = pr.first, Bq = pr.second;
+                int32_t f[3], j = 0;
+                for (int a = 0; a < 4; ++a)
+                    if (a != tri[A]) f[j++] = node(A, a);
+                int32_t v[4] = {f[0], f[1], f[2], node(A, tri[A])};
+                if (!(det4(v) > 0.0)) std::swap(v[0], v[1]);
+                const int32_t bb = node(Bq, tri[Bq]);
+                for (int a = 0; a < 4; ++a) recnodes.push_back(v[a]);
+                recnodes.push_back(bb);
+                for (int a = 0; a < 3; ++a) recnodes.push_back(-1);
+                eorig[(size_t)(e0 + pos)] = orig_h[(size_t)(e0 + A)];
+                eorig[(size_t)(e0 + pos + 1)] = orig_h[(size_t)(e0 + Bq)];
+                pos += 2;
+            }
+            for (size_t i = 0; i < rest.size(); i += 2) {
+                for (int h = 0; h < 2; ++h) {
+                    if (i + h < rest.size()) {
+                        const int el = rest[i + h];
+                        for (int a = 0; a < 4; ++a) recnodes.push_back(node(el, a));
+                        eorig[(size_t)(e0 + pos + h)] = orig_h[(size_t)(e0 + el)];
+                    } else
+                        for (int a = 0; a < 4; ++a) recnodes.push_back(-1);
+                }
+                pos += 2;
+            }
+            const int nrec = (int)(recnodes.size() / 8);
+            uniq.clear();
+            for (int32_t v : recnodes)
+                if (v >= 0) uniq.push_back(v);
+            std::sort(uniq.begin(), uniq.end());
+            uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+            const int L = (int)uniq.size();
+            const int Lp = (L + 3) & ~3;
+            if (Lp > 1024) {
+                fits = false;
+                break;
+            }
+            lmp = std::max(lmp, Lp);
+            auto lof = [&](int32_t id) { return (int)(std::lower_bound(uniq.begin(), uniq.end(), id) - uniq.begin()); };
+            lcount.assign(L, 0);
+            for (int32_t v : recnodes)
+                if (v >= 0) lcount[lof(v)]++;
+            // local order: decreasing slot count (similar loop lengths in a reducer warp)
+            order.resize(L);
+            for (int l = 0; l < L; ++l) order[l] = l;
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return lcount[x] > lcount[y]; });
+            lrank.resize(L);
+            for (int l = 0; l < L; ++l) lrank[order[l]] = l;
+            // slot (node l, its t-th incidence) at toff[t] + l: toff[t + 1] - toff[t]
+            // = number of nodes with more than t slots (a prefix of the order)
+            {
+                uint32_t *to = &toff[(size_t)k * 68];
+                int hist[68] = {};
+                for (int l = 0; l < L; ++l) hist[std::min(lcount[l], 67)]++;
+                int above = L;   // nodes with more than t slots
+                to[0] = 0u;
+                for (int t = 0; t < 67; ++t) {
+                    above -= hist[t];
+                    to[t + 1] = to[t] + (uint32_t)above;
+                }
+            }
+            fill.assign(L, 0);
+            for (int r = 0; r < nrec && fits; ++r) {
+                uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                for (int a = 0; a < 8; ++a) {
+                    const int32_t id = recnodes[(size_t)8 * r + a];
+                    if (id < 0) continue;
+                    const int l = lrank[lof(id)];
+                    const int rk = fill[l]++;
+                    if (rk >= 64) fits = false;
+                    v[a] = (uint32_t)l | ((uint32_t)rk << 10);
+                }
+                elem[(size_t)(k * R + r)] = make_uint4(v[0] | (v[1] << 16), v[2] | (v[3] << 16), v[4] | (v[5] << 16),
+                                                       v[6] | (v[7] << 16));
+            }
+            const int32_t o = uniq[0];
+            const double ox = X[o], oy = X[n + o], oz = X[2 * n + o];
+            for (int l = 0; l < L; ++l) {
+                const int32_t id = uniq[order[l]];
+                recs.push_back(make_float4((float)(X[id] - ox), (float)(X[n + id] - oy), (float)(X[2 * n + id] - oz), 0.f));
+                idv.push_back((uint32_t)id);
+            }
+            // a node is the chunk's own when all its element incidences lie in the chunk
+            {
+                std::vector<int> elinc(L, 0);
+                for (int el = 0; el < ne; ++el)
+                    for (int a = 0; a < 4; ++a) elinc[lrank[lof(node(el, a))]]++;
+                for (int l = 0; l < L; ++l) {
+                    uint32_t &w = idv[idv.size() - L + l];
+                    if (elinc[l] != m.inc_total[(int32_t)w]) w |= 0x80000000u;
+                }
+            }
+            for (int l = L; l < Lp; ++l) {
+                recs.push_back(make_float4(0.f, 0.f, 0.f, 0.f));
+                idv.push_back(0u);
+            }
+            nodes_n[(size_t)k] = L;
+            nfp[(size_t)k] = n_fp;
+            off[(size_t)k + 1] = off[(size_t)k] + Lp;
+        }
+        if (!fits || tet_ws_smem_bytes(nw, lmp) > kMaxBlockSmem) continue;
+        CK(b.ws_off.alloc(off.size()));
+        CK(b.ws_nodes.alloc(nodes_n.size()));
+        CK(b.ws_nfp.alloc(nfp.size()));
+        CK(b.ws_rec.alloc(recs.size()));
+        CK(b.ws_ids.alloc(idv.size()));
+        CK(b.ws_elem.alloc(elem.size()));
+        CK(b.ws_eorig.alloc(eorig.size()));
+        CK(b.ws_toff.alloc(toff.size()));
+        CK(cudaMemcpy(b.ws_toff.p, toff.data(), toff.size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b.ws_off.p, off.data(), off.size() * 8, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b.ws_nodes.p, nodes_n.data(), nodes_n.size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b.ws_nfp.p, nfp.data(), nfp.size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b.ws_rec.p, recs.data(), recs.size() * sizeof(float4), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b.ws_ids.p, idv.data(), idv.size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b.ws_elem.p, elem.data(), elem.size() * sizeof(uint4), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b.ws_eorig.p, eorig.data(), eorig.size() * 4, cudaMemcpyHostToDevice));
+        b.ws_nw = nw;
+        b.ws_lmp = lmp;
+        b.ws_nch = nch;
+        return FEA_OK;
+    }
+    return FEA_OK;
+}
+
 // Greedy colouring of a category's elements in their (Morton) order
 // (greedy_colour: each element takes the lowest colour that none of its
 // nodes has seen yet, so no two elements of a colour share a node); the
@@ -530,8 +799,7 @@ bool tail_order(const Mesh &m, fea_prec prec, fea_closure closure, fea_scatter s
         if (!bp->count) continue;
         if (bp->fp64j && bp->etype == FEA_PEN06 && bp->lconn.p)
             ++n_pen64;
-        else if (!bp->fp64j && bp->etype == FEA_TET04 && bp->lconn.p &&
-                 tet_pipe_smem_bytes(bp->dev()) <= kChunkSmemLimit)
+        else if (!bp->fp64j && bp->etype == FEA_TET04 && bp->ws_rec.p)
             ++n_tet;
         else
             ++other;
@@ -584,6 +852,7 @@ fea_status assemble_into(fea_ctx *ctx, Mesh &m, fea_prec prec, fea_closure closu
             a.mlp = closure == FEA_CLOSURE_MLP ? mlp_fast_ptr(ctx->mlp_w.p) : nullptr;
             a.mlp_fb = closure == FEA_CLOSURE_MLP ? ctx->mlp_fb.p : nullptr;
             a.pdl = tail && b.fp64j;
+            a.wait_polls = ctx->wait_polls;
             cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
             if (ctx->profiling) CK(cudaStreamIsCapturing(s, &cap));
             ProfRec pr{b.etype, b.fp64j, nullptr, nullptr};
@@ -652,7 +921,7 @@ fea_status rk_stage_impl(fea_ctx *ctx, Mesh &m, int stage, double dt, fea_prec p
         CK(launch_fold(m.slaves.p, m.masters.p, (int64_t)m.slaves.n, m.rhs.p, 3, m.n, s));
         ctx->launches += 2;
     }
-    CK(launch_rk_update(m.n, m.un.p, m.uk.p, stage == 2 ? m.un.p : nullptr, m.rhs.p, m.minv.p,
+    CK(launch_rk_update(m.n, m.un.p, m.uk.p, m.uk.p, stage == 2 ? m.un.p : nullptr, m.rhs.p, m.minv.p,
                         m.dirichlet.n ? m.dirichlet.p : nullptr, m.p64.p, m.up32.p, A[stage], B[stage], dt, s));
     ctx->launches++;
     return FEA_OK;
@@ -732,6 +1001,7 @@ fea_status stage_with_scratch(fea_ctx *ctx, int32_t mesh, int32_t stage, double 
             a.mlp = closure == FEA_CLOSURE_MLP ? mlp_fast_ptr(ctx->mlp_w.p) : nullptr;
             a.mlp_fb = closure == FEA_CLOSURE_MLP ? ctx->mlp_fb.p : nullptr;
             a.pdl = tail && b.fp64j;
+            a.wait_polls = ctx->wait_polls;
             if (colour) {
                 CK(launch_assemble_colour(b.dev(), f, a, prec, m->plan.threads_per_block, b.col_off.data(),
                                           b.n_colours, ls));
@@ -754,8 +1024,7 @@ fea_status stage_with_scratch(fea_ctx *ctx, int32_t mesh, int32_t stage, double 
         CK(launch_fold(m->slaves.p, m->masters.p, (int64_t)m->slaves.n, rhs, 3, n, s));
         ctx->launches += 2;
     }
-    if (uk_out != uk) CK(cudaMemcpyAsync(uk_out, uk, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
-    CK(launch_rk_update(n, un, uk_out, nullptr, rhs, m->minv.p, m->dirichlet.n ? m->dirichlet.p : nullptr, p, up,
+    CK(launch_rk_update(n, un, uk, uk_out, nullptr, rhs, m->minv.p, m->dirichlet.n ? m->dirichlet.p : nullptr, p, up,
                         A[stage], B[stage], dt, s));
     ctx->launches += 2;
     return FEA_OK;
@@ -795,6 +1064,10 @@ fea_status fea_create(int device, fea_ctx **out) {
         if (cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) { st = FEA_ECUDA; break; }
         RefTables t = make_tables();
         if (upload_ref_tables(t) != cudaSuccess) { st = FEA_ECUDA; break; }
+        // the allocation-free stage's static scratch: its module is loaded
+        // (and the array reserved) here, not at that entry point's first call
+        void *scratch = nullptr;
+        if (noalloc_scratch_address(device, &scratch) != cudaSuccess) { st = FEA_ECUDA; break; }
     } while (0);
     if (st != FEA_OK) {
         cudaGetLastError();
@@ -975,6 +1248,8 @@ fea_status fea_mesh_upload(fea_ctx *ctx, const fea_mesh_desc *d, void *stream, i
         CK(cudaStreamSynchronize(s));
     }
     if ((st_up = ensure_chunks(ctx, *m, m->plan.chunk_elems))) return st_up;
+    for (auto &bp : m->buckets)
+        if ((st_up = build_ws_tables(ctx, *m, *bp, ws_warps_for(m->plan.threads_per_block)))) return st_up;
     CK(m->un.alloc(3 * n));
     CK(m->uk.alloc(3 * n));
     CK(m->p64.alloc(n));
@@ -1251,6 +1526,8 @@ fea_status fea_set_plan(fea_ctx *ctx, int32_t mesh, const fea_plan *plan) {
             if (b->count && chunk_kernel_smem(b->dev(), plan->chunk_acc) > kChunkSmemLimit)
                 return fail(ctx, FEA_EINVAL, "chunk of %d elements needs more than 220 KB of shared memory",
                             plan->chunk_elems);
+        for (auto &b : m->buckets)
+            if ((st = build_ws_tables(ctx, *m, *b, ws_warps_for(plan->threads_per_block)))) return st;
     }
     m->plan = *plan;
     if (m->graph.exec) {
@@ -1316,6 +1593,8 @@ fea_status fea_autotune(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure c
     for (const fea_plan &cand : cands) {
         if (cand.scatter == FEA_SCATTER_CHUNK) {
             if ((st = ensure_chunks(ctx, *m, cand.chunk_elems))) return st;
+            for (auto &b : m->buckets)
+                if ((st = build_ws_tables(ctx, *m, *b, ws_warps_for(cand.threads_per_block)))) return st;
             bool fits = true;
             for (auto &b : m->buckets)
                 if (b->count && (chunk_kernel_smem(b->dev(), cand.chunk_acc) > kChunkSmemLimit ||
@@ -1353,7 +1632,11 @@ fea_status fea_autotune(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure c
         best = best_chunk;
         best_ms = best_chunk_ms;
     }
-    if (best.scatter == FEA_SCATTER_CHUNK && (st = ensure_chunks(ctx, *m, best.chunk_elems))) return st;
+    if (best.scatter == FEA_SCATTER_CHUNK) {
+        if ((st = ensure_chunks(ctx, *m, best.chunk_elems))) return st;
+        for (auto &b : m->buckets)
+            if ((st = build_ws_tables(ctx, *m, *b, ws_warps_for(best.threads_per_block)))) return st;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (cache_path) {
@@ -1824,6 +2107,17 @@ fea_status fea_profile_read(fea_ctx *ctx, int etype, int fp64_jac, double *total
         }
         ctx->prof.clear();
     }
+    return FEA_OK;
+}
+
+fea_status fea_set_wait_limit(fea_ctx *ctx, uint32_t polls) {
+    if (!ctx) return FEA_EINVAL;
+    ctx->wait_polls = polls;
+    for (auto &m : ctx->meshes)
+        if (m && m->graph.exec) {
+            cudaGraphExecDestroy(m->graph.exec);
+            m->graph.exec = nullptr;
+        }
     return FEA_OK;
 }
 

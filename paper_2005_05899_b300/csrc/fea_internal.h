@@ -63,6 +63,29 @@ struct BucketDev {
     // colouring (FEA_SCATTER_COLOUR): the elements reordered colour by colour
     const int32_t *col_conn;        // [nen][count] node ids in colour order
     const int32_t *col_orig;        // [count] caller element index, colour order
+    // tables of the warp-specialised TET04 kernel (k_tet_ws): chunks of
+    // C = 64 ws_nw elements, each with its L_k distinct nodes ordered by
+    // decreasing incidence count, their incidences numbered node by node
+    int ws_nw = 0;                  // compute warps per CTA (0: no tables)
+    int32_t ws_lmp = 0;             // max padded node-list length (multiple of 4, <= 1024)
+    int64_t ws_nch = 0;
+    const int64_t *ws_off = nullptr;    // [ws_nch + 1] offsets into ws_rec / ws_ids
+    const int32_t *ws_nodes = nullptr;  // [ws_nch] L_k
+    const float4 *ws_rec = nullptr;     // per local node: FP32 coordinates relative to the
+                                        // chunk's first node (.w unused); padded to a multiple
+                                        // of 4 entries
+    const uint32_t *ws_ids = nullptr;   // per local node: caller node id, bit 31 set when
+                                        // elements outside the chunk touch it too
+    const uint4 *ws_elem = nullptr;     // [ws_nch][C/2] records of 8 x u16 (local node id
+                                        // (10 bits) | the incidence's rank among the node's
+                                        // slots << 10): first ws_nfp face pairs
+                                        // (f0, f1, f2, a, b; see the kernel), then pairs of
+                                        // elements (4 + 4 nodes)
+    const int32_t *ws_nfp = nullptr;    // [ws_nch] face pairs per chunk
+    const uint32_t *ws_toff = nullptr;  // [ws_nch][68] first slot of the t-th incidences
+                                        // (t = 0..64; nodes by decreasing slot count)
+    const int32_t *ws_eorig = nullptr;  // [ws_nch][C] caller element index of record
+                                        // position 2t / 2t + 1 (-1: none)
 };
 
 // Per-mesh nodal data used by the kernels.
@@ -91,6 +114,9 @@ struct AsmArgs {
     // it on the stream (starts while that one drains; waits for it to
     // complete before it ends itself)
     int pdl = 0;
+    // bounded device waits (warp-specialised TET04 kernel): polls before a
+    // wait gives up; 0 = the default (about 4 million)
+    uint32_t wait_polls = 0;
 };
 
 // launchers (fea_kernels.cu); all return cudaGetLastError() of the launch
@@ -119,17 +145,18 @@ cudaError_t launch_assemble_batch(const void *buckets, const void *fields, const
                                   cudaStream_t s);
 size_t batch_item_bytes();
 cudaError_t launch_zero_batch(double *const *rhs_dev, const int64_t *len_dev, int n_meshes, cudaStream_t s);
-cudaError_t launch_tet_pipe(const BucketDev &b, const FieldDev &f, const AsmArgs &a, int threads, int sms,
-                           cudaStream_t s);
-size_t tet_pipe_smem_bytes(const BucketDev &b);
+cudaError_t launch_tet_ws(const BucketDev &b, const FieldDev &f, const AsmArgs &a, int sms, cudaStream_t s);
+size_t tet_ws_smem_bytes(int nw, int lmp);
 constexpr int lconn_pitch(int etype) { return etype == FEA_TET04 ? 4 : 8; }
 cudaError_t launch_lumped_mass(const BucketDev &b, const double *xyz64, int64_t n, double *mass, unsigned *err,
                                unsigned long long *bad, cudaStream_t s);
 cudaError_t launch_fold(const int32_t *slaves, const int32_t *masters, int64_t n_slaves, double *v, int ncomp,
                         int64_t n, cudaStream_t s);
-cudaError_t launch_rk_update(int64_t n, const double *un, double *uk, double *un_out, const double *rhs,
-                             const double *minv, const uint8_t *dirichlet, const double *p64, float4 *up32,
-                             double a, double b, double dt, cudaStream_t s);
+// stage update: reads u^n (un) and u^(k) (uk_in), writes the result to
+// uk_out (and un_out if not NULL); the three may alias
+cudaError_t launch_rk_update(int64_t n, const double *un, const double *uk_in, double *uk_out, double *un_out,
+                             const double *rhs, const double *minv, const uint8_t *dirichlet, const double *p64,
+                             float4 *up32, double a, double b, double dt, cudaStream_t s);
 cudaError_t launch_pack_field(int64_t n, const double *u64, const double *p64, float4 *up32, cudaStream_t s);
 // wall-model boundary term (fea_wall.cu): faces [nv][n_faces] and their
 // exchange nodes, FP64; adds into rhs [3][n]
@@ -216,6 +243,9 @@ fea_status stage_with_scratch(fea_ctx *ctx, int32_t mesh, int32_t stage, double 
                               const double *p, double *uk_out, double *rhs, float4 *up, int64_t max_nodes,
                               cudaStream_t s);
 int context_device(const fea_ctx *ctx);
+// device address of the allocation-free stage's static scratch on `device`
+// (fea_noalloc.cu); looked up once per device, first at fea_create
+cudaError_t noalloc_scratch_address(int device, void **out);
 fea_status context_fail(fea_ctx *ctx, fea_status st, const char *msg);
 
 }  // namespace fea

@@ -1451,8 +1451,7 @@ cudaError_t launch_zero_batch(double *const *rhs_dev, const int64_t *len_dev, in
 
 
 size_t chunk_kernel_smem(const BucketDev &b, int compensated) {
-    if (b.etype == FEA_TET04 && !b.fp64j && !compensated && tet_pipe_smem_bytes(b) <= kChunkSmemLimit)
-        return tet_pipe_smem_bytes(b);
+    (void)compensated;
     return chunk_smem_bytes(b);
 }
 
@@ -1512,8 +1511,9 @@ cudaError_t launch_assemble_chunk(const BucketDev &b, const FieldDev &f, const A
     if (b.count == 0) return cudaSuccess;
     if (!b.lconn || b.n_chunks <= 0) return cudaErrorInvalidValue;
     if (b.etype == FEA_TET04 && !b.fp64j && !compensated && a.closure != FEA_CLOSURE_MLP && f.conv_form == 0 &&
-        f.delta_form == 0 && tet_pipe_smem_bytes(b) <= kChunkSmemLimit)
-        return launch_tet_pipe(b, f, a, threads, 0, s);
+        f.delta_form == 0) {
+        if (b.ws_rec) return launch_tet_ws(b, f, a, 0, s);
+    }
     if (threads > 256) threads = 256;
     switch (b.etype) {
         case FEA_TET04:
@@ -1616,8 +1616,11 @@ cudaError_t launch_fold(const int32_t *slaves, const int32_t *masters, int64_t n
 // A0: a = 0 (first stage) reads no u^n except at held nodes.  One node per
 // thread, every load of the node issued before any is used (the hold flag
 // only selects), so that each warp has all its streams in flight at once.
+// un, uk_in and uk_out may alias one another (the last stage writes u^(n+1)
+// over u^n; an in-place stage writes over u^(k)): every thread reads its own
+// index of each before it writes it, so they carry no __restrict__.
 template <bool A0>
-__global__ void __launch_bounds__(256) k_rk_update(int64_t n, const double *__restrict__ un, double *uk,
+__global__ void __launch_bounds__(256) k_rk_update(int64_t n, const double *un, const double *uk_in, double *uk_out,
                                                    double *un_out, const double *__restrict__ rhs,
                                                    const double *__restrict__ minv,
                                                    const uint8_t *__restrict__ dirichlet,
@@ -1632,37 +1635,33 @@ __global__ void __launch_bounds__(256) k_rk_update(int64_t n, const double *__re
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         r[q] = __ldg(&rhs[(int64_t)q * n + i]);
-        k[q] = uk[(int64_t)q * n + i];
-        o[q] = A0 ? 0.0 : __ldg(&un[(int64_t)q * n + i]);
+        k[q] = uk_in[(int64_t)q * n + i];
+        o[q] = (A0 && !hold) ? 0.0 : un[(int64_t)q * n + i];
     }
     double v[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) v[q] = A0 ? fma(c, r[q], k[q]) : fma(c, r[q], fma(a, o[q], b * k[q]));
-    if (hold) {
-#pragma unroll
-        for (int q = 0; q < 3; ++q) v[q] = A0 ? __ldg(&un[(int64_t)q * n + i]) : o[q];
-    }
+    for (int q = 0; q < 3; ++q) v[q] = hold ? o[q] : (A0 ? fma(c, r[q], k[q]) : fma(c, r[q], fma(a, o[q], b * k[q])));
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        uk[(int64_t)q * n + i] = v[q];
+        uk_out[(int64_t)q * n + i] = v[q];
         if (un_out) un_out[(int64_t)q * n + i] = v[q];
     }
     up32[i] = make_float4(f64_to_f32_rn(v[0]), f64_to_f32_rn(v[1]), f64_to_f32_rn(v[2]), f64_to_f32_rn(pi));
 }
 
-cudaError_t launch_rk_update(int64_t n, const double *un, double *uk, double *un_out, const double *rhs,
-                             const double *minv, const uint8_t *dirichlet, const double *p64, float4 *up32, double a,
-                             double b, double dt, cudaStream_t s) {
+cudaError_t launch_rk_update(int64_t n, const double *un, const double *uk_in, double *uk_out, double *un_out,
+                             const double *rhs, const double *minv, const uint8_t *dirichlet, const double *p64,
+                             float4 *up32, double a, double b, double dt, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const int t = 256;
     const int64_t blocks = (n + t - 1) / t;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (a == 0.0 && b == 1.0)
-        k_rk_update<true><<<(unsigned)blocks, t, 0, s>>>(n, un, uk, un_out, rhs, minv, dirichlet, p64, up32, a, b,
-                                                         b * dt);
+        k_rk_update<true><<<(unsigned)blocks, t, 0, s>>>(n, un, uk_in, uk_out, un_out, rhs, minv, dirichlet, p64,
+                                                         up32, a, b, b * dt);
     else
-        k_rk_update<false><<<(unsigned)blocks, t, 0, s>>>(n, un, uk, un_out, rhs, minv, dirichlet, p64, up32, a, b,
-                                                          b * dt);
+        k_rk_update<false><<<(unsigned)blocks, t, 0, s>>>(n, un, uk_in, uk_out, un_out, rhs, minv, dirichlet, p64,
+                                                          up32, a, b, b * dt);
     return cudaGetLastError();
 }
 

@@ -5,8 +5,10 @@
 // let the library allocate per call.  fea_rk_stage_noalloc keeps its
 // per-call scratch -- the intermediate FP64 right-hand side and the FP32
 // packed copy of the stage velocity and pressure -- in one file-scope device
-// array of fixed size, reserved when the library's device code is loaded on
-// a GPU and held until the process exits.
+// array of fixed size.  The array belongs to this file's device module, which
+// CUDA loads lazily; fea_create looks up its address on the context's
+// device, so the module is loaded and the array reserved at set-up, and held
+// until the process exits.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,7 +29,10 @@ constexpr int kMaxDevices = 64;
 void *g_scratch_dev[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
-cudaError_t scratch_address(int device, void **out) {
+}  // namespace
+
+cudaError_t fea::noalloc_scratch_address(int device, void **out) {
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (!g_scratch_dev[device]) {
         int prev = 0;
@@ -44,8 +49,6 @@ cudaError_t scratch_address(int device, void **out) {
     return cudaSuccess;
 }
 
-}  // namespace
-
 extern "C" fea_status fea_rk_stage_noalloc(fea_ctx *ctx, int32_t mesh, int32_t stage, double dt, fea_prec prec,
                                            fea_closure closure, double nu, double c_vreman, const double *un,
                                            const double *uk, const double *p, double *uk_out, void *stream) {
@@ -53,7 +56,7 @@ extern "C" fea_status fea_rk_stage_noalloc(fea_ctx *ctx, int32_t mesh, int32_t s
     const int device = fea::context_device(ctx);
     if (device < 0 || device >= kMaxDevices) return fea::context_fail(ctx, FEA_EINVAL, "device ordinal out of range");
     void *base = nullptr;
-    cudaError_t e = scratch_address(device, &base);
+    cudaError_t e = fea::noalloc_scratch_address(device, &base);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fea::context_fail(ctx, FEA_ECUDA, cudaGetErrorString(e));

@@ -35,7 +35,7 @@ EXPORTED = (
     "fea_mlp_fallback_read", "fea_sfc_order", "fea_partition_sfc", "fea_interface_pack", "fea_interface_unpack",
     "fea_poisson_setup", "fea_poisson_solve", "fea_divergence", "fea_gradient", "fea_project",
     "fea_balance_update", "fea_set_model", "fea_wall_setup", "fea_wall_assemble", "fea_autotune_batched",
-    "fea_colour_elements",
+    "fea_colour_elements", "fea_set_wait_limit",
 )
 MLP_NPARAM = 8833
 NOALLOC_MAX_NODES = 262144
@@ -189,6 +189,7 @@ def lib() -> ctypes.CDLL:
         L.fea_set_plan.argtypes = [vp, i32, ctypes.POINTER(Plan)]
         L.fea_autotune.argtypes = [vp, i32, ctypes.c_int, ctypes.c_int, ctypes.c_char_p]
         L.fea_sync_status.argtypes = [vp, vp]
+        L.fea_set_wait_limit.argtypes = [vp, ctypes.c_uint32]
         L.fea_profile_enable.argtypes = [vp, ctypes.c_int]
         L.fea_mlp_load.argtypes = [vp, vp, vp, vp, dbl, vp]
         L.fea_mlp_get.argtypes = [vp, vp, vp]
@@ -414,6 +415,12 @@ class Context:
 
     def sync_status(self, stream=None):
         self.check(self._lib.fea_sync_status(self.handle, _stream(stream)))
+
+    def set_wait_limit(self, polls: int):
+        """Poll limit of the TET04 kernel's bounded device waits (0: default)."""
+        if not 0 <= int(polls) < 2 ** 32:
+            raise ValueError("polls must fit in 32 bits")
+        self.check(self._lib.fea_set_wait_limit(self.handle, int(polls)))
 
     def upload_mesh(self, mesh, stream=None) -> "DeviceMesh":
         """mesh: meshgen.Mesh-like object (xyz (N,3), conn dict, optional

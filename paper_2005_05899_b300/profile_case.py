@@ -29,6 +29,7 @@ def main(argv=None) -> int:
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--rk3", action="store_true")
+    ap.add_argument("--time", type=int, default=0, help="then time this many assemblies per category")
     ap.add_argument("--closure", choices=["vreman", "mlp"], default="vreman")
     ap.add_argument("--project-iters", type=int, default=0,
                     help="instead of assemblies: Laplacian set-up, then projections of this many CG iterations")
@@ -77,6 +78,21 @@ def main(argv=None) -> int:
     torch.cuda.synchronize()
     ctx.sync_status()
     print(f"ok {m.counts()} {a.reps} reps {time.time() - t:.3f}s", flush=True)
+    if a.time:
+        # each category's kernels alone on the stream, timed with CUDA events
+        ctx.profile(True)
+        ctx.profile_read(0, 0, reset=True)
+        for _ in range(a.time):
+            dm.assemble(out, prec=a.prec, closure=a.closure)
+        torch.cuda.synchronize()
+        ctx.sync_status()
+        for et, name in enumerate(("TET04", "PYR05", "PEN06", "HEX08")):
+            for fj in (0, 1):
+                ms, n = ctx.profile_read(et, fj, reset=False)
+                if n:
+                    print(f"time {name}{' fp64J' if fj else ''}: {ms / n:.4f} ms per launch ({n} launches, "
+                          f"{m.counts()[name] / (ms / n) / 1e3:.0f} Melem/s of that type)", flush=True)
+        ctx.profile(False)
     return 0
 
 

@@ -47,5 +47,6 @@ def test_null_arguments_rejected_without_device():
     lib = fea.lib()
     assert lib.fea_create(0, None) == fea.EINVAL
     assert lib.fea_sync_status(None, None) == fea.EINVAL
+    assert lib.fea_set_wait_limit(None, 5) == fea.EINVAL
     assert lib.fea_last_error(None) == b"null context"
     lib.fea_destroy(None)

@@ -254,7 +254,10 @@ def test_mlp_envelope_falls_back_to_vreman(ctx):
     r, n = run("mlp")
     assert np.array_equal(r, r_mlp) and np.array_equal(n, n_mlp)
     assert ctx.mlp_fallback_read(reset=True) == 0
-    # an empty envelope gives the Vreman assembly at every Gauss point
+    # an empty envelope gives the Vreman assembly at every Gauss point (up
+    # to FP32 rounding: the Vreman path's TET04 kernel works on coordinates
+    # relative to the chunks of its own tables, whose origins differ from
+    # the fused kernel's, hence 1e-5 and not bitwise)
     ctx.mlp_set_envelope(np.full(6, 1e30), np.full(6, -1e30))
     r, n = run("mlp")
     assert ctx.mlp_fallback_read(reset=True) == NG
@@ -276,6 +279,6 @@ def test_mlp_envelope_falls_back_to_vreman(ctx):
     assert abs(count - int((~inside).sum())) <= int((~clear).sum())
     a, b = clear & inside, clear & ~inside
     assert np.all(np.abs(n[a] - n_mlp[a]) <= 1e-6 * np.abs(n_mlp[a]) + 1e-12)
-    assert np.all(np.abs(n[b] - n_vre[b]) <= 1e-6 * np.abs(n_vre[b]) + 1e-12)
+    assert np.all(np.abs(n[b] - n_vre[b]) <= 1e-5 * np.abs(n_vre[b]) + 1e-12)
     assert 0.2 * NG < count < 0.4 * NG
     ctx.mlp_set_envelope(None, None)
