@@ -80,6 +80,21 @@ def tet_algorithmic_bytes(mesh) -> tuple:
 TET_FLOPS = 411
 
 
+def elem_flops(nen: int, ng: int) -> int:
+    """FP32 operations of one element assembly by the per-Gauss-point method
+    of the generic kernels (a multiply-add counts 2), per Gauss point:
+    Jacobian 18 nen, its determinant, adjugate and inverse 42, weight 1,
+    Cartesian derivatives 18 nen, u_g / G / grad p 30 nen, Vreman 66,
+    convective vector 26, strain and stress coefficients 12, the residual
+    rows 24 nen (N_a (c + grad p) and the stress term, 3 components); plus
+    the element's filter width 5 (sum of weights, cube root, square)."""
+    return ng * (90 * nen + 147) + 5
+
+
+ELEM_FLOPS = {"TET04": elem_flops(4, 4), "PYR05": elem_flops(5, 8), "PEN06": elem_flops(6, 6),
+              "HEX08": elem_flops(8, 8)}
+
+
 def max_over_ranks(values, ws: int, device: str = "cuda"):
     """Element-wise maximum of `values` over the ranks (the slowest rank sets
     the time of a weak-scaling run); the values themselves when ws == 1."""
@@ -98,11 +113,18 @@ def peaks():
     return 6400.0, "fallback", 2032.0
 
 
-def fp32_peak_tflops(sm_mhz: float) -> float:
-    """FP32 roof: SMs x 128 FP32 lanes x 2 (multiply-add) x the maximum SM clock."""
+def fp32_derived(sm_mhz: float) -> float:
+    """FP32 figure from unit counts: SMs x 128 FP32 lanes x 2 (multiply-add) x SM clock (context only)."""
     import torch
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fp32_peak_tflops(ctx) -> dict:
+    """FP32 roof measured on this GPU by the library's FMA-chain kernel
+    (fea_fp32_peak): scalar FFMA and paired FFMA2, the larger is the peak."""
+    a, b = ctx.fp32_peak()
+    return {"ffma": a, "ffma2": b, "peak": max(a, b)}
 
 
 def kernel_source_hash() -> str:
@@ -259,6 +281,98 @@ def cpu_baseline(mesh, field, target_s: float = 12.0):
     v, cores, desc, _ = sampler.run(target_s)
     return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
             "serial_value": sampler.serial(), "cpu_model": cpu_model()}
+
+
+def _timed(fn, reps: int) -> float:
+    """ms per call of fn, CUDA events on the current stream after 3 warm-up calls."""
+    import torch
+    for _ in range(3):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def secondary_channel(ctx, peak_tflops: float, reps: int = 10) -> dict:
+    """The mixed-type channel (128x64x64 cells, 942,079 elements): one
+    mixed-precision assembly with the Vreman closure, autotuned plan."""
+    import torch
+    from paper_2005_05899_b300 import meshgen as mg
+    m = mg.channel_mesh()
+    f = mg.channel_field(m)
+    dm = ctx.upload_mesh(m)
+    dm.upload_field(f.u, f.p, f.nu, f.c_vreman)
+    plan = dm.autotune(prec="mixed", closure="vreman").as_dict()
+    out = torch.empty((3, dm.n_nodes), dtype=torch.float64, device="cuda")
+    ms = _timed(lambda: dm.assemble(out), reps)
+    ctx.sync_status()
+    counts = m.counts()
+    flops = sum(ELEM_FLOPS[t] * n for t, n in counts.items())
+    E = m.n_elem_total
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"workload": "channel 4pi x 2 x 2pi, 128x64x64 cells, stretched wall layers as PEN06 (FP64 Jacobian), "
+                        "10% split cells as PYR05 + TET04", "counts": counts, "elements": E, "plan": plan,
+            "assemble_ms": ms, "melem_s": E / ms / 1e3, "fp32_tflops": achieved,
+            "fp32_frac": achieved / peak_tflops, "flops_per_elem": ELEM_FLOPS,
+            "flops_note": "algorithmic FP32 operations of the per-Gauss-point method (bench.elem_flops); the "
+                          "FP64 Jacobians of the prisms are not counted"}
+
+
+def secondary_batch(ctx, reps: int = 5) -> dict:
+    """64 channel-like meshes of log-uniform 1e4-5e5 elements in one
+    persistent launch (the batch autotuner's plan)."""
+    import torch
+    from paper_2005_05899_b300 import meshgen as mg
+    meshes = mg.batch_meshes(count=64, seed=7)
+    dms, outs = [], []
+    E = 0
+    for m, f in meshes:
+        dm = ctx.upload_mesh(m)
+        dm.upload_field(f.u, f.p, f.nu, f.c_vreman)
+        dms.append(dm)
+        outs.append(torch.empty((3, dm.n_nodes), dtype=torch.float64, device="cuda"))
+        E += m.n_elem_total
+    best = ctx.autotune_batched(dms)
+    l0 = ctx.launch_count
+    ms = _timed(lambda: ctx.assemble_batched(dms, outs), reps)
+    launches = (ctx.launch_count - l0) / (reps + 3)
+    ctx.sync_status()
+    return {"workload": "64 channel-like mixed meshes, log-uniform 1e4-5e5 elements, own field and nu each",
+            "elements": E, "plan": best.as_dict(), "assemble_ms": ms, "melem_s": E / ms / 1e3,
+            "launches_per_call": launches}
+
+
+def sampled_error(ctx, dm, mesh, field, n_sample: int = 3000, seed: int = 0) -> dict:
+    """Error of the headline RHS (one mixed assembly, the plan in use) against
+    the FP64 oracle at n_sample random nodes: the oracle assembles only the
+    elements incident to those nodes (their RHS is then complete)."""
+    import torch
+    import oracle as O
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(mesh.n_nodes, size=n_sample, replace=False))
+    mark = np.zeros(mesh.n_nodes, bool)
+    mark[pick] = True
+    sub = {t: c[mark[c].any(axis=1)] for t, c in mesh.conn.items()}
+    used = np.unique(np.concatenate([c.ravel() for c in sub.values()]))
+    remap = np.full(mesh.n_nodes, -1, np.int64)
+    remap[used] = np.arange(used.size)
+    om = O.OracleMesh(mesh.xyz[used], {t: remap[c].astype(np.int32) for t, c in sub.items()})
+    ref = O.assemble_rhs(om, field.u[used], field.p[used], field.nu, field.c_vreman, "vreman")[remap[pick]]
+    out = torch.empty((3, dm.n_nodes), dtype=torch.float64, device="cuda")
+    dm.upload_field(field.u, field.p, field.nu, field.c_vreman)   # the timed steps advanced the state
+    dm.assemble(out, prec="mixed", closure="vreman")
+    ctx.sync_status()
+    got = out[:, torch.from_numpy(pick).cuda()].cpu().numpy().T
+    d = got - ref
+    return {"rel_l2": float(np.linalg.norm(d) / np.linalg.norm(ref)),
+            "max_norm": float(np.abs(d).max() / np.abs(ref).max()), "nodes": n_sample,
+            "against": "FP64 oracle on the elements incident to the sampled nodes", "tolerance": {"rel_l2": 2e-5,
+                                                                                              "max_norm": 2e-4}}
 
 
 def run_reference(args):
@@ -428,12 +542,13 @@ def run_ours(args):
     e2e_val = ws * 3 * E * e2e_steps / (e2e_ms / 1e3) / 1e6
     e2e_serial = ws * 3 * E * e2e_steps / (e2e_serial_ms / 1e3) / 1e6
     # roofline of the TET04 kernel: its arithmetic intensity (411 FLOP per
-    # 24.8 algorithmic bytes) is above the FP32 ridge point (77 TFLOP/s over
-    # 6.5 TB/s = 11.8 FLOP/B), so the FP32 roof bounds it; the HBM fraction
-    # is reported beside it
+    # 24.8 algorithmic bytes) is above the FP32 ridge point (about 70 TFLOP/s
+    # measured over 6.5 TB/s = 10.8 FLOP/B), so the FP32 roof bounds it; the
+    # HBM fraction is reported beside it
     alg, e_tet, n_tet = tet_algorithmic_bytes(mesh)
     hbm_peak, peak_kind, sm_max = peaks()
-    alu_peak = fp32_peak_tflops(sm_max)
+    fp32 = fp32_peak_tflops(ctx)
+    alu_peak = fp32["peak"]
     per_launch_s = tet_ms / 1e3 / max(tet_n, 1)
     achieved = TET_FLOPS * e_tet / per_launch_s / 1e12
     achieved_gbs = alg / per_launch_s / 1e9
@@ -446,7 +561,9 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU", "plan": plan.as_dict()},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak, "traffic": traffic, "kernel": "TET04 assembly (mixed, Vreman)",
-                         "peak_kind": f"derived FP32: SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
+                         "peak_kind": "measured FP32: the library's FMA-chain kernel (fea_fp32_peak), the larger "
+                                      "of scalar FFMA and paired FFMA2",
+                         "fp32_peaks": {**fp32, "derived_max_clock": fp32_derived(sm_max)},
                          "alg_flops_per_elem": TET_FLOPS, "alg_bytes_per_launch": alg,
                          "kernel_ms": per_launch_s * 1e3, "kernel_melem_s": e_tet / per_launch_s / 1e6,
                          "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
@@ -456,7 +573,13 @@ def run_ours(args):
                     "streams while step k computes (double-buffered device staging)",
                     "serial_value": e2e_serial},
             "gpu_launches": launches, "clocks": clk}
+    if rank == 0 and not args.no_secondary:
+        t = time.time()
+        line["secondary"] = {"channel": secondary_channel(ctx, alu_peak), "batch": secondary_batch(ctx)}
+        log(f"[bench] secondary configs {time.time() - t:.1f}s")
     if rank == 0 and ws == 1 and not args.no_cpu:
+        # the CPU leg: the oracle's error of the headline RHS, then its rate
+        line["error"] = sampled_error(ctx, dm, mesh, field)
         line["cpu_baseline"] = cpu_baseline(mesh, field, target_s=args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -477,7 +600,8 @@ def main():
                     help="keep the default launch plan instead of timing the candidates")
     ap.add_argument("--plan", default="", help="fixed launch plan scatter:threads:chunk_elems:chunk_acc "
                     "(e.g. chunk:128:256:0) instead of autotuning")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline and the oracle error")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the channel and batch measurements")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
     if args.warmup < 3:

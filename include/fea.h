@@ -507,6 +507,15 @@ fea_status fea_autotune(fea_ctx *ctx, int32_t mesh, fea_prec prec, fea_closure c
  * FEA_ETIMEOUT (bounded wait gave up), or FEA_OK. */
 fea_status fea_sync_status(fea_ctx *ctx, void *stream);
 
+/* Measured FP32 arithmetic peak of the context's device (a measurement
+ * utility; the paper has no counterpart): every thread runs eight
+ * independent multiply-add chains, scalar FFMA or paired FFMA2 on float2, 8
+ * CTAs of 256 threads per SM; the best of three timed launches (CUDA events
+ * on `stream`, after one warm-up launch) of each kind, a multiply-add
+ * counting two operations.  *tflops_ffma, *tflops_ffma2: host outputs in
+ * TFLOP/s.  Synchronous; allocates 4 bytes of device memory for the call. */
+fea_status fea_fp32_peak(fea_ctx *ctx, double *tflops_ffma, double *tflops_ffma2, void *stream);
+
 /* Poll limit of the bounded device-side waits of the TET04 assembly kernel
  * (mixed precision, chunk scatter), which otherwise give up after about four
  * million polls of an mbarrier phase, each of which may suspend the warp for

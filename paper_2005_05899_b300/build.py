@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfea.so")
-SOURCES = ["fea_api.cu", "fea_kernels.cu", "fea_tet_ws.cu", "fea_noalloc.cu", "fea_mlp.cu", "fea_partition.cu", "fea_poisson.cu",
+SOURCES = ["fea_api.cu", "fea_kernels.cu", "fea_tet_ws.cu", "fea_peak.cu", "fea_noalloc.cu", "fea_mlp.cu", "fea_partition.cu", "fea_poisson.cu",
            "fea_wall.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -2110,6 +2110,14 @@ fea_status fea_profile_read(fea_ctx *ctx, int etype, int fp64_jac, double *total
     return FEA_OK;
 }
 
+fea_status fea_fp32_peak(fea_ctx *ctx, double *tflops_ffma, double *tflops_ffma2, void *stream) {
+    if (!ctx) return FEA_EINVAL;
+    if (!tflops_ffma || !tflops_ffma2) return fail(ctx, FEA_EINVAL, "null output");
+    CK(measure_fp32_peak(ctx->sms, (cudaStream_t)stream, tflops_ffma, tflops_ffma2));
+    ctx->launches += 8;
+    return FEA_OK;
+}
+
 fea_status fea_set_wait_limit(fea_ctx *ctx, uint32_t polls) {
     if (!ctx) return FEA_EINVAL;
     ctx->wait_polls = polls;

@@ -172,6 +172,9 @@ cudaError_t launch_wall(const WallDev &w, const double *xyz64, const double *u64
                         unsigned *err, bool fp64, cudaStream_t s);
 cudaError_t launch_f32_to_f64(const float *src, double *dst, int64_t count, cudaStream_t s);
 cudaError_t launch_recip(const double *m, double *minv, int64_t n, cudaStream_t s);
+// FP32 FMA-chain peak (fea_peak.cu): TFLOP/s of scalar FFMA and of paired
+// FFMA2, best of three timed launches each on stream s (synchronous)
+cudaError_t measure_fp32_peak(int sms, cudaStream_t s, double *tflops_ffma, double *tflops_ffma2);
 
 // pressure projection element operators (fea_kernels.cu), FP64
 cudaError_t launch_lap_assemble(const BucketDev &b, const double *xyz, int64_t n, const int32_t *cls,

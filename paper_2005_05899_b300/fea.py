@@ -35,7 +35,7 @@ EXPORTED = (
     "fea_mlp_fallback_read", "fea_sfc_order", "fea_partition_sfc", "fea_interface_pack", "fea_interface_unpack",
     "fea_poisson_setup", "fea_poisson_solve", "fea_divergence", "fea_gradient", "fea_project",
     "fea_balance_update", "fea_set_model", "fea_wall_setup", "fea_wall_assemble", "fea_autotune_batched",
-    "fea_colour_elements", "fea_set_wait_limit",
+    "fea_colour_elements", "fea_set_wait_limit", "fea_fp32_peak",
 )
 MLP_NPARAM = 8833
 NOALLOC_MAX_NODES = 262144
@@ -190,6 +190,7 @@ def lib() -> ctypes.CDLL:
         L.fea_autotune.argtypes = [vp, i32, ctypes.c_int, ctypes.c_int, ctypes.c_char_p]
         L.fea_sync_status.argtypes = [vp, vp]
         L.fea_set_wait_limit.argtypes = [vp, ctypes.c_uint32]
+        L.fea_fp32_peak.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp]
         L.fea_profile_enable.argtypes = [vp, ctypes.c_int]
         L.fea_mlp_load.argtypes = [vp, vp, vp, vp, dbl, vp]
         L.fea_mlp_get.argtypes = [vp, vp, vp]
@@ -415,6 +416,12 @@ class Context:
 
     def sync_status(self, stream=None):
         self.check(self._lib.fea_sync_status(self.handle, _stream(stream)))
+
+    def fp32_peak(self, stream=None):
+        """Measured FP32 peak (TFLOP/s) as (scalar FFMA, paired FFMA2)."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self.check(self._lib.fea_fp32_peak(self.handle, ctypes.byref(a), ctypes.byref(b), _stream(stream)))
+        return a.value, b.value
 
     def set_wait_limit(self, polls: int):
         """Poll limit of the TET04 kernel's bounded device waits (0: default)."""
