@@ -347,6 +347,62 @@ def secondary_batch(ctx, reps: int = 5) -> dict:
             "launches_per_call": launches}
 
 
+CLOSURE_WEIGHTS = os.path.join(ROOT, "paper_2005_05899_b300", "closure_tgv256.npz")
+
+
+def secondary_closure(ctx, reps: int = 5, dims=(269, 134, 135)) -> dict:
+    """The learned closure (network trained on box-filtered 256^3 Taylor-Green
+    runs of the plain method by paper_2005_05899_b300.bench_configs --closure
+    --save, stored in the package) fused into the assembly of the 8M-element
+    mixed channel against the Vreman path on the same GPU: time per
+    assembly, share of Gauss points that fall back to Vreman (outside the
+    training envelope), and the relative L2 differences of nu_t, of the RHS
+    and of its subgrid term."""
+    import torch
+    from paper_2005_05899_b300 import fea
+    from paper_2005_05899_b300 import meshgen as mg
+    w = np.load(CLOSURE_WEIGHTS)
+    ctx.mlp_load(w["theta"], w["mean"], w["std"], float(w["scale"]))
+    ctx.mlp_set_envelope(w["env_lo"], w["env_hi"])
+    m = mg.channel_mesh(*dims)
+    f = mg.channel_field(m, nu=1.0 / 5600.0)
+    dm = ctx.upload_mesh(m)
+    dm.upload_field(f.u, f.p, f.nu, f.c_vreman)
+    N, NG, E = dm.n_nodes, dm.n_gauss_total, m.n_elem_total
+    res = {}
+    for k in ("vreman", "mlp"):
+        plan = dm.autotune(prec="mixed", closure=k).as_dict()
+        rhs = torch.empty((3, N), dtype=torch.float64, device="cuda")
+        ms = _timed(lambda: dm.assemble(rhs, prec="mixed", closure=k), reps)
+        ctx.sync_status()
+        nut = torch.empty(NG, dtype=torch.float32, device="cuda")
+        sgs = torch.empty((3, N), dtype=torch.float64, device="cuda")
+        ctx.mlp_fallback_read(reset=True)
+        dm.assemble(rhs, prec="mixed", closure=k, nut_out=nut)
+        ctx.sync_status()
+        fb = ctx.mlp_fallback_read(reset=True) / NG if k == "mlp" else None
+        dm.assemble(sgs, prec="mixed", closure=k, mask=fea.TERM_SGS)
+        ctx.sync_status()
+        res[k] = {"ms": ms, "melem_s": E / ms / 1e3, "plan": plan, "rhs": rhs, "nut": nut, "sgs": sgs,
+                  "fallback": fb}
+
+    def rel(a, b):
+        return float(torch.linalg.norm((a - b).double()) / torch.linalg.norm(b.double()))
+
+    v, n = res["vreman"], res["mlp"]
+    out = {"workload": f"learned closure (6-64-64-64-1 SiLU MLP on dimensionless invariants and log(Delta^2|G|/nu), "
+                       f"trained on filtered 256^3 Taylor-Green runs) fused into the {dims[0]}x{dims[1]}x{dims[2]} "
+                       f"mixed channel ({E:,} elements, {NG:,} Gauss points), against Vreman",
+           "vreman_ms": v["ms"], "mlp_ms": n["ms"], "mlp_over_vreman_time": n["ms"] / v["ms"],
+           "melem_s": {"vreman": v["melem_s"], "mlp": n["melem_s"]}, "plans": {"vreman": v["plan"], "mlp": n["plan"]},
+           "fallback_frac": n["fallback"],
+           "nut_mean": {"vreman": float(v["nut"].double().mean()), "mlp": float(n["nut"].double().mean())},
+           "nut_rel_l2_vs_vreman": rel(n["nut"], v["nut"]), "rhs_rel_l2_vs_vreman": rel(n["rhs"], v["rhs"]),
+           "sgs_rel_l2_vs_vreman": rel(n["sgs"], v["sgs"])}
+    ctx.mlp_set_envelope(None, None)
+    return out
+
+
 def sampled_error(ctx, dm, mesh, field, n_sample: int = 3000, seed: int = 0) -> dict:
     """Error of the headline RHS (one mixed assembly, the plan in use) against
     the FP64 oracle at n_sample random nodes: the oracle assembles only the
@@ -575,7 +631,8 @@ def run_ours(args):
             "gpu_launches": launches, "clocks": clk}
     if rank == 0 and not args.no_secondary:
         t = time.time()
-        line["secondary"] = {"channel": secondary_channel(ctx, alu_peak), "batch": secondary_batch(ctx)}
+        line["secondary"] = {"channel": secondary_channel(ctx, alu_peak), "batch": secondary_batch(ctx),
+                             "closure": secondary_closure(ctx)}
         log(f"[bench] secondary configs {time.time() - t:.1f}s")
     if rank == 0 and ws == 1 and not args.no_cpu:
         # the CPU leg: the oracle's error of the headline RHS, then its rate

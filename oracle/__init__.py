@@ -233,10 +233,12 @@ def vreman(G: np.ndarray, delta: float, c: float) -> float:
     return float(lib().orc_vreman(_dp(G), ctypes.c_double(delta), ctypes.c_double(c)))
 
 
-def mlp_features(G: np.ndarray, delta: float) -> np.ndarray:
+def mlp_features(G: np.ndarray, delta: float, nu: float) -> np.ndarray:
+    """The closure's six dimensionless inputs of one velocity gradient G (3x3),
+    filter width delta and viscosity nu (see orc_mlp_features)."""
     G = np.ascontiguousarray(G, dtype=np.float64).reshape(9)
     x = np.zeros(6)
-    lib().orc_mlp_features(_dp(G), ctypes.c_double(delta), _dp(x))
+    lib().orc_mlp_features(_dp(G), ctypes.c_double(delta), ctypes.c_double(nu), _dp(x))
     return x
 
 

@@ -80,7 +80,7 @@ typedef struct {
     const double *w4, *b4;    /* [64], [1] */
     const double *feat_mean;  /* [6] */
     const double *feat_std;   /* [6] */
-    double out_scale;         /* nu_t = out_scale * softplus(z) */
+    double out_scale;         /* coefficient C = out_scale * softplus(z); nu_t = C Delta^2 |G| */
 } orc_mlp;
 
 typedef struct {
@@ -360,35 +360,47 @@ static void mat3mul(const double A[3][3], const double B[3][3], double C[3][3]) 
 
 static double tr3(const double A[3][3]) { return A[0][0] + A[1][1] + A[2][2]; }
 
-static double signed_root(double v, double d) {
-    if (v == 0.0) return 0.0;
-    return (v > 0.0 ? 1.0 : -1.0) * pow(fabs(v), 1.0 / d);
-}
-
-void orc_mlp_features(const double *G, double delta, double *x /*[6]*/) {
+/* Dimensionless inputs of the learned closure (reading of config 5's "five
+ * invariants of the velocity-gradient tensor plus the element size", made
+ * scale-free): with S = (G + G^T)/2, O = (G - G^T)/2 and g = |G| (Frobenius,
+ * g^2 = tr S^2 - tr O^2),
+ *   x = (tr S^2 / g^2, tr O^2 / g^2, tr S^3 / g^3, tr S O^2 / g^3,
+ *        tr S^2 O^2 / g^4, log(Delta^2 g / nu)),
+ * the last the element's Reynolds number.  A vanishing gradient (g = 0) has
+ * no direction: x = 0 (and the closure is zero there).  Returns g.        */
+double orc_mlp_features(const double *G, double delta, double nu, double *x /*[6]*/) {
     double S[3][3], O[3][3], S2[3][3], O2[3][3], S3[3][3], SO2[3][3], S2O2[3][3];
+    double g2 = 0.0;
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
             S[i][j] = 0.5 * (G[3 * i + j] + G[3 * j + i]);
             O[i][j] = 0.5 * (G[3 * i + j] - G[3 * j + i]);
+            g2 += G[3 * i + j] * G[3 * i + j];
         }
+    if (!(g2 > 0.0)) {
+        for (int k = 0; k < MLP_IN; ++k) x[k] = 0.0;
+        return 0.0;
+    }
+    const double g = sqrt(g2);
     mat3mul(S, S, S2);
     mat3mul(O, O, O2);
     mat3mul(S2, S, S3);
     mat3mul(S, O2, SO2);
     mat3mul(S2, O2, S2O2);
-    x[0] = signed_root(tr3(S2), 2.0);
-    x[1] = signed_root(tr3(O2), 2.0);
-    x[2] = signed_root(tr3(S3), 3.0);
-    x[3] = signed_root(tr3(SO2), 3.0);
-    x[4] = signed_root(tr3(S2O2), 4.0);
-    x[5] = log(delta);
+    x[0] = tr3(S2) / g2;
+    x[1] = tr3(O2) / g2;
+    x[2] = tr3(S3) / (g2 * g);
+    x[3] = tr3(SO2) / (g2 * g);
+    x[4] = tr3(S2O2) / (g2 * g2);
+    x[5] = log(delta * delta * g / nu);
+    return g;
 }
 
 static double silu(double z) { return z / (1.0 + exp(-z)); }
 static double softplus(double z) { return z > 30.0 ? z : log1p(exp(z)); }
 
-/* Forward pass for a batch of raw (un-normalised) features; y = nu_t. */
+/* Forward pass for a batch of raw (un-normalised) features; y = the
+ * coefficient C = out_scale softplus(z) (the closure's nu_t is C Delta^2 |G|). */
 void orc_mlp_forward(const orc_mlp *m, const double *x /*[B][6]*/, int64_t B, double *y /*[B]*/) {
     for (int64_t b = 0; b < B; ++b) {
         double in[MLP_IN], h1[MLP_H], h2[MLP_H], h3[MLP_H];
@@ -460,8 +472,10 @@ static int element_rhs(int etype, const double *X, const double *U, const double
                 nut_g = prm->delta_form ? orc_vreman_aniso(G, dm, prm->c_vreman) : orc_vreman(G, delta, prm->c_vreman);
             } else if (prm->closure == ORC_CLOSURE_MLP && prm->mlp) {
                 double f[MLP_IN];
-                orc_mlp_features(G, delta, f);
-                orc_mlp_forward(prm->mlp, f, 1, &nut_g);
+                const double g = orc_mlp_features(G, delta, prm->nu, f);
+                double C = 0.0;
+                if (g > 0.0) orc_mlp_forward(prm->mlp, f, 1, &C);
+                nut_g = C * delta * delta * g;
             }
         }
         if (nut) nut[g] = nut_g;

@@ -119,7 +119,7 @@ def _time_assemble(dm, out, reps: int, **kw) -> float:
     return e0.elapsed_time(e1) / reps
 
 
-def closure(reps: int, n_f: int = 256, steps: int = 8000, dims=(269, 134, 135)):
+def closure(reps: int, n_f: int = 256, steps: int = 8000, dims=(269, 134, 135), save: str = ""):
     """Learned closure: GPU training on box-filtered n_f^3 Taylor-Green runs,
     a-priori errors on a held-out time, then the network fused at every Gauss
     point of a mixed channel mesh against the Vreman path: time per assembly,
@@ -134,7 +134,7 @@ def closure(reps: int, n_f: int = 256, steps: int = 8000, dims=(269, 134, 135)):
     ctx = fea.Context(0)
     t = time.time()
     res = cd.run(n_f=n_f, ratios=(2, 4, 8), t_train=(3.0, 4.0, 5.0, 7.0, 8.0), t_test=(6.0,), steps=steps,
-                 log=None, ctx=ctx)
+                 log=None, ctx=ctx, save=save)
     model = res.pop("model")
     train_total_s = time.time() - t
     m = mg.channel_mesh(*dims)
@@ -339,6 +339,7 @@ def main(argv=None) -> int:
     ap.add_argument("--wall", action="store_true")
     ap.add_argument("--n-f", type=int, default=256, help="fine Taylor-Green grid of the closure's training runs")
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--save", default="", help="with --closure: write the trained network (npz) here")
     a = ap.parse_args(argv)
     if not (a.channel or a.batch or a.closure or a.projection or a.balance or a.wall):
         a.channel = a.batch = True
@@ -347,7 +348,7 @@ def main(argv=None) -> int:
     if a.batch:
         batch(a.reps)
     if a.closure:
-        closure(a.reps, n_f=a.n_f)
+        closure(a.reps, n_f=a.n_f, save=a.save)
     if a.projection:
         projection()
     if a.balance:

@@ -19,8 +19,11 @@ learned model, so this module defines the data pipeline:
    velocity, Delta = V_e^(1/3), the subgrid stress tau = bar(u u) - bar(u)
    bar(u) averaged over the element's vertices, and the least-squares eddy
    viscosity nu_t* = max(0, -tau^d : S / (2 S : S)), S = (G + G^T)/2.
-4. **Features** exactly as the kernels compute them (invariants of S and
-   O = (G - G^T)/2 with signed roots, and log Delta).
+4. **Features** exactly as the kernels compute them, dimensionless so that a
+   network fitted on one flow transfers to other scales: the invariants of S
+   and O = (G - G^T)/2 over powers of g = |G|, and the element Reynolds
+   number log(Delta^2 g / nu).  The network's target is the coefficient
+   C* = nu_t* / (Delta^2 g) (the closure evaluates nu_t = C Delta^2 g).
 
 All GPU work uses the library (assembly, fold, lumped mass, MLP training and
 inference); torch supplies device memory, FFTs and elementwise data plumbing.
@@ -140,14 +143,18 @@ class CoarseSet:
     n_c: int
     mesh: mg.Mesh
     u_nodes: np.ndarray       # (N, 3) filtered velocity at the coarse mesh's stored nodes
-    feats: np.ndarray         # (E, 6) raw features per element
+    feats: np.ndarray         # (E, 6) raw (dimensionless) features per element
     target: np.ndarray        # (E,) nu_t*
+    coef: np.ndarray          # (E,) the network's target C* = nu_t* / (Delta^2 |G|) (NaN where G = 0)
     tau_d: np.ndarray         # (E, 3, 3) deviatoric subgrid stress per element (None: training only)
     grad_n: np.ndarray        # (E, 4, 3) shape-function gradients (None: training only)
     vol: np.ndarray           # (E,)
 
 
-def _features(G: torch.Tensor, delta: torch.Tensor) -> torch.Tensor:
+def _features(G: torch.Tensor, delta: torch.Tensor, nu: float):
+    """The closure's dimensionless inputs (the library's and the oracle's
+    definition): invariants of S and O over powers of g = |G|, and
+    log(Delta^2 g / nu); returns (features (E, 6), g (E,))."""
     S = 0.5 * (G + G.transpose(1, 2))
     O = 0.5 * (G - G.transpose(1, 2))
     S2, O2 = S @ S, O @ O
@@ -155,14 +162,18 @@ def _features(G: torch.Tensor, delta: torch.Tensor) -> torch.Tensor:
     def tr(a):
         return a.diagonal(dim1=1, dim2=2).sum(-1)
 
+    g2 = (G * G).sum((1, 2))
+    g = g2.sqrt()
+    some = g2 > 0
+    safe = torch.where(some, g, torch.ones_like(g))
     inv = [tr(S2), tr(O2), tr(S2 @ S), tr(S @ O2), tr(S2 @ O2)]
     deg = [2.0, 2.0, 3.0, 3.0, 4.0]
-    cols = [torch.sign(v) * v.abs() ** (1.0 / d) for v, d in zip(inv, deg)]
-    cols.append(torch.log(delta))
-    return torch.stack(cols, dim=1)
+    cols = [torch.where(some, v / safe ** d, torch.zeros_like(v)) for v, d in zip(inv, deg)]
+    cols.append(torch.where(some, torch.log(delta * delta * safe / nu), torch.zeros_like(g)))
+    return torch.stack(cols, dim=1), g
 
 
-def coarse_samples(snap: Snapshot, r: int, keep_stress: bool = True) -> CoarseSet:
+def coarse_samples(snap: Snapshot, r: int, keep_stress: bool = True, nu: float = 1.0 / 1600.0) -> CoarseSet:
     """Filtered coarse field, features and targets at filter ratio r; the
     per-element stresses and gradients are kept for the a-priori comparison
     only when keep_stress."""
@@ -194,9 +205,13 @@ def coarse_samples(snap: Snapshot, r: int, keep_stress: bool = True) -> CoarseSe
     td = te - torch.eye(3, device="cuda", dtype=torch.float64) * (te.diagonal(dim1=1, dim2=2).sum(-1) / 3.0)[:, None, None]
     ss = (S * S).sum((1, 2))
     target = torch.clamp(-(td * S).sum((1, 2)) / (2.0 * ss + 1e-300), min=0.0)
-    feats = _features(G, vol.abs() ** (1.0 / 3.0))
+    delta = vol.abs() ** (1.0 / 3.0)
+    feats, g = _features(G, delta, nu)
+    coef = torch.where(g > 0, target / (delta * delta * torch.where(g > 0, g, torch.ones_like(g))),
+                       torch.full_like(g, float("nan")))
     return CoarseSet(n_c=n_c, mesh=mesh, u_nodes=u_nodes.cpu().numpy(), feats=feats.cpu().numpy(),
-                     target=target.cpu().numpy(), tau_d=td.cpu().numpy() if keep_stress else None,
+                     target=target.cpu().numpy(), coef=coef.cpu().numpy(),
+                     tau_d=td.cpu().numpy() if keep_stress else None,
                      grad_n=gN.cpu().numpy() if keep_stress else None, vol=vol.cpu().numpy())
 
 
@@ -215,7 +230,7 @@ class TrainedClosure:
     mean: np.ndarray
     std: np.ndarray
     scale: float
-    losses: List[float]       # batch losses every 100 steps (units of scale^2)
+    losses: List[float]       # batch losses every 100 steps (units of scale^2; targets C* / scale)
     fit_mse: float = float("nan")      # full training set, same units
     n_samples: int = 0
     env_lo: np.ndarray = None          # training envelope (raw features), set in the context
@@ -225,7 +240,8 @@ class TrainedClosure:
 
 def train(ctx: fea.Context, sets: Sequence[CoarseSet], steps: int = 2000, batch: int = 65536, lr: float = 2e-3,
           seed: int = 0, max_per_set: int = 2_000_000, envelope_q: float = 1e-4) -> TrainedClosure:
-    """Fits the network to nu_t* on the GPU (the library's training step).
+    """Fits the network to the coefficient C* = nu_t* / (Delta^2 |G|) on the
+    GPU (the library's training step).
     Each set contributes at most max_per_set seeded random samples, so fine
     filter widths (many coarse elements) do not swamp the coarse ones.  The
     per-feature [q, 1 - q] quantiles of the training features, widened by 5 %
@@ -237,7 +253,7 @@ def train(ctx: fea.Context, sets: Sequence[CoarseSet], steps: int = 2000, batch:
         if take.size > max_per_set:
             take = np.sort(rng.choice(take.size, max_per_set, replace=False))
         xs.append(c.feats[take])
-        ys.append(c.target[take])
+        ys.append(c.coef[take])
     x = np.concatenate(xs).astype(np.float32)
     y = np.concatenate(ys)
     keep = np.all(np.isfinite(x), axis=1) & np.isfinite(y)

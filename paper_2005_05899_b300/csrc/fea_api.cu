@@ -809,6 +809,9 @@ bool tail_order(const Mesh &m, fea_prec prec, fea_closure closure, fea_scatter s
 
 fea_status assemble_into(fea_ctx *ctx, Mesh &m, fea_prec prec, fea_closure closure, uint32_t mask,
                          fea_scatter scatter, double *rhs, float *nut, cudaStream_t s) {
+    // the learned closure's last input is log(Delta^2 |G| / nu)
+    if (closure == FEA_CLOSURE_MLP && !(m.nu > 0.0))
+        return fail(ctx, FEA_EINVAL, "the MLP closure needs nu > 0 (its input is the element Reynolds number)");
     CK(cudaMemsetAsync(rhs, 0, sizeof(double) * 3 * m.n, s));
     FieldDev f = m.field();
     if (scatter == FEA_SCATTER_AUTO) scatter = (fea_scatter)m.plan.scatter;
@@ -951,7 +954,11 @@ fea_status stage_with_scratch(fea_ctx *ctx, int32_t mesh, int32_t stage, double 
     if (stage < 0 || stage > 2) return fail(ctx, FEA_EINVAL, "stage must be 0, 1 or 2");
     if (!(dt > 0.0)) return fail(ctx, FEA_EINVAL, "dt must be > 0");
     if (!(nu >= 0.0) || !(c_vreman >= 0.0)) return fail(ctx, FEA_EINVAL, "nu and c_vreman must be >= 0");
+    if (closure == FEA_CLOSURE_MLP && !(nu > 0.0))
+        return fail(ctx, FEA_EINVAL, "the MLP closure needs nu > 0 (its input is the element Reynolds number)");
     if (!un || !uk || !p || !uk_out) return fail(ctx, FEA_EINVAL, "null state array");
+    if (closure == FEA_CLOSURE_MLP && !(nu > 0.0))
+        return fail(ctx, FEA_EINVAL, "the MLP closure needs nu > 0 (its input is the element Reynolds number)");
     if (m->n > max_nodes)
         return fail(ctx, FEA_EINVAL, "mesh has %lld nodes, above the %lld-node limit of the static scratch",
                     (long long)m->n, (long long)max_nodes);

@@ -397,8 +397,9 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
     const int lane = threadIdx.x & 31;
     uint32_t *featw = reinterpret_cast<uint32_t *>(mu.scratch);
     float *Stile = reinterpret_cast<float *>(mu.scratch + mlp_feat_bytes(ng));
-    float *ntile = Stile + ng * 9 * 32;
+    float *ntile = Stile + ng * 9 * 32;   // the network's coefficient C per point
     float *qtile = ntile + ng * 32;
+    float *gtile = qtile + ng * 32;       // |G| per point
     uint32_t inside_mask = 0;   // bit g: point g inside the training envelope
     // element volume (sum of the weights W, in R: it only sets Delta)
     R V = R(0);
@@ -496,7 +497,7 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
 #pragma unroll
                 for (int j = 0; j < 3; ++j) Gf[i][j] = float(G[i][j]);
             uint32_t wds[3];
-            const bool inside = mlp_gp_words(Gf, *mu.w, wds);
+            const bool inside = mlp_gp_words(Gf, *mu.w, wds, &gtile[g * 32 + lane]);
             uint32_t *row = featw + (g * 32 + lane) * 4;
             row[0] = wds[0];
             row[1] = wds[1];
@@ -558,14 +559,16 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
     }
     int fallbacks = 0;
     if constexpr (MLP) {
-        // Delta = V^(1/3) completes every row (column 5)
+        // Delta = V^(1/3) completes every row: column 5, log(Delta^2 |G| / nu)
         const R delta = cbrt_r(V);
         const R d2 = delta * delta;
-        bool delta_inside;
-        const uint16_t db = mlp_delta_bits(float(delta), *mu.w, &delta_inside);
-        if (!delta_inside) inside_mask = 0;
 #pragma unroll 1
-        for (int g = 0; g < ng; ++g) reinterpret_cast<uint16_t *>(featw + (g * 32 + lane) * 4)[5] = db;
+        for (int g = 0; g < ng; ++g) {
+            bool re_inside;
+            reinterpret_cast<uint16_t *>(featw + (g * 32 + lane) * 4)[5] =
+                mlp_re_bits(float(delta), gtile[g * 32 + lane], float(f.nu), *mu.w, &re_inside);
+            if (!re_inside) inside_mask &= ~(1u << g);
+        }
         __syncwarp();
 #pragma unroll 1
         for (int g = 0; g < ng; ++g) mlp_rows32(*mu.w, reinterpret_cast<const uint16_t *>(featw), ntile, g);
@@ -574,7 +577,9 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
         for (int g = 0; g < ng; ++g) {
             const bool use = (inside_mask >> g) & 1u;
             fallbacks += !use;
-            const R nt = use ? R(ntile[g * 32 + lane]) : R(qtile[g * 32 + lane]) * (aniso ? R(1) : d2);
+            // nu_t = C Delta^2 |G| (network) or Vreman's
+            const R nt = use ? R(ntile[g * 32 + lane]) * d2 * R(gtile[g * 32 + lane])
+                             : R(qtile[g * 32 + lane]) * (aniso ? R(1) : d2);
             if (nut_out) nut_out[g] = float(nt);
             if (mask & FEA_TERM_SGS) {
                 R Sg[3][3];
@@ -656,17 +661,20 @@ __device__ int tet_residual(const Gathered<R, J64> &el, const FieldDev &f, const
         uint32_t *row = reinterpret_cast<uint32_t *>(mu.scratch) + lane * 4;
         float *ntile = reinterpret_cast<float *>(mu.scratch + mlp_feat_bytes(1) + mlp_s_bytes(1));
         uint32_t wds[3];
-        const bool inside = mlp_gp_words(Gf, *mu.w, wds);
-        bool delta_inside;
+        float gabs;
+        const bool inside = mlp_gp_words(Gf, *mu.w, wds, &gabs);
+        bool re_inside;
+        const R delta0 = cbrt_r(V);
         row[0] = wds[0];
         row[1] = wds[1];
-        row[2] = (wds[2] & 0xffffu) | ((uint32_t)mlp_delta_bits(float(cbrt_r(V)), *mu.w, &delta_inside) << 16);
+        row[2] = (wds[2] & 0xffffu) |
+                 ((uint32_t)mlp_re_bits(float(delta0), gabs, float(f.nu), *mu.w, &re_inside) << 16);
         row[3] = 0u;
         __syncwarp();
         mlp_rows32(*mu.w, reinterpret_cast<const uint16_t *>(mu.scratch), ntile, 0);
         __syncwarp();
-        if (inside && delta_inside) {
-            nut = R(ntile[lane]);
+        if (inside && re_inside) {
+            nut = R(ntile[lane]) * delta0 * delta0 * R(gabs);   // nu_t = C Delta^2 |G|
         } else {
             const R delta = cbrt_r(V);
             if (VAR && f.delta_form == 1) {

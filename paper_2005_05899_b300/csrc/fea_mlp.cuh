@@ -2,11 +2,13 @@
 // layers, softplus output) evaluated on BF16 tensor cores with FP32
 // accumulation, warp-cooperatively on tiles of 16 rows.
 //
-// Inputs per row (Gauss point or element): the invariants of S = (G+G^T)/2
-// and O = (G-G^T)/2 of the velocity gradient G_ij = du_i/dx_j,
-//   x_k = sign(I_k) |I_k|^(1/d_k), I = (tr S^2, tr O^2, tr S^3, tr S O^2,
-//   tr S^2 O^2), d = (2, 2, 3, 3, 4), and x_6 = log Delta,
-// normalised as (x - mean) / std; output nu_t = out_scale softplus(z).
+// Inputs per row (Gauss point or element), dimensionless: the invariants of
+// S = (G+G^T)/2 and O = (G-G^T)/2 of the velocity gradient G_ij = du_i/dx_j
+// over powers of g = |G| (g^2 = tr S^2 - tr O^2),
+//   x_1..5 = (tr S^2, tr O^2, tr S^3, tr S O^2, tr S^2 O^2) / g^(2, 2, 3, 3, 4),
+// and the element Reynolds number x_6 = log(Delta^2 g / nu), normalised as
+// (x - mean) / std; output the coefficient C = out_scale softplus(z), and
+// nu_t = C Delta^2 g (zero where g = 0, whose features are all zero).
 //
 // Tensor-core tiles: mma.sync m16n8k16 (row.col, BF16 in, FP32 accumulate).
 // For lane l: g = l / 4, t = l % 4; an A fragment holds rows (g, g+8) and
@@ -63,56 +65,6 @@ __device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], 
 __device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
 __device__ __forceinline__ float sigmoid_f(float z) { return 1.0f / (1.0f + __expf(-z)); }
 __device__ __forceinline__ float softplus_f(float z) { return z > 20.0f ? z : log1pf(__expf(z)); }
-
-__device__ __forceinline__ float signed_root(float v, int d) {
-    const float a = fabsf(v);
-    float r = d == 2 ? sqrtf(a) : (d == 3 ? cbrtf(a) : sqrtf(sqrtf(a)));
-    return v < 0.0f ? -r : r;
-}
-
-// Raw features of one velocity gradient (row-major G) and filter width.
-__device__ __forceinline__ void mlp_features(const float G[3][3], float delta, float x[kMlpIn]) {
-    float S[3][3], O[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            S[i][j] = 0.5f * (G[i][j] + G[j][i]);
-            O[i][j] = 0.5f * (G[i][j] - G[j][i]);
-        }
-    float S2[3][3], O2[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            float a = 0.f, b = 0.f;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                a += S[i][k] * S[k][j];
-                b += O[i][k] * O[k][j];
-            }
-            S2[i][j] = a;
-            O2[i][j] = b;
-        }
-    float trS2 = 0.f, trO2 = 0.f, trS3 = 0.f, trSO2 = 0.f, trS2O2 = 0.f;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        trS2 += S2[i][i];
-        trO2 += O2[i][i];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            trS3 += S2[i][k] * S[k][i];
-            trSO2 += S[i][k] * O2[k][i];
-            trS2O2 += S2[i][k] * O2[k][i];
-        }
-    }
-    x[0] = signed_root(trS2, 2);
-    x[1] = signed_root(trO2, 2);
-    x[2] = signed_root(trS3, 3);
-    x[3] = signed_root(trSO2, 3);
-    x[4] = signed_root(trS2O2, 4);
-    x[5] = logf(delta);
-}
 
 // A fragment of the first layer from a per-warp shared tile of normalised
 // features: feat[row][kW1Pitch] bf16 (columns 6..15 zero); `row0` selects
@@ -235,10 +187,10 @@ constexpr float kFeatClamp = 64.0f;
 // needs once nu_t is known, and nu_t [ng*32] f32.
 __host__ __device__ constexpr size_t mlp_feat_bytes(int ng) { return (size_t)ng * 32 * 16; }
 __host__ __device__ constexpr size_t mlp_s_bytes(int ng) { return (size_t)ng * 9 * 32 * 4; }
-// after them: nu_t [ng*32] f32 and Vreman's q = nu_t / Delta^2 [ng*32] f32
-// (negative where the point is inside the training envelope)
+// after them: the network's coefficient [ng*32] f32, Vreman's q = nu_t /
+// Delta^2 [ng*32] f32 (for the fallback) and g = |G| [ng*32] f32
 __host__ __device__ constexpr size_t mlp_warp_scratch_bytes(int ng) {
-    return mlp_feat_bytes(ng) + mlp_s_bytes(ng) + (size_t)ng * 32 * 4 * 2;
+    return mlp_feat_bytes(ng) + mlp_s_bytes(ng) + (size_t)ng * 32 * 4 * 3;
 }
 
 __device__ __forceinline__ void mlp_copy_fast(const MlpFast *g, MlpFast *s) {
@@ -383,19 +335,23 @@ __device__ __forceinline__ void mlp_rows32(const MlpFast &w, const uint16_t *fea
     }
 }
 
-// The five invariant features of G (signed roots; log Delta is the sixth),
-// normalised and clamped, as f16 words: word 0 = (x0, x1), word 1 =
-// (x2, x3), word 2 = (x4, 0).  Non-finite values (degenerate elements, idle
-// lanes) become the mean.  Returns whether the five lie inside the training
+// The five invariant features of G over powers of g = |G| (the element
+// Reynolds number is the sixth, mlp_re_bits), normalised and clamped, as f16
+// words: word 0 = (x1, x2), word 1 = (x3, x4), word 2 = (x5, 0).  *gout = g.
+// A vanishing gradient gives zero features (and a zero nu_t: the caller
+// multiplies by g).  Non-finite values (degenerate elements, idle lanes)
+// become the mean.  Returns whether the five lie inside the training
 // envelope (the caller falls back to Vreman's nu_t where they do not).
-__device__ __forceinline__ bool mlp_gp_words(const float G[3][3], const MlpFast &w, uint32_t words[3]) {
+__device__ __forceinline__ bool mlp_gp_words(const float G[3][3], const MlpFast &w, uint32_t words[3], float *gout) {
     float S[3][3], O[3][3];
+    float g2 = 0.f;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             S[i][j] = 0.5f * (G[i][j] + G[j][i]);
             O[i][j] = 0.5f * (G[i][j] - G[j][i]);
+            g2 += G[i][j] * G[i][j];
         }
     float S2[3][3], O2[3][3];
 #pragma unroll
@@ -423,17 +379,16 @@ __device__ __forceinline__ bool mlp_gp_words(const float G[3][3], const MlpFast 
             I[4] += S2[i][k] * O2[k][i];
         }
     }
+    const bool some = g2 > 0.f;
+    const float ig2 = some ? 1.f / g2 : 0.f, ig = some ? rsqrtf(g2) : 0.f;
+    *gout = some ? g2 * ig : 0.f;
+    const float sc[5] = {ig2, ig2, ig2 * ig, ig2 * ig, ig2 * ig2};
     float xn[5];
     bool inside = true;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-        const float a = fabsf(I[k]);
-        // roots of degree 2, 2, 3, 3, 4; the features are rounded to FP16 next,
-        // so the fast exp2/log2 power is ample for the cube root
-        float r = (k < 2) ? sqrtf(a) : (k < 4 ? __powf(a, 1.0f / 3.0f) : sqrtf(sqrtf(a)));
-        r = I[k] < 0.0f ? -r : r;
-        const float v = (r - w.mean[k]) * w.istd[k];
-        inside = inside && v >= w.env_lo[k] && v <= w.env_hi[k];   // false for NaN
+        const float v = (I[k] * sc[k] - w.mean[k]) * w.istd[k];
+        inside = inside && (!some || (v >= w.env_lo[k] && v <= w.env_hi[k]));   // false for NaN
         xn[k] = isfinite(v) ? fminf(fmaxf(v, -kFeatClamp), kFeatClamp) : 0.0f;
     }
     words[0] = pack_f16x2(xn[0], xn[1]);
@@ -442,11 +397,13 @@ __device__ __forceinline__ bool mlp_gp_words(const float G[3][3], const MlpFast 
     return inside;
 }
 
-// f16 bits of the normalised (clamped) log-Delta feature; *inside: within
-// the training envelope
-__device__ __forceinline__ uint16_t mlp_delta_bits(float delta, const MlpFast &w, bool *inside) {
-    float v = (__logf(delta) - w.mean[5]) * w.istd[5];
-    *inside = v >= w.env_lo[5] && v <= w.env_hi[5];
+// f16 bits of the normalised (clamped) element Reynolds number
+// log(Delta^2 g / nu) (zero raw feature where g = 0); *inside: within the
+// training envelope
+__device__ __forceinline__ uint16_t mlp_re_bits(float delta, float g, float nu, const MlpFast &w, bool *inside) {
+    const bool some = g > 0.f;
+    float v = ((some ? __logf(delta * delta * g / nu) : 0.f) - w.mean[5]) * w.istd[5];
+    *inside = !some || (v >= w.env_lo[5] && v <= w.env_hi[5]);
     v = isfinite(v) ? fminf(fmaxf(v, -kFeatClamp), kFeatClamp) : 0.0f;
     return (uint16_t)(pack_f16x2(v, 0.0f) & 0xffffu);
 }

@@ -59,10 +59,10 @@ def ctx():
     c.close()
 
 
-def sample_features(rng, n):
+def sample_features(rng, n, nu=1e-3):
     G = rng.standard_normal((n, 3, 3)) * rng.uniform(0.1, 3.0, (n, 1, 1))
     delta = rng.uniform(0.005, 0.05, n)
-    return np.stack([O.mlp_features(G[k], delta[k]) for k in range(n)]).astype(np.float32)
+    return np.stack([O.mlp_features(G[k], delta[k], nu) for k in range(n)]).astype(np.float32)
 
 
 def test_forward_matches_oracle(ctx):
@@ -151,12 +151,12 @@ from paper_2005_05899_b300 import meshgen as mg  # noqa: E402
 
 
 def closure_model(rng, mesh, field):
-    """An MLP whose nu_t is of the size of Vreman's on this field."""
+    """An MLP whose nu_t = C Delta^2 |G| is of the size of Vreman's (Vreman's
+    nu_t / (Delta^2 |G|) is c sqrt(B / (G:G)) / |G| <= c / sqrt(2): the
+    coefficient scale 0.03 with softplus of order one)."""
     theta = (0.2 * rng.standard_normal(fea.MLP_NPARAM)).astype(np.float32)
-    om = O.OracleMesh.of(mesh)
-    _, nut = O.assemble_rhs(om, field.u, field.p, field.nu, field.c_vreman, "vreman", want_nut=True)
-    scale = float(np.mean(np.concatenate([v.ravel() for v in nut.values()]))) + 1e-8
-    x = sample_features(rng, 2000)
+    scale = 0.03
+    x = sample_features(rng, 2000, field.nu)
     mean = x.mean(axis=0).astype(np.float32)
     std = (x.std(axis=0) + 1e-3).astype(np.float32)
     return theta, mean, std, scale
@@ -224,7 +224,7 @@ def oracle_gp_features(mesh, field):
             U = field.u[conn[e]]
             delta = W.sum() ** (1.0 / 3.0)
             for g in range(ng):
-                F[e, g] = O.mlp_features(U.T @ d[g], delta)
+                F[e, g] = O.mlp_features(U.T @ d[g], delta, field.nu)
         out[t] = F
     return out
 

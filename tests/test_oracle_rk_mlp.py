@@ -170,34 +170,54 @@ def test_adam_step_matches_torch_optim():
 
 
 def test_mlp_features_closed_forms_and_invariance():
+    nu = 1e-3
+    # solid rotation: no strain, |G|^2 = 2 w^2
     w = 1.3
     G = np.array([[0, -w, 0], [w, 0, 0], [0, 0, 0]], float)
-    x = O.mlp_features(G, 0.5)
-    assert np.allclose(x, [0, -math.sqrt(2) * w, 0, 0, 0, math.log(0.5)], atol=1e-14)
-    s = 0.7
-    x = O.mlp_features(np.diag([s, s, -2 * s]), 2.0)
-    assert np.allclose(x, [math.sqrt(6) * s, 0, -(6 ** (1 / 3)) * s, 0, 0, math.log(2.0)], atol=1e-14)
+    x = O.mlp_features(G, 0.5, nu)
+    assert np.allclose(x, [0, -1, 0, 0, 0, math.log(0.25 * math.sqrt(2) * w / nu)], atol=1e-14)
+    # axisymmetric strain diag(s, s, -2s): tr S^3 / |G|^3 = -6 s^3 / (6 s^2)^(3/2) = -1/sqrt(6)
+    s_ = 0.7
+    x = O.mlp_features(np.diag([s_, s_, -2 * s_]), 2.0, nu)
+    assert np.allclose(x, [1, 0, -1 / math.sqrt(6), 0, 0, math.log(4.0 * math.sqrt(6) * s_ / nu)], atol=1e-14)
+    # plane shear u = (gy, 0, 0): S and O share |G|^2 / 2; tr S O^2 = 0, tr S^2 O^2 = -|G|^4 / 8
+    x = O.mlp_features(np.array([[0, 2.0, 0], [0, 0, 0], [0, 0, 0]]), 1.0, nu)
+    assert np.allclose(x[:5], [0.5, -0.5, 0, 0, -0.125], atol=1e-14)
     rng = np.random.default_rng(4)
     G = rng.standard_normal((3, 3))
     q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
-    assert np.allclose(O.mlp_features(q @ G @ q.T, 0.3), O.mlp_features(G, 0.3), rtol=1e-12, atol=1e-13)
+    # rotation invariance, and scale invariance of the first five (the sixth shifts by log lambda)
+    assert np.allclose(O.mlp_features(q @ G @ q.T, 0.3, nu), O.mlp_features(G, 0.3, nu), rtol=1e-12, atol=1e-13)
+    lam = 37.0
+    x1, x2 = O.mlp_features(G, 0.3, nu), O.mlp_features(lam * G, 0.3, nu)
+    assert np.allclose(x2[:5], x1[:5], rtol=1e-12, atol=1e-14)
+    assert abs(x2[5] - x1[5] - math.log(lam)) < 1e-12
+    # a vanishing gradient has no direction
+    assert np.all(O.mlp_features(np.zeros((3, 3)), 0.3, nu) == 0)
 
 
 def test_mlp_closure_with_constant_output_is_a_viscosity():
-    """With all weights zero the network's output is the constant
-    s softplus(b4): the MLP closure's subgrid term must then equal the
-    viscous term with nu replaced by that constant, element type by type
-    (the 2 eps form is linear in the viscosity)."""
-    m = mg.channel_mesh(nx=6, ny=8, nz=4, seed=3, n_layers=2, split_frac=0.3)
-    assert len(m.conn) == 4
-    f = mg.channel_field(m, seed=2, nu=1e-3)
+    """With all weights zero the network's output is the constant C = s
+    softplus(b4), so nu_t = C Delta^2 |G|.  A linear velocity field (one G
+    everywhere) on a Kuhn-split grid of equal cubes (one element volume, so
+    one Delta) makes that a constant viscosity: the MLP closure's subgrid
+    term must equal the viscous term with nu replaced by C Delta^2 |G| (the
+    2 eps form is linear in the viscosity)."""
+    m = mg.tgv_mesh(4)
+    rng = np.random.default_rng(6)
+    B = rng.standard_normal((3, 3))
+    u = m.xyz @ B.T + 0.3
+    p = np.zeros(m.n_nodes)
+    nu = 1e-3
     theta = np.zeros(O.nparam())
     theta[-1] = 0.3
-    scale = 2e-4
+    scale = 2e-2
     mlp = O.MLPParams(theta, np.zeros(6), np.ones(6), out_scale=scale)
-    nut = scale * math.log1p(math.exp(0.3))
+    h = 2 * math.pi / 4
+    delta = (h ** 3 / 6.0) ** (1.0 / 3.0)
+    nut = scale * math.log1p(math.exp(0.3)) * delta ** 2 * np.linalg.norm(B)
     om = O.OracleMesh.of(m)
-    sgs, nut_gp = O.assemble_rhs(om, f.u, f.p, f.nu, f.c_vreman, "mlp", mask=O.TERM_SGS, mlp=mlp, want_nut=True)
-    visc = O.assemble_rhs(om, f.u, f.p, f.nu, f.c_vreman, "none", mask=O.TERM_VISC)
-    assert all(np.allclose(v, nut, rtol=1e-14, atol=0) for v in nut_gp.values())
-    assert np.abs(sgs - visc * (nut / f.nu)).max() <= 1e-12 * np.abs(visc * (nut / f.nu)).max()
+    sgs, nut_gp = O.assemble_rhs(om, u, p, nu, 0.07, "mlp", mask=O.TERM_SGS, mlp=mlp, want_nut=True)
+    visc = O.assemble_rhs(om, u, p, nu, 0.07, "none", mask=O.TERM_VISC)
+    assert all(np.allclose(v, nut, rtol=1e-12, atol=0) for v in nut_gp.values())
+    assert np.abs(sgs - visc * (nut / nu)).max() <= 1e-11 * np.abs(visc * (nut / nu)).max()
