@@ -1392,7 +1392,7 @@ fea_status fea_assemble_rhs_batched(fea_ctx *ctx, const int32_t *meshes, int32_t
         }
     const int64_t n_items = (int64_t)items.size() / 2;
     if (smem > kChunkSmemLimit) return fail(ctx, FEA_EINVAL, "batched chunk needs more than 200 KB of shared memory");
-    if (closure == FEA_CLOSURE_MLP && smem + mlp_smem_bytes(256, kMaxNg) > kMaxBlockSmem)
+    if (closure == FEA_CLOSURE_MLP && ((smem + 127) & ~(size_t)127) + mlp_smem_bytes(128, kMaxNg) > kMaxBlockSmem)
         return fail(ctx, FEA_EINVAL, "batched chunk with the MLP closure needs more than 227 KB of shared memory");
     auto grow = [&](DevBuf<unsigned char> &d, size_t bytes) -> cudaError_t {
         return d.n >= bytes ? cudaSuccess : d.alloc(bytes);
@@ -2061,7 +2061,7 @@ fea_status fea_mlp_forward(fea_ctx *ctx, const float *x, int64_t B, float *nut, 
     if (!ctx) return FEA_EINVAL;
     if (B < 0 || (B > 0 && (!x || !nut))) return fail(ctx, FEA_EINVAL, "bad MLP forward arguments");
     if (!ctx->mlp_ready) return fail(ctx, FEA_ESTATE, "no MLP loaded");
-    CK(launch_mlp_forward(ctx->mlp_w.p, x, B, nut, ctx->sms, (cudaStream_t)stream));
+    CK(launch_mlp_forward(ctx->mlp_w.p, x, B, nut, ctx->sms, ctx->d_err, (cudaStream_t)stream));
     ctx->launches++;
     return FEA_OK;
 }

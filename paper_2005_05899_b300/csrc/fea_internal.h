@@ -108,7 +108,7 @@ struct AsmArgs {
     double *rhs;          // [3][n]
     float *nut;           // optional: type block of nu_t output (already offset)
     unsigned *err;        // device error word
-    const void *mlp;      // MLP closure weights (device MlpFast) when closure == FEA_CLOSURE_MLP
+    const void *mlp;      // MLP closure weights (device tc::MlpTc) when closure == FEA_CLOSURE_MLP
     unsigned long long *mlp_fb = nullptr;   // count of Gauss points that fell back to Vreman (MLP only)
     // chunk kernels: launched as a programmatic dependent of the kernel before
     // it on the stream (starts while that one drains; waits for it to
@@ -232,7 +232,8 @@ const void *mlp_fast_ptr(const void *w);   // inference layout inside the weight
 int mlp_param_count();
 cudaError_t launch_mlp_pack(const float *theta, const float *mean, const float *stdv, float out_scale, void *w,
                             cudaStream_t s);
-cudaError_t launch_mlp_forward(const void *w, const float *x, int64_t B, float *y, int sms, cudaStream_t s);
+cudaError_t launch_mlp_forward(const void *w, const float *x, int64_t B, float *y, int sms, unsigned *err,
+                               cudaStream_t s);
 cudaError_t launch_mlp_train(const void *w, const float *x, const float *y, int64_t B, float *grad, float *loss,
                              cudaStream_t s);
 cudaError_t launch_adam(float *theta, const float *grad, float *m1, float *m2, int n, float lr, float b1, float b2,

@@ -348,12 +348,19 @@ __device__ __forceinline__ JR adjugate(const JR J[3][3], JR A[3][3]) {
 // so the subgrid term is accumulated without the Delta^2 factor and added
 // once V_e is complete.  J, its adjugate and determinant are in JR (FP64
 // for flagged elements), the rest in R.
-// MLP closure in an element kernel: the weights in shared memory and this
-// warp's scratch (mlp_warp_scratch_bytes of the element's row count).
+// MLP closure in an element kernel (CTA = one warpgroup of 128 threads):
+// the weights in shared memory, this warp's scratch (mlp_warp_scratch_bytes
+// of the element's row count), the warpgroup's feature tiles (row
+// 32 (warp % 4) + lane of tile g: this thread's element at Gauss point g),
+// the shared zero K block and the tensor-core state.
 struct MlpUse {
-    const MlpFast *w;
+    const tc::MlpTc *w;
     unsigned char *scratch;
+    unsigned char *feat;
+    unsigned char *zero;
+    tc::Warpgroup *wg;
 };
+__device__ __forceinline__ int mlp_row() { return 32 * ((threadIdx.x >> 5) & 3) + (threadIdx.x & 31); }
 
 // rows of the network per element: one per Gauss point, one for TET04
 // (constant gradient, so every Gauss point has the same nu_t)
@@ -365,7 +372,7 @@ __host__ __device__ constexpr int mlp_rows_per_elem(int et) {
 // Vreman (outside the training envelope); 0 without the MLP.
 template <int ET, typename R, bool J64, bool MLP = false, bool VAR = true>
 __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, const AsmArgs &args, R r[][3],
-                                float *nut_out, bool &bad, const MlpUse &mu = MlpUse{nullptr, nullptr}) {
+                                float *nut_out, bool &bad, const MlpUse &mu = MlpUse{}) {
     using JR = typename std::conditional<J64, double, R>::type;
     constexpr int nen = kNen[ET], ng = kNg[ET];
     const uint32_t mask = args.mask;
@@ -395,8 +402,7 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
     // subgrid term; phase 2 runs the network over the warp's 32 x ng rows;
     // phase 3 adds the subgrid term with the per-point nu_t.
     const int lane = threadIdx.x & 31;
-    uint32_t *featw = reinterpret_cast<uint32_t *>(mu.scratch);
-    float *Stile = reinterpret_cast<float *>(mu.scratch + mlp_feat_bytes(ng));
+    float *Stile = reinterpret_cast<float *>(mu.scratch);
     float *ntile = Stile + ng * 9 * 32;   // the network's coefficient C per point
     float *qtile = ntile + ng * 32;
     float *gtile = qtile + ng * 32;       // |G| per point
@@ -498,11 +504,8 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
                 for (int j = 0; j < 3; ++j) Gf[i][j] = float(G[i][j]);
             uint32_t wds[3];
             const bool inside = mlp_gp_words(Gf, *mu.w, wds, &gtile[g * 32 + lane]);
-            uint32_t *row = featw + (g * 32 + lane) * 4;
-            row[0] = wds[0];
-            row[1] = wds[1];
-            row[2] = wds[2];
-            row[3] = 0u;
+            *reinterpret_cast<uint4 *>(mu.feat + (g * tc::kRows + mlp_row()) * 16) =
+                make_uint4(wds[0], wds[1], wds[2], tc::kOnesWord);
             inside_mask |= (uint32_t)inside << g;
             // with an envelope, Vreman's q = nu_t / Delta^2 (nu_t itself with
             // per-direction widths) for the fallback
@@ -565,14 +568,12 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
 #pragma unroll 1
         for (int g = 0; g < ng; ++g) {
             bool re_inside;
-            reinterpret_cast<uint16_t *>(featw + (g * 32 + lane) * 4)[5] =
+            reinterpret_cast<uint16_t *>(mu.feat + (g * tc::kRows + mlp_row()) * 16)[5] =
                 mlp_re_bits(float(delta), gtile[g * 32 + lane], float(f.nu), *mu.w, &re_inside);
             if (!re_inside) inside_mask &= ~(1u << g);
         }
-        __syncwarp();
-#pragma unroll 1
-        for (int g = 0; g < ng; ++g) mlp_rows32(*mu.w, reinterpret_cast<const uint16_t *>(featw), ntile, g);
-        __syncwarp();
+        // phase 2: the warpgroup's 128 elements x ng points as ng tiles of 128 rows
+        tc::run(*mu.wg, mu.w, mu.feat, mu.zero, ng, ntile + lane, 32);
 #pragma unroll 1
         for (int g = 0; g < ng; ++g) {
             const bool use = (inside_mask >> g) & 1u;
@@ -614,7 +615,7 @@ __device__ int element_residual(const Gathered<R, J64> &el, const FieldDev &f, c
 //   sum_g W N_a N_b = V (1 + delta_ab) / 20,  sum_g W N_a = V / 4.
 template <typename R, bool J64, bool MLP = false, bool VAR = true>
 __device__ int tet_residual(const Gathered<R, J64> &el, const FieldDev &f, const AsmArgs &args, R r[][3],
-                            float *nut_out, bool &bad, const MlpUse &mu = MlpUse{nullptr, nullptr}) {
+                            float *nut_out, bool &bad, const MlpUse &mu = MlpUse{}) {
     using JR = typename std::conditional<J64, double, R>::type;
     const uint32_t mask = args.mask;
     JR J[3][3];
@@ -651,28 +652,23 @@ __device__ int tet_residual(const Gathered<R, J64> &el, const FieldDev &f, const
     R nut = R(0);
     int fallbacks = 0;
     if constexpr (MLP) {
-        // one row per element (lane) through the warp's 32-row tile
+        // one row per element: the warpgroup's 128 elements as one tile
         const int lane = threadIdx.x & 31;
         float Gf[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int j = 0; j < 3; ++j) Gf[i][j] = float(G[i][j]);
-        uint32_t *row = reinterpret_cast<uint32_t *>(mu.scratch) + lane * 4;
-        float *ntile = reinterpret_cast<float *>(mu.scratch + mlp_feat_bytes(1) + mlp_s_bytes(1));
+        float *ntile = reinterpret_cast<float *>(mu.scratch + mlp_s_bytes(1));
         uint32_t wds[3];
         float gabs;
         const bool inside = mlp_gp_words(Gf, *mu.w, wds, &gabs);
         bool re_inside;
         const R delta0 = cbrt_r(V);
-        row[0] = wds[0];
-        row[1] = wds[1];
-        row[2] = (wds[2] & 0xffffu) |
+        wds[2] = (wds[2] & 0xffffu) |
                  ((uint32_t)mlp_re_bits(float(delta0), gabs, float(f.nu), *mu.w, &re_inside) << 16);
-        row[3] = 0u;
-        __syncwarp();
-        mlp_rows32(*mu.w, reinterpret_cast<const uint16_t *>(mu.scratch), ntile, 0);
-        __syncwarp();
+        *reinterpret_cast<uint4 *>(mu.feat + mlp_row() * 16) = make_uint4(wds[0], wds[1], wds[2], tc::kOnesWord);
+        tc::run(*mu.wg, mu.w, mu.feat, mu.zero, 1, ntile + lane, 32);
         if (inside && re_inside) {
             nut = R(ntile[lane]) * delta0 * delta0 * R(gabs);   // nu_t = C Delta^2 |G|
         } else {
@@ -744,6 +740,41 @@ __device__ int tet_residual(const Gathered<R, J64> &el, const FieldDev &f, const
     return fallbacks;
 }
 
+// Shared memory of a fused-closure CTA (128 threads, one warpgroup) from a
+// 128-byte aligned base: the weights (tc::MlpTc), the feature tiles
+// [ng][128][8] BF16 and the zero K block, the four warps' scratch, then four
+// mbarriers and the TMEM address.
+__host__ __device__ constexpr size_t mlp_cta_bytes(int ng) {
+    return sizeof(tc::MlpTc) + tc::feat_bytes(ng) + 4 * mlp_warp_scratch_bytes(ng) + 64;
+}
+// A fused-closure CTA's dynamic shared memory is held at no less than this,
+// so that at most two such CTAs share an SM: each allocates 256 of the SM's
+// 512 TMEM columns, and a third would wait for one of them to finish.
+constexpr size_t kMlpMinCtaSmem = 80 * 1024;
+
+// SMs of the current device (persistent grids of the fused closure)
+static int device_sms() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 148;
+}
+
+__device__ __forceinline__ void mlp_cta_setup(unsigned char *base, int ng, const void *gw, unsigned *err,
+                                              uint32_t polls, MlpUse &mu, tc::Warpgroup &wg) {
+    tc::MlpTc *w = reinterpret_cast<tc::MlpTc *>(base);
+    unsigned char *feat = base + sizeof(tc::MlpTc);
+    unsigned char *zero = feat + (size_t)ng * tc::kRows * 16;
+    unsigned char *scr = zero + tc::kRows * 16;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(scr + 4 * mlp_warp_scratch_bytes(ng));
+    tc::setup(static_cast<const tc::MlpTc *>(gw), w, zero, bars, wg, err, polls);
+    mu.w = w;
+    mu.feat = feat;
+    mu.zero = zero;
+    mu.scratch = scr + (threadIdx.x >> 5) * mlp_warp_scratch_bytes(ng);
+    mu.wg = &wg;
+}
+
 // warp-aggregated count of MLP fallbacks (all 32 lanes call it together)
 __device__ __forceinline__ void count_fallbacks(unsigned long long *counter, int n) {
 #pragma unroll
@@ -780,27 +811,15 @@ __device__ __forceinline__ void peer_sum3(unsigned act, unsigned peers, double &
 // elements have the same node in the same local slot sum their contributions
 // (Morton-ordered neighbours often share a corner in the same slot); the
 // lowest such lane issues the atomics.
-template <int ET, typename R, bool J64, bool MLP = false, bool AGG = false>
-__global__ void __launch_bounds__(256) k_assemble_atomic(BucketDev b, FieldDev f, AsmArgs args) {
+// One element of the atomic scatter (e_raw may lie past the category's end:
+// with the MLP such a thread repeats the last element through the network
+// and stores nothing).
+template <int ET, typename R, bool J64, bool MLP, bool AGG>
+__device__ __forceinline__ void atomic_element(const BucketDev &b, const FieldDev &f, const AsmArgs &args,
+                                               int64_t e_raw, unsigned act, const MlpUse &mu) {
     constexpr int nen = kNen[ET], ng = kNg[ET];
-    const int64_t e_raw = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    // lanes with an element (blocks are whole warps); taken before any lane returns
-    const unsigned act = AGG ? __ballot_sync(0xffffffffu, e_raw < b.count) : 0u;
-    // with the MLP the whole warp evaluates the network together: idle lanes
-    // repeat the last element and store nothing
-    if (!MLP && e_raw >= b.count) return;
     const bool active = e_raw < b.count;
     const int64_t e = active ? e_raw : b.count - 1;
-    MlpUse mu{nullptr, nullptr};
-    if constexpr (MLP) {
-        // weights, then one scratch block per warp (no thread has returned)
-        extern __shared__ float4 smem4[];
-        unsigned char *base = reinterpret_cast<unsigned char *>(smem4);
-        MlpFast *w = reinterpret_cast<MlpFast *>(base);
-        mlp_copy_fast(static_cast<const MlpFast *>(args.mlp), w);
-        mu.w = w;
-        mu.scratch = base + sizeof(MlpFast) + (threadIdx.x >> 5) * mlp_warp_scratch_bytes(mlp_rows_per_elem(ET));
-    }
     int idx[nen];
 #pragma unroll
     for (int a = 0; a < nen; ++a) idx[a] = __ldg(&b.conn[(int64_t)a * b.count + e]);
@@ -841,6 +860,31 @@ __global__ void __launch_bounds__(256) k_assemble_atomic(BucketDev b, FieldDev f
         for (int a = 0; a < nen; ++a)
 #pragma unroll
             for (int i = 0; i < 3; ++i) atomicAdd(&args.rhs[(int64_t)i * f.n + idx[a]], to_f64(r[a][i]));
+    }
+}
+
+// Thread per element.  With the MLP the kernel is persistent (two CTAs of
+// one warpgroup per SM, set up once): each CTA takes blocks of 128
+// consecutive elements in turn, the warpgroup running the network over them
+// together.
+template <int ET, typename R, bool J64, bool MLP = false, bool AGG = false>
+__global__ void __launch_bounds__(MLP ? 128 : 256, MLP ? 2 : 1) k_assemble_atomic(BucketDev b, FieldDev f,
+                                                                                    AsmArgs args) {
+    if constexpr (MLP) {
+        extern __shared__ float4 smem4[];
+        MlpUse mu{};
+        tc::Warpgroup wg;
+        mlp_cta_setup(reinterpret_cast<unsigned char *>(smem4), mlp_rows_per_elem(ET), args.mlp, args.err,
+                      args.wait_polls, mu, wg);
+        for (int64_t blk = blockIdx.x; blk * 128 < b.count; blk += gridDim.x)
+            atomic_element<ET, R, J64, true, false>(b, f, args, blk * 128 + threadIdx.x, 0u, mu);
+        tc::teardown(wg);
+    } else {
+        const int64_t e_raw = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        // lanes with an element (blocks are whole warps); taken before any lane returns
+        const unsigned act = AGG ? __ballot_sync(0xffffffffu, e_raw < b.count) : 0u;
+        if (e_raw >= b.count) return;
+        atomic_element<ET, R, J64, false, AGG>(b, f, args, e_raw, act, MlpUse{});
     }
 }
 
@@ -910,13 +954,15 @@ static cudaError_t launch_atomic_t(const BucketDev &b, const FieldDev &f, const 
                                    int threads, bool agg, cudaStream_t s) {
     const unsigned blocks = (unsigned)((b.count + threads - 1) / threads);
     if (a.closure == FEA_CLOSURE_MLP) {
-        const size_t smem = mlp_smem_bytes(threads, mlp_rows_per_elem(ET));
+        // one warpgroup per CTA
+        const size_t smem = mlp_smem_bytes(128, mlp_rows_per_elem(ET));
         auto kern = prec == FEA_FP64 ? k_assemble_atomic<ET, double, false, true>
                                      : (b.fp64j ? k_assemble_atomic<ET, float, true, true>
                                                 : k_assemble_atomic<ET, float, false, true>);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<blocks, threads, smem, s>>>(b, f, a);
+        const int64_t blocks128 = (b.count + 127) / 128;
+        kern<<<(unsigned)std::min<int64_t>(blocks128, 2 * (int64_t)device_sms()), 128, smem, s>>>(b, f, a);
     } else if (agg) {
         if (prec == FEA_FP64)
             k_assemble_atomic<ET, double, false, false, true><<<blocks, threads, 0, s>>>(b, f, a);
@@ -967,6 +1013,8 @@ __host__ __device__ __forceinline__ size_t chunk_smem_bytes_dev(const BucketDev 
     const int nen = b.etype == FEA_TET04 ? 4 : (b.etype == FEA_PYR05 ? 5 : (b.etype == FEA_PEN06 ? 6 : 8));
     return sizeof(float4) * (2 * (size_t)b.max_chunk_nodes + (size_t)nen * b.chunk_elems);
 }
+// offset of the fused closure's block after `bytes` of chunk buffers
+__host__ __device__ __forceinline__ size_t mlp_tail_offset(size_t bytes) { return (bytes + 127) & ~(size_t)127; }
 
 __device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
     const float t = s + x;
@@ -1103,19 +1151,26 @@ __device__ __forceinline__ void chunk_body(const BucketDev &b, const FieldDev &f
 // (216 and 150 registers unbounded) are held there too: with 256 threads
 // the channel mesh assembles 5 % faster (measured).
 template <int ET, bool J64, bool COMP, bool MLP = false, bool VAR = true>
-__global__ void __launch_bounds__(256, ((J64 || ET == FEA_HEX08 || ET == FEA_PYR05) && !MLP ? 2 : 1))
+__global__ void __launch_bounds__(MLP ? 128 : 256, (MLP || J64 || ET == FEA_HEX08 || ET == FEA_PYR05) ? 2 : 1)
     k_assemble_chunk(BucketDev b, FieldDev f, AsmArgs args) {
     extern __shared__ float4 smem4[];
-    MlpUse mu{nullptr, nullptr};
+    MlpUse mu{};
+    tc::Warpgroup wg;
     if constexpr (MLP) {
-        // weights and per-warp scratch after the chunk's buffers
-        unsigned char *tail = reinterpret_cast<unsigned char *>(smem4) + chunk_smem_bytes_dev(b);
-        MlpFast *w = reinterpret_cast<MlpFast *>(tail);
-        mlp_copy_fast(static_cast<const MlpFast *>(args.mlp), w);
-        mu.w = w;
-        mu.scratch = tail + sizeof(MlpFast) + (threadIdx.x >> 5) * mlp_warp_scratch_bytes(mlp_rows_per_elem(ET));
+        // the fused closure's block after the chunk's buffers (one warpgroup)
+        unsigned char *tail = reinterpret_cast<unsigned char *>(smem4) + mlp_tail_offset(chunk_smem_bytes_dev(b));
+        mlp_cta_setup(tail, mlp_rows_per_elem(ET), args.mlp, args.err, args.wait_polls, mu, wg);
     }
-    chunk_body<ET, J64, COMP, MLP, VAR>(b, f, args, blockIdx.x, smem4, mu);
+    if constexpr (MLP) {
+        // persistent: two CTAs per SM take the chunks in turn
+        for (int64_t k = blockIdx.x; k < b.n_chunks; k += gridDim.x) {
+            chunk_body<ET, J64, COMP, MLP, VAR>(b, f, args, k, smem4, mu);
+            __syncthreads();   // the chunk buffers are refilled by the next chunk
+        }
+        tc::teardown(wg);
+    } else {
+        chunk_body<ET, J64, COMP, MLP, VAR>(b, f, args, blockIdx.x, smem4, mu);
+    }
     // as a programmatic dependent: the grid it overlapped has completed (and
     // its writes are visible) before this one does, so whatever the stream
     // runs next sees both; a no-op for an ordinary launch
@@ -1134,28 +1189,26 @@ struct BatchItem {
 };
 
 template <bool MLP, bool VAR = true>
-__global__ void __launch_bounds__(256, 2) k_assemble_batch(const BucketDev *__restrict__ bk,
+__global__ void __launch_bounds__(MLP ? 128 : 256, 2) k_assemble_batch(const BucketDev *__restrict__ bk,
                                                         const FieldDev *__restrict__ fd,
                                                         const AsmArgs *__restrict__ ag,
                                                         const BatchItem *__restrict__ items, int64_t n_items,
                                                         unsigned long long *counter, size_t chunk_bytes) {
     extern __shared__ float4 smem4[];
     __shared__ long long item_s;
-    MlpUse mu{nullptr, nullptr};
+    MlpUse mu{};
+    tc::Warpgroup wg;
     if constexpr (MLP) {
-        // element types vary per item: scratch for the largest row count
-        unsigned char *tail = reinterpret_cast<unsigned char *>(smem4) + chunk_bytes;
-        MlpFast *w = reinterpret_cast<MlpFast *>(tail);
-        mlp_copy_fast(static_cast<const MlpFast *>(ag[0].mlp), w);
-        mu.w = w;
-        mu.scratch = tail + sizeof(MlpFast) + (threadIdx.x >> 5) * mlp_warp_scratch_bytes(kMaxNg);
+        // element types vary per item: tiles and scratch for the largest row count
+        unsigned char *tail = reinterpret_cast<unsigned char *>(smem4) + mlp_tail_offset(chunk_bytes);
+        mlp_cta_setup(tail, kMaxNg, ag[0].mlp, ag[0].err, ag[0].wait_polls, mu, wg);
     }
     for (;;) {
         if (threadIdx.x == 0) item_s = (long long)atomicAdd(counter, 1ull);
         __syncthreads();
         const long long w = item_s;
         __syncthreads();
-        if (w >= n_items) return;
+        if (w >= n_items) break;
         const BatchItem it = items[w];
         const BucketDev b = bk[it.bucket];
         const FieldDev f = fd[it.bucket];
@@ -1170,6 +1223,7 @@ __global__ void __launch_bounds__(256, 2) k_assemble_batch(const BucketDev *__re
         }
         __syncthreads();   // shared memory is reused by the next item
     }
+    if constexpr (MLP) tc::teardown(wg);
 }
 
 cudaError_t launch_assemble_batch(const void *buckets, const void *fields, const void *args, const void *items,
@@ -1177,19 +1231,21 @@ cudaError_t launch_assemble_batch(const void *buckets, const void *fields, const
                                   bool variants, cudaStream_t s) {
     if (n_items == 0) return cudaSuccess;
     const size_t chunk_bytes = smem;
-    if (mlp) smem += mlp_smem_bytes(256, kMaxNg);
+    const int threads = mlp ? 128 : 256;   // the fused closure: one warpgroup per CTA
+    if (mlp) smem = mlp_tail_offset(smem) + mlp_smem_bytes(threads, kMaxNg);
     if (smem > kMaxBlockSmem) return cudaErrorInvalidConfiguration;
     auto kern = mlp ? k_assemble_batch<true> : (variants ? k_assemble_batch<false, true> : k_assemble_batch<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
+    if (mlp) per_sm = std::min(per_sm, 2);   // 256 TMEM columns per CTA
     const int64_t grid = std::min<int64_t>(n_items, (int64_t)per_sm * sms);
-    kern<<<(unsigned)grid, 256, smem, s>>>(static_cast<const BucketDev *>(buckets),
+    kern<<<(unsigned)grid, threads, smem, s>>>(static_cast<const BucketDev *>(buckets),
                                            static_cast<const FieldDev *>(fields), static_cast<const AsmArgs *>(args),
                                            static_cast<const BatchItem *>(items), n_items, counter, chunk_bytes);
     return cudaGetLastError();
@@ -1466,20 +1522,22 @@ size_t chunk_kernel_smem(const BucketDev &b, int compensated) {
 size_t chunk_smem_bytes(const BucketDev &b) { return chunk_smem_bytes_dev(b); }
 
 size_t mlp_smem_bytes(int threads, int rows_per_elem) {
-    return sizeof(MlpFast) + (size_t)(threads / 32) * mlp_warp_scratch_bytes(rows_per_elem);
+    (void)threads;   // the fused closure always runs one warpgroup (128 threads) per CTA
+    return std::max(mlp_cta_bytes(rows_per_elem), kMlpMinCtaSmem);
 }
 
 size_t chunk_launch_smem(const BucketDev &b, int threads, int compensated, bool mlp) {
     if (!mlp) return chunk_kernel_smem(b, compensated);
-    return chunk_smem_bytes(b) + mlp_smem_bytes(threads, mlp_rows_per_elem(b.etype));
+    return mlp_tail_offset(chunk_smem_bytes(b)) + mlp_smem_bytes(threads, mlp_rows_per_elem(b.etype));
 }
 
 template <int ET, bool J64, bool COMP>
 static cudaError_t launch_chunk_v(const BucketDev &b, const FieldDev &f, const AsmArgs &a, int threads,
                                   cudaStream_t s) {
     const bool mlp = a.closure == FEA_CLOSURE_MLP;
-    const size_t smem = chunk_smem_bytes(b) + (mlp ? mlp_smem_bytes(threads, mlp_rows_per_elem(ET)) : 0);
+    const size_t smem = chunk_launch_smem(b, threads, 0, mlp);
     if (smem > kMaxBlockSmem) return cudaErrorInvalidConfiguration;
+    if (mlp) threads = 128;   // the fused closure: one warpgroup per CTA
     const bool var = f.conv_form != 0 || f.delta_form != 0;
     auto kern = mlp ? k_assemble_chunk<ET, J64, COMP, true>
                     : (var ? k_assemble_chunk<ET, J64, COMP, false, true> : k_assemble_chunk<ET, J64, COMP, false, false>);
@@ -1487,12 +1545,13 @@ static cudaError_t launch_chunk_v(const BucketDev &b, const FieldDev &f, const A
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
+    const int64_t grid = mlp ? std::min<int64_t>(b.n_chunks, 2 * (int64_t)device_sms()) : b.n_chunks;
     if (!a.pdl) {
-        kern<<<(unsigned)b.n_chunks, threads, smem, s>>>(b, f, a);
+        kern<<<(unsigned)grid, threads, smem, s>>>(b, f, a);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)b.n_chunks);
+    cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3((unsigned)threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;

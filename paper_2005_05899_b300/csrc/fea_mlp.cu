@@ -26,53 +26,63 @@ __device__ __forceinline__ uint16_t to_bf16_bits(float v) {
     return *reinterpret_cast<uint16_t *>(&b);
 }
 
-__device__ __forceinline__ uint16_t f16_bits(float v) {
-    __half h = __float2half_rn(v);
-    return *reinterpret_cast<uint16_t *>(&h);
-}
-
-// the BF16 rounding of v, stored as FP16 (exact unless it underflows FP16's
-// normal range, where FP16 subnormals keep it to 2^-24)
-__device__ __forceinline__ uint16_t bf16_as_f16_bits(float v) {
-    return f16_bits(__uint_as_float((uint32_t)to_bf16_bits(v) << 16));
-}
-
 __device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
 
+// BF16 bits of v and of the remainder v - bf16(v) (hi + lo = v to 2^-17)
+__device__ __forceinline__ void bf16_split(float v, uint16_t &hi, uint16_t &lo) {
+    hi = to_bf16_bits(v);
+    lo = to_bf16_bits(v - __uint_as_float((uint32_t)hi << 16));
+}
+
 __global__ void k_mlp_pack(const float *theta, const float *mean, const float *stdv, float out_scale, MlpWeights *w,
-                           MlpFast *fw) {
+                           tc::MlpTc *fw) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nth = gridDim.x * blockDim.x;
-    // inference layout: the BF16 values of the hidden weights, halved (exact),
-    // in FP16 containers (exact); hidden biases halved
-    for (int k = tid; k < kMlpH * 8; k += nth) {
-        const int o = k / 8, i = k % 8;
-        fw->w1[o][i] = bf16_as_f16_bits(i < kMlpIn ? 0.5f * theta[OFF_W1 + o * kMlpIn + i] : 0.f);
-    }
-    for (int k = tid; k < kMlpH * kWPitch; k += nth) {
-        const int o = k / kWPitch, i = k % kWPitch;
-        const bool in = i < kMlpH;
-        fw->w2[o][i] = bf16_as_f16_bits(in ? 0.5f * theta[OFF_W2 + o * kMlpH + i] : 0.f);
-        fw->w3[o][i] = bf16_as_f16_bits(in ? 0.5f * theta[OFF_W3 + o * kMlpH + i] : 0.f);
-    }
-    for (int k = tid; k < 8 * kWPitch; k += nth) {
-        const int o = k / kWPitch, i = k % kWPitch;
+    // inference layout (tensor-core operands, K blocks of 8): the BF16
+    // values of the hidden weights, halved (exact); the hidden biases halved
+    // and split into BF16 hi and lo parts beside the weights
+    for (int k = tid; k < 2 * kMlpH * 8; k += nth) {
+        const int blk = k / (kMlpH * 8), o = (k / 8) % kMlpH, i = k % 8;
         uint16_t v = 0;
-        if (i < kMlpH && o < 2) {
-            const float x = theta[OFF_W4 + i];
-            const float hi = __uint_as_float((uint32_t)to_bf16_bits(x) << 16);
-            v = f16_bits(o == 0 ? hi : x - hi);
+        if (blk == 0 && i < kMlpIn) {
+            v = to_bf16_bits(0.5f * theta[OFF_W1 + o * kMlpIn + i]);
+        } else if (blk == 0) {
+            uint16_t hi, lo;
+            bf16_split(0.5f * theta[OFF_B1 + o], hi, lo);
+            v = i == 6 ? hi : lo;
         }
-        fw->w4[o][i] = v;
+        fw->w1[blk][o][i] = v;
     }
-    for (int k = tid; k < kMlpH; k += nth) {
-        fw->b1[k] = 0.5f * theta[OFF_B1 + k];
-        fw->b2[k] = 0.5f * theta[OFF_B2 + k];
-        fw->b3[k] = 0.5f * theta[OFF_B3 + k];
+    for (int k = tid; k < 10 * kMlpH * 8; k += nth) {
+        const int blk = k / (kMlpH * 8), o = (k / 8) % kMlpH, i = k % 8;
+        uint16_t v2 = 0, v3 = 0;
+        if (blk < 8) {
+            v2 = to_bf16_bits(0.5f * theta[OFF_W2 + o * kMlpH + 8 * blk + i]);
+            v3 = to_bf16_bits(0.5f * theta[OFF_W3 + o * kMlpH + 8 * blk + i]);
+        } else if (blk == 8 && i < 2) {
+            uint16_t h2, l2, h3, l3;
+            bf16_split(0.5f * theta[OFF_B2 + o], h2, l2);
+            bf16_split(0.5f * theta[OFF_B3 + o], h3, l3);
+            v2 = i == 0 ? h2 : l2;
+            v3 = i == 0 ? h3 : l3;
+        }
+        fw->w2[blk][o][i] = v2;
+        fw->w3[blk][o][i] = v3;
+    }
+    for (int k = tid; k < 10 * 16 * 8; k += nth) {
+        const int blk = k / (16 * 8), o = (k / 8) % 16, i = k % 8;
+        uint16_t v = 0, hi, lo;
+        if (blk < 8 && o < 2) {
+            bf16_split(theta[OFF_W4 + 8 * blk + i], hi, lo);
+            v = o == 0 ? hi : lo;
+        } else if (blk == 8 && o == 0 && i < 2) {
+            bf16_split(theta[OFF_B4], hi, lo);
+            v = i == 0 ? hi : lo;
+        }
+        fw->w4[blk][o][i] = v;
     }
     if (tid == 0) {
-        fw->b4 = theta[OFF_B4];
         for (int k = 0; k < kMlpIn; ++k) {
             fw->mean[k] = mean[k];
             fw->istd[k] = 1.0f / stdv[k];
@@ -120,37 +130,44 @@ __device__ __forceinline__ void copy_weights_to_smem(const MlpWeights *g, MlpWei
     __syncthreads();
 }
 
-// batched forward: raw features x [B][6] -> nu_t y [B]; each warp takes 32
-// rows at a time through a [32][8] bf16 feature tile and a [32] nu_t tile
-constexpr int kFwdTileBytes = 32 * 16 + 32 * 4;
+// batched forward: raw features x [B][6] -> C y [B] on the tensor cores;
+// a CTA (one warpgroup of 128 threads) takes 256 rows at a time as two
+// 128-row tiles (thread t: rows t and 128 + t)
+constexpr int kFwdTiles = 2;
+constexpr size_t kFwdSmem = sizeof(tc::MlpTc) + tc::feat_bytes(kFwdTiles) + kFwdTiles * 128 * 4 + 64;
 
-__global__ void __launch_bounds__(256) k_mlp_forward(const MlpFast *wg, const float *x, int64_t B, float *y) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    MlpFast *w = reinterpret_cast<MlpFast *>(smem);
-    mlp_copy_fast(wg, w);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char *mine = smem + sizeof(MlpFast) + warp * kFwdTileBytes;
-    uint32_t *feat = reinterpret_cast<uint32_t *>(mine);
-    float *nut = reinterpret_cast<float *>(mine + 32 * 16);
-    const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32; base < B; base += warps_total * 32) {
-        const int64_t r = base + lane;
-        float xn[kMlpIn];
+__global__ void __launch_bounds__(128) k_mlp_forward(const tc::MlpTc *wg, const float *x, int64_t B, float *y,
+                                                     unsigned *err) {
+    extern __shared__ __align__(128) unsigned char fwd_smem[];
+    tc::MlpTc *w = reinterpret_cast<tc::MlpTc *>(fwd_smem);
+    unsigned char *feat = fwd_smem + sizeof(tc::MlpTc);
+    unsigned char *zero = feat + kFwdTiles * tc::kRows * 16;
+    float *outb = reinterpret_cast<float *>(zero + tc::kRows * 16);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(outb + kFwdTiles * tc::kRows);
+    tc::Warpgroup wgs;
+    tc::setup(wg, w, zero, bars, wgs, err, 0);
+    const int row = threadIdx.x;
+    for (int64_t base = (int64_t)blockIdx.x * (kFwdTiles * tc::kRows); base < B;
+         base += (int64_t)gridDim.x * (kFwdTiles * tc::kRows)) {
+        for (int t = 0; t < kFwdTiles; ++t) {
+            const int64_t r = base + t * tc::kRows + row;
+            float xn[kMlpIn];
 #pragma unroll
-        for (int k = 0; k < kMlpIn; ++k) {
-            const float v = r < B ? (x[r * kMlpIn + k] - w->mean[k]) * w->istd[k] : 0.0f;
-            xn[k] = isfinite(v) ? fminf(fmaxf(v, -kFeatClamp), kFeatClamp) : 0.0f;
+            for (int k = 0; k < kMlpIn; ++k) {
+                const float v = r < B ? (x[r * kMlpIn + k] - w->mean[k]) * w->istd[k] : 0.0f;
+                xn[k] = isfinite(v) ? fminf(fmaxf(v, -kFeatClamp), kFeatClamp) : 0.0f;
+            }
+            *reinterpret_cast<uint4 *>(feat + (t * tc::kRows + row) * 16) =
+                make_uint4(tc::pack_bf16x2(xn[0], xn[1]), tc::pack_bf16x2(xn[2], xn[3]),
+                           tc::pack_bf16x2(xn[4], xn[5]), tc::kOnesWord);
         }
-        feat[lane * 4 + 0] = pack_f16x2(xn[0], xn[1]);
-        feat[lane * 4 + 1] = pack_f16x2(xn[2], xn[3]);
-        feat[lane * 4 + 2] = pack_f16x2(xn[4], xn[5]);
-        feat[lane * 4 + 3] = 0u;
-        __syncwarp();
-        mlp_rows32(*w, reinterpret_cast<const uint16_t *>(feat), nut, 0);
-        __syncwarp();
-        if (r < B) y[r] = nut[lane];
-        __syncwarp();
+        tc::run(wgs, w, feat, zero, kFwdTiles, outb + row, tc::kRows);
+        for (int t = 0; t < kFwdTiles; ++t) {
+            const int64_t r = base + t * tc::kRows + row;
+            if (r < B) y[r] = outb[t * tc::kRows + row];
+        }
     }
+    tc::teardown(wgs);
 }
 
 // ---- training step ------------------------------------------------------------
@@ -418,28 +435,29 @@ __global__ void k_adam(float *theta, const float *grad, float *m1, float *m2, in
 }  // namespace
 
 // One device block holds the training layout (MlpWeights) followed by the
-// inference layout (MlpFast).
+// inference layout (tc::MlpTc).
 constexpr size_t kFastOffset = (sizeof(MlpWeights) + 255) & ~size_t(255);
 
-size_t mlp_weights_bytes() { return kFastOffset + sizeof(MlpFast); }
+size_t mlp_weights_bytes() { return kFastOffset + sizeof(tc::MlpTc); }
 int mlp_param_count() { return kMlpParams; }
 const void *mlp_fast_ptr(const void *w) { return static_cast<const unsigned char *>(w) + kFastOffset; }
 
 cudaError_t launch_mlp_pack(const float *theta, const float *mean, const float *stdv, float out_scale, void *w,
                             cudaStream_t s) {
     k_mlp_pack<<<16, 256, 0, s>>>(theta, mean, stdv, out_scale, static_cast<MlpWeights *>(w),
-                                  reinterpret_cast<MlpFast *>(static_cast<unsigned char *>(w) + kFastOffset));
+                                  reinterpret_cast<tc::MlpTc *>(static_cast<unsigned char *>(w) + kFastOffset));
     return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_forward(const void *w, const float *x, int64_t B, float *y, int sms, cudaStream_t s) {
+cudaError_t launch_mlp_forward(const void *w, const float *x, int64_t B, float *y, int sms, unsigned *err,
+                               cudaStream_t s) {
     if (B <= 0) return cudaSuccess;
-    const size_t smem = sizeof(MlpFast) + 8 * kFwdTileBytes;
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
     if (e != cudaSuccess) return e;
-    const int64_t want = (B + 255) / 256;
-    const int grid = (int)std::min<int64_t>(want, (int64_t)sms * 4);
-    k_mlp_forward<<<grid, 256, smem, s>>>(static_cast<const MlpFast *>(mlp_fast_ptr(w)), x, B, y);
+    // two CTAs per SM: each holds 256 of the SM's 512 TMEM columns
+    const int64_t want = (B + kFwdTiles * tc::kRows - 1) / (kFwdTiles * tc::kRows);
+    const int grid = (int)std::min<int64_t>(want, (int64_t)sms * 2);
+    k_mlp_forward<<<grid, 128, kFwdSmem, s>>>(static_cast<const tc::MlpTc *>(mlp_fast_ptr(w)), x, B, y, err);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,399 @@
+// Learned eddy-viscosity closure on the fifth-generation tensor cores
+// (tcgen05, sm_103a): a 6 -> 64 -> 64 -> 64 -> 1 MLP (SiLU hidden layers,
+// softplus output) evaluated over tiles of M = 128 rows by one warpgroup
+// (4 warps, thread = row), BF16 operands and FP32 accumulators in tensor
+// memory (TMEM).
+//
+// Per tile and layer:
+//   layer 1   D[128 x 64]  = F[128 x 16] W1'^T        A: features in shared memory
+//   layer 2,3 D[128 x 64]  = H[128 x 80] W'^T         A: activations in TMEM
+//   output    D[128 x 16]  = H[128 x 80] W4'^T        (columns 0, 1 used)
+// with the biases folded into the products: feature columns 6, 7 and
+// activation columns 64, 65 hold 1, the matching weight columns the bias
+// split into its BF16 hi and lo parts (FP32 values to 2^-17).  The hidden layers'
+// weights and biases are stored halved (exact in BF16), so an accumulator
+// holds h = z/2 and SiLU(z) = z sigmoid(z) = h (1 + tanh h): one packed FP16
+// tanh per two activations, the rest in FP32 and one rounding to the next
+// layer's BF16 operand.  The output weights and
+// bias are split into BF16 hi and lo parts (rows 0 and 1 of W4'), so
+// z = D[:, 0] + D[:, 1] carries the FP32 values to 2^-17.
+//
+// Shared-memory operands use the no-swizzle K-major layout: 8 x 16-byte
+// core matrices, the 8-row groups 128 bytes apart (SBO) and the K blocks of
+// 8 elements LBO bytes apart; with that choice a [rows][8] BF16 array is one
+// K block, row r at byte 16 r.
+//
+// Each warpgroup owns 256 TMEM columns: two slots of {accumulator 64
+// columns, activations 32 columns, a constant "ones" block 8 columns}, so
+// that the epilogue of one tile (TMEM -> registers -> SiLU -> TMEM) overlaps
+// the MMAs of the other.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fea {
+namespace tc {
+
+constexpr int kRows = 128;          // rows of a tile (TMEM lanes)
+constexpr int kH = 64;              // hidden width
+constexpr int kColsPerWg = 256;     // TMEM columns a warpgroup allocates
+constexpr int kSlotCols = 128;      // columns per slot
+constexpr int kActCol = 64;         // activations within a slot (32 columns of BF16 pairs)
+constexpr int kOnesCol = 96;        // the bias block's constant ones (8 columns)
+constexpr uint32_t kOnesWord = 0x3F803F80u;   // BF16 pair (1, 1)
+constexpr uint32_t kDefaultPolls = 1u << 20;
+
+// Inference weights in the tensor cores' shared-memory operand layout, plus
+// the feature normalisation and the training envelope.  Copied into shared
+// memory by every kernel that evaluates the network.
+struct __align__(128) MlpTc {
+    uint16_t w1[2][kH][8];    // K blocks of W1/2 [n][k]: block 0 columns 0..5 weights, 6, 7 hi/lo of b1/2; block 1 zero
+    uint16_t w2[10][kH][8];   // K blocks 0..7: W2/2; block 8: columns 0, 1 = hi/lo of b2/2; block 9 zero
+    uint16_t w3[10][kH][8];
+    uint16_t w4[10][16][8];   // rows 0, 1: hi and lo parts of w4; block 8 row 0: hi/lo of b4; rows 2..15 zero
+    float mean[6], istd[6];
+    float env_lo[6], env_hi[6];   // training envelope in normalised units (+-inf: none)
+    float out_scale;
+    int env_on;                    // any finite envelope bound
+};
+
+// shared-memory bytes, after the MlpTc block, of one warpgroup's feature tiles
+// ([tiles][128][8] BF16) plus the zero K block every feature tile shares
+__host__ __device__ constexpr size_t feat_bytes(int tiles) { return (size_t)tiles * kRows * 16 + (size_t)kRows * 16; }
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// ---- PTX wrappers ---------------------------------------------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(dst)), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy shared-memory writes made visible to the tensor cores' reads
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// D (+)= A B^T, A and B from shared-memory descriptors
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// D (+)= A B^T, A from TMEM (row r in lane r, BF16 pairs per column)
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+        "r"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// arrive (once) on the mbarrier when every MMA this thread issued so far has completed
+__device__ __forceinline__ void commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+#define FEA_TC_R8(b) "=r"(r[b + 0]), "=r"(r[b + 1]), "=r"(r[b + 2]), "=r"(r[b + 3]), "=r"(r[b + 4]), "=r"(r[b + 5]), \
+                     "=r"(r[b + 6]), "=r"(r[b + 7])
+#define FEA_TC_W8(b) "+r"(r[b + 0]), "+r"(r[b + 1]), "+r"(r[b + 2]), "+r"(r[b + 3]), "+r"(r[b + 4]), "+r"(r[b + 5]), \
+                     "+r"(r[b + 6]), "+r"(r[b + 7])
+#define FEA_TC_S8(b) "r"(r[b + 0]), "r"(r[b + 1]), "r"(r[b + 2]), "r"(r[b + 3]), "r"(r[b + 4]), "r"(r[b + 5]), \
+                     "r"(r[b + 6]), "r"(r[b + 7])
+
+// 32 consecutive FP32 columns of this thread's lane
+__device__ __forceinline__ void ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : FEA_TC_R8(0), FEA_TC_R8(8), FEA_TC_R8(16), FEA_TC_R8(24)
+        : "r"(taddr));
+}
+// completes the loads above; the registers pass through it so that no use is
+// scheduled before it
+__device__ __forceinline__ void wait_ld(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : FEA_TC_W8(0), FEA_TC_W8(8), FEA_TC_W8(16), FEA_TC_W8(24)::"memory");
+}
+__device__ __forceinline__ void ld2(uint32_t taddr, uint32_t &a, uint32_t &b) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(a), "=r"(b) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(a), "+r"(b)::"memory");
+}
+__device__ __forceinline__ void st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+        "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        FEA_TC_S8(0), FEA_TC_S8(8), FEA_TC_S8(16), FEA_TC_S8(24)
+        : "memory");
+}
+__device__ __forceinline__ void st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), FEA_TC_S8(0)
+                 : "memory");
+}
+__device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+#undef FEA_TC_R8
+#undef FEA_TC_W8
+#undef FEA_TC_S8
+
+__device__ __forceinline__ void mb_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mb_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mb_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Shared-memory matrix descriptor: no swizzle, K-major; start, LBO and SBO
+// in bytes (multiples of 16); bit 46 = descriptor version 1 (sm_100 family).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    uint32_t h;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(hi), "f"(lo));
+    return h;
+}
+// SiLU of two halved pre-activations (FP32 accumulator bits) as one BF16
+// pair: h + h tanh h, the tanh packed in FP16 (one special-function
+// operation for both), the product and sum in FP32 (no cancellation at
+// h << 0 beyond the tanh's own error), then one rounding to BF16.
+__device__ __forceinline__ uint32_t silu_bf16x2(uint32_t lo_bits, uint32_t hi_bits) {
+    const float hl = __uint_as_float(lo_bits), hh = __uint_as_float(hi_bits);
+    uint32_t h16, t16;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h16) : "f"(hh), "f"(hl));
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(t16) : "r"(h16));
+    float tl, th;
+    asm("{\n .reg .f16 a, b;\n mov.b32 {a, b}, %2;\n cvt.f32.f16 %0, a;\n cvt.f32.f16 %1, b;\n}\n"
+        : "=f"(tl), "=f"(th)
+        : "r"(t16));
+    const float2 hv = make_float2(hl, hh);
+    const float2 s = __ffma2_rn(hv, make_float2(tl, th), hv);
+    return pack_bf16x2(s.x, s.y);
+}
+
+// One warpgroup's tensor-core state: TMEM base (lane 0, first of its 256
+// columns), the mbarriers (MMA completion per slot, count 1; activations
+// ready per slot, count 128), phase bits (bit s: mma[s], bit 2 + s: rdy[s])
+// and the polls a wait may take before it gives up.
+struct Warpgroup {
+    uint32_t tmem;
+    uint64_t *mma, *rdy;
+    uint32_t ph;
+    uint32_t polls;
+    bool issuer;     // the one thread that issues the MMAs
+    bool dead;       // a wait gave up: the rest of the network is skipped
+    unsigned *err;   // device error word (ERR_TIMEOUT = 4 on a wait that gave up)
+
+    // wait of all 32 lanes of a warp for the next phase of an MMA barrier:
+    // the outcome is warp-uniform
+    __device__ __forceinline__ bool wait_warp(int s) {
+        if (__any_sync(0xffffffffu, dead)) {
+            dead = true;
+            return false;
+        }
+        const uint32_t par = (ph >> s) & 1u;
+        ph ^= 1u << s;
+        for (uint32_t i = 0; i < polls; ++i)
+            if (__all_sync(0xffffffffu, mb_try(&mma[s], par))) return true;
+        dead = true;
+        if ((threadIdx.x & 31) == 0) atomicOr(err, 4u);
+        return false;
+    }
+    // wait of the issuer alone for all 128 rows of slot s to be ready
+    __device__ __forceinline__ bool wait_ready(int s) {
+        const uint32_t par = (ph >> (2 + s)) & 1u;
+        ph ^= 1u << (2 + s);
+        if (dead) return false;
+        for (uint32_t i = 0; i < polls; ++i)
+            if (mb_try(&rdy[s], par)) return true;
+        dead = true;
+        atomicOr(err, 4u);
+        return false;
+    }
+};
+
+// Set-up by all threads of a CTA of 128 threads (one warpgroup): copies the
+// weights into shared memory, zeroes the shared zero K block, allocates the
+// TMEM columns (warp 0), initialises the mbarriers and writes the constant
+// ones block of both slots.  `bars` holds 4 mbarriers and the TMEM address.
+__device__ __forceinline__ void setup(const MlpTc *gw, MlpTc *sw, unsigned char *zero_block, uint64_t *bars,
+                                      Warpgroup &wg, unsigned *err, uint32_t polls) {
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(gw);
+        int4 *dst = reinterpret_cast<int4 *>(sw);
+        for (int k = threadIdx.x; k < (int)(sizeof(MlpTc) / 16); k += blockDim.x) dst[k] = src[k];
+        int4 *z = reinterpret_cast<int4 *>(zero_block);
+        for (int k = threadIdx.x; k < kRows; k += blockDim.x) z[k] = make_int4(0, 0, 0, 0);
+    }
+    uint32_t *taddr_slot = reinterpret_cast<uint32_t *>(bars + 4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        tmem_alloc(taddr_slot, kColsPerWg);
+        tmem_relinquish();
+    }
+    if (threadIdx.x == 0) {
+        mb_init(&bars[0], 1);
+        mb_init(&bars[1], 1);
+        mb_init(&bars[2], kRows);
+        mb_init(&bars[3], kRows);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_async_smem();   // the weights and the zero block, for the tensor cores
+    fence_before();
+    __syncthreads();
+    fence_after();
+    wg.tmem = *taddr_slot;
+    wg.mma = bars;
+    wg.rdy = bars + 2;
+    wg.ph = 0;
+    wg.polls = polls ? polls : kDefaultPolls;
+    wg.issuer = threadIdx.x == 0;
+    wg.dead = false;
+    wg.err = err;
+    // the ones block of each slot: column kOnesCol holds (1, 1), the rest 0
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    uint32_t ones[8] = {kOnesWord, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    st8(wg.tmem + lane_base + kOnesCol, ones);
+    st8(wg.tmem + lane_base + kSlotCols + kOnesCol, ones);
+    wait_st();
+    (void)lane;
+    fence_before();
+    __syncthreads();
+    fence_after();
+}
+
+// Release of the TMEM columns (all threads of the CTA, after their last use).
+__device__ __forceinline__ void teardown(const Warpgroup &wg) {
+    fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        fence_after();
+        tmem_dealloc(wg.tmem, kColsPerWg);
+    }
+}
+
+// MMAs of one layer for one slot (issuer only).
+//   layer 0: features of tile `tile` (shared memory) x W1'
+//   layer 1, 2: activations (TMEM) x W2', W3'
+//   layer 3: activations x W4' (N = 16)
+__device__ __forceinline__ void issue_layer(const Warpgroup &wg, const MlpTc *sw, uint32_t feat_tile,
+                                            uint32_t zero_addr, int layer, int slot) {
+    const uint32_t d = wg.tmem + (uint32_t)(slot * kSlotCols);
+    if (layer == 0) {
+        // rows 16 bytes apart (8-row groups 128 B apart); the second K block is the shared zero block
+        const uint64_t a = sdesc(feat_tile, zero_addr - feat_tile, 128);
+        const uint64_t b = sdesc(su32(sw->w1), kH * 16, 128);
+        mma_ss(d, a, b, idesc_bf16(kRows, kH), 0u);
+        return;
+    }
+    const uint32_t act = d + kActCol;
+    if (layer < 3) {
+        const uint32_t w = su32(layer == 1 ? &sw->w2[0][0][0] : &sw->w3[0][0][0]);
+#pragma unroll
+        for (int kk = 0; kk < 5; ++kk)
+            mma_ts(d, act + 8 * kk, sdesc(w + kk * 2 * kH * 16, kH * 16, 128), idesc_bf16(kRows, kH), kk > 0);
+    } else {
+        const uint32_t w = su32(&sw->w4[0][0][0]);
+#pragma unroll
+        for (int kk = 0; kk < 5; ++kk)
+            mma_ts(d, act + 8 * kk, sdesc(w + kk * 2 * 16 * 16, 16 * 16, 128), idesc_bf16(kRows, 16), kk > 0);
+    }
+}
+
+__device__ __forceinline__ float softplus_tc(float z) { return z > 20.0f ? z : log1pf(__expf(z)); }
+
+// The network over `tiles` feature tiles of this warpgroup (tile g at
+// feat + 2048 g, this thread's row 32 (warp % 4) + lane), called by all 128
+// threads after they have written their feature rows.  Writes the output
+// coefficient C = out_scale softplus(z) of this thread's row of tile g to
+// out[g * out_stride].  Every wait is bounded: one that gives up sets the
+// error word and the remaining outputs are not meaningful (no hang).
+__device__ __forceinline__ void run(Warpgroup &wg, const MlpTc *sw, const unsigned char *feat,
+                                    const unsigned char *zero_block, int tiles, float *out, int out_stride) {
+    const int warp = threadIdx.x >> 5;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const uint32_t f0 = su32(feat), z0 = su32(zero_block);
+    fence_async_smem();
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    if (wg.issuer && !wg.dead) {
+        fence_after();
+        for (int s = 0; s < 2 && s < tiles; ++s) {
+            issue_layer(wg, sw, f0 + (uint32_t)s * kRows * 16, z0, 0, s);
+            commit(&wg.mma[s]);
+        }
+    }
+    __syncwarp();
+    for (int p = 0; p < tiles; p += 2) {
+        const int np = tiles - p < 2 ? tiles - p : 2;
+        // hidden layers: TMEM -> SiLU -> TMEM, then the next layer's MMAs
+        for (int layer = 1; layer <= 3; ++layer) {
+            for (int s = 0; s < np; ++s) {
+                wg.wait_warp(s);
+                fence_after();
+                const uint32_t acc = wg.tmem + lane_base + (uint32_t)(s * kSlotCols);
+                uint32_t v[32], o[32];
+                ld32(acc, v);
+                wait_ld(v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) o[j] = silu_bf16x2(v[2 * j], v[2 * j + 1]);
+                ld32(acc + 32, v);
+                wait_ld(v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) o[16 + j] = silu_bf16x2(v[2 * j], v[2 * j + 1]);
+                st32(acc + kActCol, o);
+                wait_st();
+                fence_before();
+                mb_arrive(&wg.rdy[s]);
+                if (wg.issuer && wg.wait_ready(s)) {
+                    fence_after();
+                    issue_layer(wg, sw, 0, 0, layer, s);
+                    commit(&wg.mma[s]);
+                }
+                __syncwarp();
+            }
+        }
+        // output layer: z = D[:, 0] + D[:, 1]; then the next pair's first layer
+        for (int s = 0; s < np; ++s) {
+            wg.wait_warp(s);
+            fence_after();
+            uint32_t a, b;
+            ld2(wg.tmem + lane_base + (uint32_t)(s * kSlotCols), a, b);
+            const float z = __uint_as_float(a) + __uint_as_float(b);
+            out[(p + s) * out_stride] = sw->out_scale * softplus_tc(z);
+            fence_before();
+            mb_arrive(&wg.rdy[s]);
+            if (wg.issuer && wg.wait_ready(s) && p + 2 + s < tiles) {
+                fence_after();
+                issue_layer(wg, sw, f0 + (uint32_t)(p + 2 + s) * kRows * 16, z0, 0, s);
+                commit(&wg.mma[s]);
+            }
+            __syncwarp();
+        }
+    }
+}
+
+}  // namespace tc
+}  // namespace fea
