@@ -517,9 +517,9 @@ fea_status fea_sync_status(fea_ctx *ctx, void *stream);
 fea_status fea_fp32_peak(fea_ctx *ctx, double *tflops_ffma, double *tflops_ffma2, void *stream);
 
 /* Poll limit of the bounded device-side waits of the TET04 assembly kernel
- * (mixed precision, chunk scatter), which otherwise give up after about four
- * million polls of an mbarrier phase, each of which may suspend the warp for
- * a hardware-chosen time: polls > 0 sets the limit and makes every poll a
+ * (mixed precision, chunk scatter), which otherwise give up after 131,072
+ * polls of an mbarrier phase, each of which suspends the warp until the
+ * phase completes or 20 us pass: polls > 0 sets the limit and makes every poll a
  * non-suspending test, 0 restores the default.  A wait that gives up makes
  * its CTA stop assembling, lets
  * the copies it has in flight land, and sets the device error word

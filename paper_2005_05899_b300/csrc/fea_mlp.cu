@@ -29,27 +29,38 @@ __device__ __forceinline__ uint16_t to_bf16_bits(float v) {
 __device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
 
-// BF16 bits of v and of the remainder v - bf16(v) (hi + lo = v to 2^-17)
-__device__ __forceinline__ void bf16_split(float v, uint16_t &hi, uint16_t &lo) {
-    hi = to_bf16_bits(v);
-    lo = to_bf16_bits(v - __uint_as_float((uint32_t)hi << 16));
+__device__ __forceinline__ uint16_t f16_bits(float v) {
+    __half h = __float2half_rn(v);
+    return *reinterpret_cast<uint16_t *>(&h);
+}
+// the BF16 rounding of v, as FP16 bits (exact unless it underflows FP16's
+// normal range, where FP16 subnormals keep it to 2^-24)
+__device__ __forceinline__ uint16_t bf16_as_f16_bits(float v) {
+    return f16_bits(__uint_as_float((uint32_t)to_bf16_bits(v) << 16));
+}
+// FP16 bits of v and of the remainder v - hi: hi + lo = v to about 2^-22
+// relative; hi = the FP16 value of v
+__device__ __forceinline__ void f16_split(float v, uint16_t &hi, uint16_t &lo) {
+    hi = f16_bits(v);
+    lo = f16_bits(v - __half2float(__ushort_as_half(hi)));
 }
 
 __global__ void k_mlp_pack(const float *theta, const float *mean, const float *stdv, float out_scale, MlpWeights *w,
                            tc::MlpTc *fw) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nth = gridDim.x * blockDim.x;
-    // inference layout (tensor-core operands, K blocks of 8): the BF16
-    // values of the hidden weights, halved (exact); the hidden biases halved
-    // and split into BF16 hi and lo parts beside the weights
+    // inference layout (tensor-core operands, K blocks of 8, FP16 bits): the
+    // BF16 values of the hidden weights, halved (exact); the hidden biases
+    // halved and split into hi and lo parts beside the weights; the output
+    // weights and bias as hi = their BF16 value and lo = the rest
     for (int k = tid; k < 2 * kMlpH * 8; k += nth) {
         const int blk = k / (kMlpH * 8), o = (k / 8) % kMlpH, i = k % 8;
         uint16_t v = 0;
         if (blk == 0 && i < kMlpIn) {
-            v = to_bf16_bits(0.5f * theta[OFF_W1 + o * kMlpIn + i]);
+            v = bf16_as_f16_bits(0.5f * theta[OFF_W1 + o * kMlpIn + i]);
         } else if (blk == 0) {
             uint16_t hi, lo;
-            bf16_split(0.5f * theta[OFF_B1 + o], hi, lo);
+            f16_split(0.5f * theta[OFF_B1 + o], hi, lo);
             v = i == 6 ? hi : lo;
         }
         fw->w1[blk][o][i] = v;
@@ -58,12 +69,12 @@ __global__ void k_mlp_pack(const float *theta, const float *mean, const float *s
         const int blk = k / (kMlpH * 8), o = (k / 8) % kMlpH, i = k % 8;
         uint16_t v2 = 0, v3 = 0;
         if (blk < 8) {
-            v2 = to_bf16_bits(0.5f * theta[OFF_W2 + o * kMlpH + 8 * blk + i]);
-            v3 = to_bf16_bits(0.5f * theta[OFF_W3 + o * kMlpH + 8 * blk + i]);
+            v2 = bf16_as_f16_bits(0.5f * theta[OFF_W2 + o * kMlpH + 8 * blk + i]);
+            v3 = bf16_as_f16_bits(0.5f * theta[OFF_W3 + o * kMlpH + 8 * blk + i]);
         } else if (blk == 8 && i < 2) {
             uint16_t h2, l2, h3, l3;
-            bf16_split(0.5f * theta[OFF_B2 + o], h2, l2);
-            bf16_split(0.5f * theta[OFF_B3 + o], h3, l3);
+            f16_split(0.5f * theta[OFF_B2 + o], h2, l2);
+            f16_split(0.5f * theta[OFF_B3 + o], h3, l3);
             v2 = i == 0 ? h2 : l2;
             v3 = i == 0 ? h3 : l3;
         }
@@ -72,14 +83,13 @@ __global__ void k_mlp_pack(const float *theta, const float *mean, const float *s
     }
     for (int k = tid; k < 10 * 16 * 8; k += nth) {
         const int blk = k / (16 * 8), o = (k / 8) % 16, i = k % 8;
-        uint16_t v = 0, hi, lo;
-        if (blk < 8 && o < 2) {
-            bf16_split(theta[OFF_W4 + 8 * blk + i], hi, lo);
-            v = o == 0 ? hi : lo;
-        } else if (blk == 8 && o == 0 && i < 2) {
-            bf16_split(theta[OFF_B4], hi, lo);
-            v = i == 0 ? hi : lo;
-        }
+        uint16_t v = 0;
+        auto hilo = [&](float x, int part) {
+            const float hi = __uint_as_float((uint32_t)to_bf16_bits(x) << 16);
+            return part == 0 ? f16_bits(hi) : f16_bits(x - hi);
+        };
+        if (blk < 8 && o < 2) v = hilo(theta[OFF_W4 + 8 * blk + i], o);
+        else if (blk == 8 && o == 0 && i < 2) v = hilo(theta[OFF_B4], i);
         fw->w4[blk][o][i] = v;
     }
     if (tid == 0) {
@@ -158,8 +168,8 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const tc::MlpTc *wg, const 
                 xn[k] = isfinite(v) ? fminf(fmaxf(v, -kFeatClamp), kFeatClamp) : 0.0f;
             }
             *reinterpret_cast<uint4 *>(feat + (t * tc::kRows + row) * 16) =
-                make_uint4(tc::pack_bf16x2(xn[0], xn[1]), tc::pack_bf16x2(xn[2], xn[3]),
-                           tc::pack_bf16x2(xn[4], xn[5]), tc::kOnesWord);
+                make_uint4(tc::pack_f16x2(xn[0], xn[1]), tc::pack_f16x2(xn[2], xn[3]),
+                           tc::pack_f16x2(xn[4], xn[5]), tc::kOnesWord);
         }
         tc::run(wgs, w, feat, zero, kFwdTiles, outb + row, tc::kRows);
         for (int t = 0; t < kFwdTiles; ++t) {

@@ -11,7 +11,7 @@
 // nu_t = C Delta^2 g (zero where g = 0, whose features are all zero).
 //
 // Inference (fused closure, batched forward) runs on the tcgen05 tensor
-// cores over 128-row tiles (fea_tc.cuh).  The training step below keeps
+// cores over 128-row tiles, FP16 operands and activations (fea_tc.cuh).  The training step below keeps
 // warp-level mma.sync m16n8k16 tiles (row.col, BF16 in, FP32 accumulate):
 // for lane l, g = l / 4, t = l % 4; an A fragment holds rows (g, g+8) and
 // columns (2t, 2t+1, 2t+8, 2t+9) of a 16 x 16 tile; a C fragment holds rows
@@ -129,9 +129,10 @@ __device__ __forceinline__ void mlp_output(const uint32_t h[4][4], const float *
 
 // ---------------------------------------------------------------------------
 // Inference of the same network for the fused closure and the batched
-// forward runs on the tcgen05 tensor cores (fea_tc.cuh): BF16 weights (the
-// values the network is trained with) and BF16 activations, FP32
-// accumulation.  A feature row is 8 BF16 values (16 bytes):
+// forward runs on the tcgen05 tensor cores (fea_tc.cuh): the BF16 weight
+// values the network is trained with, held exactly as FP16 operands, FP16
+// activations and hidden-layer accumulators, an FP32 output layer.  A
+// feature row is 8 FP16 values (16 bytes):
 // x1..x6 normalised and clamped to +-kFeatClamp, then 1 (the bias input)
 // and 0.  Normalised features are clamped (far outside any training data)
 // so that a degenerate gradient cannot overflow the products.
@@ -149,7 +150,7 @@ __host__ __device__ constexpr size_t mlp_warp_scratch_bytes(int ng) {
 
 // The five invariant features of G over powers of g = |G| (the element
 // Reynolds number is the sixth, mlp_re_bits), normalised and clamped, as
-// BF16 pairs: word 0 = (x1, x2), word 1 = (x3, x4), word 2 = (x5, 0).
+// FP16 pairs: word 0 = (x1, x2), word 1 = (x3, x4), word 2 = (x5, 0).
 // *gout = g.
 // A vanishing gradient gives zero features (and a zero nu_t: the caller
 // multiplies by g).  Non-finite values (degenerate elements, idle lanes)
@@ -204,13 +205,13 @@ __device__ __forceinline__ bool mlp_gp_words(const float G[3][3], const tc::MlpT
         inside = inside && (!some || (v >= w.env_lo[k] && v <= w.env_hi[k]));   // false for NaN
         xn[k] = isfinite(v) ? fminf(fmaxf(v, -kFeatClamp), kFeatClamp) : 0.0f;
     }
-    words[0] = tc::pack_bf16x2(xn[0], xn[1]);
-    words[1] = tc::pack_bf16x2(xn[2], xn[3]);
-    words[2] = tc::pack_bf16x2(xn[4], 0.0f);
+    words[0] = tc::pack_f16x2(xn[0], xn[1]);
+    words[1] = tc::pack_f16x2(xn[2], xn[3]);
+    words[2] = tc::pack_f16x2(xn[4], 0.0f);
     return inside;
 }
 
-// BF16 bits of the normalised (clamped) element Reynolds number
+// FP16 bits of the normalised (clamped) element Reynolds number
 // log(Delta^2 g / nu) (zero raw feature where g = 0); *inside: within the
 // training envelope
 __device__ __forceinline__ uint16_t mlp_re_bits(float delta, float g, float nu, const tc::MlpTc &w, bool *inside) {
@@ -218,7 +219,7 @@ __device__ __forceinline__ uint16_t mlp_re_bits(float delta, float g, float nu, 
     float v = ((some ? __logf(delta * delta * g / nu) : 0.f) - w.mean[5]) * w.istd[5];
     *inside = !some || (v >= w.env_lo[5] && v <= w.env_hi[5]);
     v = isfinite(v) ? fminf(fmaxf(v, -kFeatClamp), kFeatClamp) : 0.0f;
-    return (uint16_t)(tc::pack_bf16x2(v, 0.0f) & 0xffffu);
+    return (uint16_t)(tc::pack_f16x2(v, 0.0f) & 0xffffu);
 }
 
 }  // namespace fea

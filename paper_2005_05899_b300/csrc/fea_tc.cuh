@@ -1,26 +1,30 @@
 // Learned eddy-viscosity closure on the fifth-generation tensor cores
 // (tcgen05, sm_103a): a 6 -> 64 -> 64 -> 64 -> 1 MLP (SiLU hidden layers,
 // softplus output) evaluated over tiles of M = 128 rows by one warpgroup
-// (4 warps, thread = row), BF16 operands and FP32 accumulators in tensor
-// memory (TMEM).
+// (4 warps, thread = row): FP16 operands holding the network's BF16 weight
+// values exactly, FP16 activations, accumulators in tensor memory (TMEM).
 //
 // Per tile and layer:
-//   layer 1   D[128 x 64]  = F[128 x 16] W1'^T        A: features in shared memory
-//   layer 2,3 D[128 x 64]  = H[128 x 80] W'^T         A: activations in TMEM
-//   output    D[128 x 16]  = H[128 x 80] W4'^T        (columns 0, 1 used)
+//   layer 1   D[128 x 64]  = F[128 x 16] W1'^T   FP16 D   A: features in shared memory
+//   layer 2,3 D[128 x 64]  = H[128 x 80] W'^T    FP16 D   A: activations in TMEM
+//   output    D[128 x 16]  = H[128 x 80] W4'^T   FP32 D   (columns 0, 1 used)
 // with the biases folded into the products: feature columns 6, 7 and
 // activation columns 64, 65 hold 1, the matching weight columns the bias
-// split into its BF16 hi and lo parts (FP32 values to 2^-17).  The hidden layers'
-// weights and biases are stored halved (exact in BF16), so an accumulator
-// holds h = z/2 and SiLU(z) = z sigmoid(z) = h (1 + tanh h): one packed FP16
-// tanh per two activations, the rest in FP32 and one rounding to the next
-// layer's BF16 operand.  The output weights and
-// bias are split into BF16 hi and lo parts (rows 0 and 1 of W4'), so
-// z = D[:, 0] + D[:, 1] carries the FP32 values to 2^-17.
+// split into FP16 hi and lo parts.  The hidden layers' weights and biases are
+// stored halved (exact), so an accumulator holds h = z/2 and SiLU(z) =
+// z sigmoid(z) = h (1 + tanh h): one packed FP16 tanh and one packed FP16
+// FMA per two activations, whose result is already the next layer's
+// operand.  No conversion instruction is needed: the FP16 accumulators load
+// as FP16 values (one per TMEM column, in its low half) and are paired by
+// byte permutes; the special-function pipe, which takes 16 cycles per warp
+// for a packed tanh and 4 for a conversion, does the tanh alone.  The
+// output weights and bias are split into FP16 hi and lo parts (rows 0 and 1
+// of W4', hi = the BF16 value), so z = D[:, 0] + D[:, 1] carries the FP32
+// values to about 2^-19.
 //
 // Shared-memory operands use the no-swizzle K-major layout: 8 x 16-byte
 // core matrices, the 8-row groups 128 bytes apart (SBO) and the K blocks of
-// 8 elements LBO bytes apart; with that choice a [rows][8] BF16 array is one
+// 8 elements LBO bytes apart; with that choice a [rows][8] FP16 array is one
 // K block, row r at byte 16 r.
 //
 // Each warpgroup owns 256 TMEM columns: two slots of {accumulator 64
@@ -39,15 +43,19 @@ constexpr int kRows = 128;          // rows of a tile (TMEM lanes)
 constexpr int kH = 64;              // hidden width
 constexpr int kColsPerWg = 256;     // TMEM columns a warpgroup allocates
 constexpr int kSlotCols = 128;      // columns per slot
-constexpr int kActCol = 64;         // activations within a slot (32 columns of BF16 pairs)
+constexpr int kActCol = 64;         // activations within a slot (32 columns of FP16 pairs)
 constexpr int kOnesCol = 96;        // the bias block's constant ones (8 columns)
-constexpr uint32_t kOnesWord = 0x3F803F80u;   // BF16 pair (1, 1)
-constexpr uint32_t kDefaultPolls = 1u << 20;
+constexpr uint32_t kOnesWord = 0x3C003C00u;   // FP16 pair (1, 1)
+// default wait limit: polls of a phase, each suspending the warp for at most
+// kSuspendNs unless the phase completes first (about 2.6 s in all)
+constexpr uint32_t kDefaultPolls = 1u << 17;
+constexpr uint32_t kSuspendNs = 20000;
 
 // Inference weights in the tensor cores' shared-memory operand layout, plus
 // the feature normalisation and the training envelope.  Copied into shared
 // memory by every kernel that evaluates the network.
 struct __align__(128) MlpTc {
+    // FP16 bits; W1..W3 hold the halved BF16 weight values
     uint16_t w1[2][kH][8];    // K blocks of W1/2 [n][k]: block 0 columns 0..5 weights, 6, 7 hi/lo of b1/2; block 1 zero
     uint16_t w2[10][kH][8];   // K blocks 0..7: W2/2; block 8: columns 0, 1 = hi/lo of b2/2; block 9 zero
     uint16_t w3[10][kH][8];
@@ -59,7 +67,7 @@ struct __align__(128) MlpTc {
 };
 
 // shared-memory bytes, after the MlpTc block, of one warpgroup's feature tiles
-// ([tiles][128][8] BF16) plus the zero K block every feature tile shares
+// ([tiles][128][8] FP16) plus the zero K block every feature tile shares
 __host__ __device__ constexpr size_t feat_bytes(int tiles) { return (size_t)tiles * kRows * 16 + (size_t)kRows * 16; }
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -88,7 +96,7 @@ __device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint3
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
-// D (+)= A B^T, A from TMEM (row r in lane r, BF16 pairs per column)
+// D (+)= A B^T, A from TMEM (row r in lane r, FP16 pairs per column)
 __device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -151,10 +159,10 @@ __device__ __forceinline__ void mb_arrive(uint64_t *bar) {
 __device__ __forceinline__ bool mb_try(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(su32(bar)), "r"(parity)
+        : "r"(su32(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -165,33 +173,30 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
-// Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
-// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+// Instruction descriptor of kind::f16 with A and B FP16 (bits 7-9, 10-12 =
+// 0), both K-major, D FP16 (bits 4-5 = 0) or FP32 (= 1), N >> 3 at bit 17,
+// M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_f16(int m, int n, bool d_fp32) {
+    return ((d_fp32 ? 1u : 0u) << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+__device__ __forceinline__ uint32_t pack_f16x2(float lo, float hi) {
     uint32_t h;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(hi), "f"(lo));
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(hi), "f"(lo));
     return h;
 }
-// SiLU of two halved pre-activations (FP32 accumulator bits) as one BF16
-// pair: h + h tanh h, the tanh packed in FP16 (one special-function
-// operation for both), the product and sum in FP32 (no cancellation at
-// h << 0 beyond the tanh's own error), then one rounding to BF16.
-__device__ __forceinline__ uint32_t silu_bf16x2(uint32_t lo_bits, uint32_t hi_bits) {
-    const float hl = __uint_as_float(lo_bits), hh = __uint_as_float(hi_bits);
-    uint32_t h16, t16;
-    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h16) : "f"(hh), "f"(hl));
-    asm("tanh.approx.f16x2 %0, %1;" : "=r"(t16) : "r"(h16));
-    float tl, th;
-    asm("{\n .reg .f16 a, b;\n mov.b32 {a, b}, %2;\n cvt.f32.f16 %0, a;\n cvt.f32.f16 %1, b;\n}\n"
-        : "=f"(tl), "=f"(th)
-        : "r"(t16));
-    const float2 hv = make_float2(hl, hh);
-    const float2 s = __ffma2_rn(hv, make_float2(tl, th), hv);
-    return pack_bf16x2(s.x, s.y);
+// SiLU of a pair of halved pre-activations (FP16 pair): h (1 + tanh h)
+__device__ __forceinline__ uint32_t silu_f16x2(uint32_t h) {
+    uint32_t t, o;
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(h));
+    asm("fma.rn.f16x2 %0, %1, %2, %1;" : "=r"(o) : "r"(h), "r"(t));
+    return o;
+}
+// the FP16 values in the low halves of two TMEM words as one FP16 pair
+__device__ __forceinline__ uint32_t pair_lo16(uint32_t lo, uint32_t hi) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, 0x5410;" : "=r"(d) : "r"(lo), "r"(hi));
+    return d;
 }
 
 // One warpgroup's tensor-core state: TMEM base (lane 0, first of its 256
@@ -306,7 +311,7 @@ __device__ __forceinline__ void issue_layer(const Warpgroup &wg, const MlpTc *sw
         // rows 16 bytes apart (8-row groups 128 B apart); the second K block is the shared zero block
         const uint64_t a = sdesc(feat_tile, zero_addr - feat_tile, 128);
         const uint64_t b = sdesc(su32(sw->w1), kH * 16, 128);
-        mma_ss(d, a, b, idesc_bf16(kRows, kH), 0u);
+        mma_ss(d, a, b, idesc_f16(kRows, kH, false), 0u);
         return;
     }
     const uint32_t act = d + kActCol;
@@ -314,12 +319,12 @@ __device__ __forceinline__ void issue_layer(const Warpgroup &wg, const MlpTc *sw
         const uint32_t w = su32(layer == 1 ? &sw->w2[0][0][0] : &sw->w3[0][0][0]);
 #pragma unroll
         for (int kk = 0; kk < 5; ++kk)
-            mma_ts(d, act + 8 * kk, sdesc(w + kk * 2 * kH * 16, kH * 16, 128), idesc_bf16(kRows, kH), kk > 0);
+            mma_ts(d, act + 8 * kk, sdesc(w + kk * 2 * kH * 16, kH * 16, 128), idesc_f16(kRows, kH, false), kk > 0);
     } else {
         const uint32_t w = su32(&sw->w4[0][0][0]);
 #pragma unroll
         for (int kk = 0; kk < 5; ++kk)
-            mma_ts(d, act + 8 * kk, sdesc(w + kk * 2 * 16 * 16, 16 * 16, 128), idesc_bf16(kRows, 16), kk > 0);
+            mma_ts(d, act + 8 * kk, sdesc(w + kk * 2 * 16 * 16, 16 * 16, 128), idesc_f16(kRows, 16, true), kk > 0);
     }
 }
 
@@ -354,15 +359,15 @@ __device__ __forceinline__ void run(Warpgroup &wg, const MlpTc *sw, const unsign
                 wg.wait_warp(s);
                 fence_after();
                 const uint32_t acc = wg.tmem + lane_base + (uint32_t)(s * kSlotCols);
-                uint32_t v[32], o[32];
+                uint32_t v[32], w[32], o[32];
                 ld32(acc, v);
+                ld32(acc + 32, w);
                 wait_ld(v);
+                wait_ld(w);   // returns at once: the wait above completed both loads
 #pragma unroll
-                for (int j = 0; j < 16; ++j) o[j] = silu_bf16x2(v[2 * j], v[2 * j + 1]);
-                ld32(acc + 32, v);
-                wait_ld(v);
+                for (int j = 0; j < 16; ++j) o[j] = silu_f16x2(pair_lo16(v[2 * j], v[2 * j + 1]));
 #pragma unroll
-                for (int j = 0; j < 16; ++j) o[16 + j] = silu_bf16x2(v[2 * j], v[2 * j + 1]);
+                for (int j = 0; j < 16; ++j) o[16 + j] = silu_f16x2(pair_lo16(w[2 * j], w[2 * j + 1]));
                 st32(acc + kActCol, o);
                 wait_st();
                 fence_before();

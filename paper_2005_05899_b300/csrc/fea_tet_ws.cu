@@ -44,7 +44,10 @@ namespace {
 constexpr int kWsStages = 5;   // input stages
 constexpr int kWsLag = 2;      // the gathers of a chunk trail its bulk copies by this many chunks
 constexpr int kWsSlots = 2;    // slot buffers
-constexpr uint32_t kWsDefaultPolls = 1u << 22;
+// Default wait limit: polls of a phase, each suspending the warp for at most
+// kWsSuspendNs unless the phase completes first (about 2.6 s in all).
+constexpr uint32_t kWsDefaultPolls = 1u << 17;
+constexpr uint32_t kWsSuspendNs = 20000;
 
 __device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -60,10 +63,10 @@ __device__ __forceinline__ void mb_expect_tx(uint64_t *bar, uint32_t bytes) {
 __device__ __forceinline__ bool mb_try(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(sa(bar)), "r"(parity)
+        : "r"(sa(bar)), "r"(parity), "r"(kWsSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -79,7 +82,8 @@ __device__ __forceinline__ bool mb_test(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 // Limit of a bounded wait: `polls` polls of the phase, each a try_wait
-// (which may suspend the warp for a hardware-chosen time) or, with `quick`,
+// (which suspends the warp until the phase completes, for at most
+// kWsSuspendNs) or, with `quick`,
 // a non-suspending test_wait (a set poll limit then bounds the wait tightly).
 struct WaitLimit {
     uint32_t polls;
@@ -622,7 +626,7 @@ cudaError_t launch_tet_ws(const BucketDev &b, const FieldDev &f, const AsmArgs &
                 : launch(k_tet_ws<NW, NR, false>, 32 * (NW + NR + 1))
     switch (b.ws_nw) {
         case 12: FEA_WS_LAUNCH(12, 3);
-        case 8: FEA_WS_LAUNCH(8, 3);
+        case 8: FEA_WS_LAUNCH(8, 4);
         case 4: FEA_WS_LAUNCH(4, 2);
     }
 #undef FEA_WS_LAUNCH
