@@ -6,11 +6,14 @@ learned model, so this module defines the data pipeline:
 1. **Fine runs of the plain method.**  A Taylor-Green vortex (nu = 1/1600) on
    an n_f^3 periodic Kuhn tet mesh, advanced by the three RK3 stages of
    Algorithm 1 with the library's element assembly (mixed precision, Vreman
-   closure) for the momentum RHS.  In place of the pressure Poisson / CG
-   solve of Algorithm 1 the velocity is made divergence-free after every
-   stage by a spectral (Leray) projection on the periodic node grid (a
-   fractional-step method: momentum without the pressure gradient, then
-   projection), which on a periodic grid needs no iteration.
+   closure) for the momentum RHS.  Two ways to keep it divergence-free:
+   `projection="library"` runs Algorithm 1 itself, the library's pressure
+   projection (Jacobi-PCG on the Galerkin Laplacian) once per step after the
+   stages, which use the frozen pressure; `projection="spectral"` makes the
+   velocity divergence-free after every stage by a spectral (Leray)
+   projection on the periodic node grid, which needs no iteration (the
+   training sets of large fine meshes, where the CG solve would take
+   thousands of iterations per step).
 2. **Box filter** of the fine nodal velocity to a coarse grid of n_f / r
    cells per direction (trapezoidal top-hat of width r fine cells, periodic),
    for r in `ratios` (several filter widths give the network the range of
@@ -74,8 +77,12 @@ def _leray(ug: torch.Tensor) -> torch.Tensor:
 
 
 def fine_tgv_run(ctx: fea.Context, n_f: int, t_snap: Sequence[float], nu: float = 1.0 / 1600.0,
-                 c_vreman: float = 0.07, cfl: float = 0.3, log=None) -> List[Snapshot]:
-    """Fine LES of the Taylor-Green vortex; returns master-grid snapshots at t_snap."""
+                 c_vreman: float = 0.07, cfl: float = 0.3, log=None, projection: str = "spectral",
+                 stats: Dict = None) -> List[Snapshot]:
+    """Fine LES of the Taylor-Green vortex; returns master-grid snapshots at
+    t_snap.  projection: "spectral" (Leray projection of every stage) or
+    "library" (the library's RK3 stages and pressure projection per step,
+    Algorithm 1); stats, if given, receives the CG iteration counts."""
     mesh = mg.tgv_mesh(n_f, sfc=False)
     field = mg.tgv_field(mesh, nu=nu, c_vreman=c_vreman)
     dm = ctx.upload_mesh(mesh)
@@ -107,6 +114,30 @@ def fine_tgv_run(ctx: fea.Context, n_f: int, t_snap: Sequence[float], nu: float 
     out = []
     targets = sorted(t_snap)
     ti = 0
+    if projection == "library":
+        dm.upload_field(u, torch.tensor(field.p, device="cuda"), nu, c_vreman)
+        dm.poisson_setup()
+        state = torch.empty((3, N), dtype=torch.float64, device="cuda")
+        iters = []
+        while ti < len(targets):
+            step = min(dt, targets[ti] - t)
+            if step <= 1e-12:
+                dm.state(state)
+                torch.cuda.synchronize()
+                out.append(Snapshot(t, to_grid(state).clone()))
+                ti += 1
+                continue
+            for k in range(3):
+                dm.rk_stage(k, step, prec="mixed", closure="vreman")
+            it, rr = dm.project(step, rtol=1e-8, max_iter=20000)
+            iters.append(it)
+            t += step
+            if log and abs(t - round(t)) < 0.5 * dt:
+                log(f"fine run (library projection) t={t:.2f} CG iterations {it} residual {rr:.1e}")
+        if stats is not None:
+            stats["cg_iterations"] = iters
+        ctx.sync_status()
+        return out
     while ti < len(targets):
         step = min(dt, targets[ti] - t)
         if step <= 1e-12:
@@ -216,10 +247,10 @@ def coarse_samples(snap: Snapshot, r: int, keep_stress: bool = True, nu: float =
 
 
 def generate(ctx: fea.Context, n_f: int = 96, ratios=(4, 8), t_snap=(3.0, 4.0, 5.0, 6.0, 7.0, 8.0), log=None,
-             t_stress=None):
+             t_stress=None, projection: str = "spectral", stats: Dict = None):
     """Fine run + filtered samples: {t: [CoarseSet per ratio]}; stresses kept
     at the times in t_stress (all when None)."""
-    snaps = fine_tgv_run(ctx, n_f, t_snap, log=log)
+    snaps = fine_tgv_run(ctx, n_f, t_snap, log=log, projection=projection, stats=stats)
     return {s.t: [coarse_samples(s, r, keep_stress=t_stress is None or s.t in t_stress) for r in ratios]
             for s in snaps}
 
@@ -347,7 +378,7 @@ def apriori_errors(ctx: fea.Context, cs: CoarseSet, nu: float = 1.0 / 1600.0, c_
 
 
 def run(n_f: int = 96, ratios=(4, 8), t_train=(3.0, 4.0, 5.0, 7.0, 8.0), t_test=(6.0,), steps: int = 2000,
-        save: str = "", log=print, ctx: fea.Context = None) -> Dict:
+        save: str = "", log=print, ctx: fea.Context = None, projection: str = "spectral") -> Dict:
     """Fine run, filtering, GPU training and the a-priori comparison on held-out times.
 
     Returns a JSON-able dict plus the key "model" (the TrainedClosure, left
@@ -357,8 +388,9 @@ def run(n_f: int = 96, ratios=(4, 8), t_train=(3.0, 4.0, 5.0, 7.0, 8.0), t_test=
     if own:
         ctx = fea.Context(0)
     t0 = time.time()
+    stats: Dict = {}
     data = generate(ctx, n_f=n_f, ratios=ratios, t_snap=sorted(set(t_train) | set(t_test)), log=log,
-                    t_stress=set(t_test))
+                    t_stress=set(t_test), projection=projection, stats=stats)
     t_gen = time.time() - t0
     train_sets = [c for t in t_train for c in data[t]]
     test_sets = [c for t in t_test for c in data[t]]
@@ -368,9 +400,12 @@ def run(n_f: int = 96, ratios=(4, 8), t_train=(3.0, 4.0, 5.0, 7.0, 8.0), t_test=
     if save:
         np.savez(save, theta=model.theta, mean=model.mean, std=model.std, scale=model.scale, env_lo=model.env_lo,
                  env_hi=model.env_hi)
-    res = {"n_f": n_f, "ratios": list(ratios), "samples_train": int(model.n_samples),
+    res = {"n_f": n_f, "ratios": list(ratios), "projection": projection, "samples_train": int(model.n_samples),
            "generate_s": t_gen, "train_s": t_train_s, "loss_first": model.losses[0], "loss_last": model.losses[-1],
            "fit_mse": model.fit_mse, "target_var": model.target_var, "test": []}
+    if stats.get("cg_iterations"):
+        its = stats["cg_iterations"]
+        res["cg_iterations"] = {"steps": len(its), "mean": float(np.mean(its)), "max": int(np.max(its))}
     for c in test_sets:
         e = apriori_errors(ctx, c)
         e["n_c"] = c.n_c
@@ -388,7 +423,8 @@ if __name__ == "__main__":
     ap.add_argument("--n-f", type=int, default=96)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--save", default="")
+    ap.add_argument("--projection", choices=["spectral", "library"], default="spectral")
     a = ap.parse_args()
-    r = run(n_f=a.n_f, steps=a.steps, save=a.save)
+    r = run(n_f=a.n_f, steps=a.steps, save=a.save, projection=a.projection)
     r.pop("model")
     print(json.dumps(r), flush=True)
