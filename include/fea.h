@@ -244,16 +244,21 @@ fea_status fea_state_download(fea_ctx *ctx, int32_t mesh, double *out, void *str
 /* ---- learned closure --------------------------------------------------
  * A small network that stands in for the Vreman closure of section 2.1 (the
  * paper has no learned model): 6 -> 64 -> 64 -> 64 -> 1, SiLU hidden layers,
- * softplus output, nu_t = out_scale * softplus(z).  Inputs per Gauss point
- * (per element for TET04): with S = (G+G^T)/2, O = (G-G^T)/2,
- *   x_k = sign(I_k) |I_k|^(1/d_k),  I = (tr S^2, tr O^2, tr S^3, tr S O^2,
- *   tr S^2 O^2),  d = (2, 2, 3, 3, 4),  x_6 = log Delta  (Delta = V_e^(1/3)),
- * normalised as (x - mean) / std.  Parameter vector theta (FP32, 8,833):
+ * softplus output.  Inputs per Gauss point (per element for TET04), all
+ * dimensionless: with G the velocity gradient, S = (G+G^T)/2, O = (G-G^T)/2
+ * and g = |G| (Frobenius),
+ *   x_1..5 = (tr S^2, tr O^2, tr S^3, tr S O^2, tr S^2 O^2) / g^(2, 2, 3, 3, 4),
+ *   x_6 = log(Delta^2 g / nu)  (Delta = V_e^(1/3)),
+ * normalised as (x - mean) / std; the network gives the coefficient
+ * C = out_scale * softplus(z) and nu_t = C Delta^2 g (zero where g = 0).
+ * Parameter vector theta (FP32, 8,833):
  *   w1[64][6] b1[64] w2[64][64] b2[64] w3[64][64] b3[64] w4[64] b4[1].
  * Training evaluates BF16 weights and activations with FP32 accumulation on
- * the tensor cores and updates the FP32 master copy by Adam.  Inference
- * (fea_mlp_forward and the fused closure) uses the same BF16 weight values
- * with FP16 activations and FP32 accumulation; normalised features are
+ * warp-level tensor-core tiles and updates the FP32 master copy by Adam.
+ * Inference (fea_mlp_forward and the fused closure) runs on the tcgen05
+ * tensor cores over 128-row tiles: the same BF16 weight values held as FP16
+ * operands, FP16 activations and hidden-layer accumulators, an FP32 output
+ * layer with the output weights to about 2^-19; normalised features are
  * clamped to +-64.  With an envelope set (fea_mlp_set_envelope), a Gauss
  * point whose features or element size lie outside it takes Vreman's nu_t
  * instead (section 2.1), so the plain closure is the network's fallback. */
@@ -264,8 +269,9 @@ fea_status fea_mlp_load(fea_ctx *ctx, const float *theta, const float *feat_mean
                         double out_scale, void *stream);
 
 /* Training envelope of the fused closure: raw-feature bounds lo [6], hi [6]
- * (host).  A Gauss point uses the network only if each of its five
- * invariant features and its element's log Delta lie in [lo_k, hi_k];
+ * (host).  A Gauss point uses the network only if each of its six raw
+ * features (the five invariant ratios and log(Delta^2 g / nu)) lies in
+ * [lo_k, hi_k];
  * otherwise it uses Vreman's nu_t (c_vreman of the mesh's field), and the
  * point is counted (fea_mlp_fallback_read).  lo = hi = NULL removes the
  * envelope; fea_mlp_load also removes it.  Synchronises the stream.
@@ -280,8 +286,10 @@ fea_status fea_mlp_fallback_read(fea_ctx *ctx, int64_t *points, int reset);
 /* Copies the current FP32 parameters to theta_out [8833] (host or device). */
 fea_status fea_mlp_get(fea_ctx *ctx, float *theta_out, void *stream);
 
-/* nu_t for B rows of raw features x [B][6] (device) into nut [B] (device);
- * B = 0 is a no-op (x and nut may then be NULL). */
+/* The network's coefficient C = out_scale * softplus(z) (nu_t / (Delta^2 g))
+ * for B rows of raw features x [B][6] (device) into nut [B] (device), on
+ * the tensor-core tiles of the fused closure; B = 0 is a no-op (x and nut
+ * may then be NULL). */
 fea_status fea_mlp_forward(fea_ctx *ctx, const float *x, int64_t B, float *nut, void *stream);
 
 /* One training step on B samples: raw features x [B][6] and targets y [B]
