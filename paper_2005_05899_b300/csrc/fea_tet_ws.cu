@@ -530,47 +530,58 @@ __global__ void __launch_bounds__(32 * (NW + NR + 1), NW <= 4 ? 2 : 1)
             // node groups of 32 (lane = node): slot t of node l at toff[t] + l,
             // one loop over t for the whole warp, consecutive lanes reading
             // consecutive slots
-            for (int g = rw * 32; g < L; g += 32 * NR) {
-                const int l = g + lane;
-                float2 sxy = make_float2(0.f, 0.f);
-                float sz = 0.f;
-                // four incidences per step, their loads in flight together
-                // (toff[t + 1] - toff[t] = nodes with more than t slots)
+            // Two node groups per pass (group b = a + 32 NR), their slot
+            // loads in flight together; b's nodes have no more slots than
+            // a's (nodes numbered by decreasing slot count), so a's count
+            // ends the loop.  Each node's slots are added in the same order.
+            auto emit = [&](int l, float2 sxy, float sz) {
+                const float r0 = sxy.x, r1 = sxy.y, r2 = sz;
+                if (!isfinite(r0 + r1 + r2)) atomicOr(args.err, ERR_NONFINITE);
+                const uint32_t id = ids[l];
+                double *o = args.rhs + (id & 0x7fffffffu);
+                const double v0 = widen(r0), v1 = widen(r1), v2 = widen(r2);
+                if (id & 0x80000000u) {
+                    atomicAdd(o, v0);
+                    atomicAdd(o + f.n, v1);
+                    atomicAdd(o + 2 * f.n, v2);
+                } else {
+                    o[0] = v0;
+                    o[f.n] = v1;
+                    o[2 * f.n] = v2;
+                }
+            };
+            for (int g = rw * 32; g < L; g += 64 * NR) {
+                const int gb = g + 32 * NR;
+                const int la = g + lane, lb = gb + lane;
+                float2 sa = make_float2(0.f, 0.f), sb = make_float2(0.f, 0.f);
+                float za = 0.f, zb = 0.f;
+                // four incidences per step (toff[t + 1] - toff[t] = nodes
+                // with more than t slots)
                 uint32_t o0 = toff[0];
                 for (int t = 0; t < 64; t += 4) {
                     uint32_t o[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) o[u] = toff[t + 1 + u];
                     if (g >= (int)(o[0] - o0)) break;
-                    float4 v[4];
+                    float4 va[4], vb[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const uint32_t lo = u ? o[u - 1] : o0;
-                        v[u] = l < (int)(o[u] - lo) ? slot[lo + l] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const int cnt = (int)(o[u] - lo);
+                        va[u] = la < cnt ? slot[lo + la] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        vb[u] = lb < cnt ? slot[lo + lb] : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        sxy = __fadd2_rn(sxy, make_float2(v[u].x, v[u].y));
-                        sz += v[u].z;
+                        sa = __fadd2_rn(sa, make_float2(va[u].x, va[u].y));
+                        za += va[u].z;
+                        sb = __fadd2_rn(sb, make_float2(vb[u].x, vb[u].y));
+                        zb += vb[u].z;
                     }
                     o0 = o[3];
                 }
-                if (l < L) {
-                    const float r0 = sxy.x, r1 = sxy.y, r2 = sz;
-                    if (!isfinite(r0 + r1 + r2)) atomicOr(args.err, ERR_NONFINITE);
-                    const uint32_t id = ids[l];
-                    double *o = args.rhs + (id & 0x7fffffffu);
-                    const double v0 = widen(r0), v1 = widen(r1), v2 = widen(r2);
-                    if (id & 0x80000000u) {
-                        atomicAdd(o, v0);
-                        atomicAdd(o + f.n, v1);
-                        atomicAdd(o + 2 * f.n, v2);
-                    } else {
-                        o[0] = v0;
-                        o[f.n] = v1;
-                        o[2 * f.n] = v2;
-                    }
-                }
+                if (la < L) emit(la, sa, za);
+                if (lb < L) emit(lb, sb, zb);
             }
             __syncwarp();
             if (lane == 0) {
