@@ -134,9 +134,20 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def tet_kernel_config(plan: dict) -> dict:
+    """Launch configuration of the TET04 kernel a plan selects: with the chunk
+    scatter (FP32 node sums) the warp-specialised kernel runs 12, 8 or 4
+    compute warps (threads per block >= 384, >= 256, else), its chunks 64
+    elements per compute warp whatever the plan's chunk_elems."""
+    t = int(plan.get("threads_per_block", 0))
+    return {"scatter": plan.get("scatter"), "chunk_acc": plan.get("chunk_acc"),
+            "compute_warps": 12 if t >= 384 else (8 if t >= 256 else 4)}
+
+
 def ncu_traffic(kernel_key: str, plan: dict):
     """dram read+write bytes per launch from a committed ncu summary, if it was
-    taken on the current kernel sources with the same launch plan; else None."""
+    taken on the current kernel sources with the same TET04 kernel
+    configuration; else None."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
@@ -147,7 +158,7 @@ def ncu_traffic(kernel_key: str, plan: dict):
     for rec in recs:   # one record per launch plan measured
         if rec.get("source_hash") != kernel_source_hash():
             continue
-        if any(rec.get("plan", {}).get(k) != plan.get(k) for k in ("scatter", "threads_per_block", "chunk_elems")):
+        if tet_kernel_config(rec.get("plan", {})) != tet_kernel_config(plan):
             continue
         return float(rec["dram_bytes_per_launch"])
     return None

@@ -45,8 +45,14 @@ def test_traffic_record_needs_matching_sources_and_plan(bench, monkeypatch):
     # every recorded plan finds its own record
     for r in recs:
         assert bench.ncu_traffic("tet04_mixed_assembly", dict(r["plan"])) == r["dram_bytes_per_launch"]
-    # a plan that was not captured, another kernel key, changed sources: no traffic figure
-    assert bench.ncu_traffic("tet04_mixed_assembly", dict(plan, chunk_elems=96)) is None
+    # the generic chunk size does not change the TET04 kernel's launch
+    assert bench.ncu_traffic("tet04_mixed_assembly", dict(plan, chunk_elems=96)) == rec["dram_bytes_per_launch"]
+    # a configuration that was not captured, another kernel key, changed sources: no traffic figure
+    captured = {bench.tet_kernel_config(r["plan"])["compute_warps"] for r in recs}
+    missing = [t for t, w in ((128, 4), (256, 8), (384, 12)) if w not in captured]
+    if missing:
+        assert bench.ncu_traffic("tet04_mixed_assembly", dict(plan, threads_per_block=missing[0])) is None
+    assert bench.ncu_traffic("tet04_mixed_assembly", dict(plan, chunk_acc=1)) is None
     assert bench.ncu_traffic("no_such_kernel", plan) is None
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
     assert bench.ncu_traffic("tet04_mixed_assembly", plan) is None
