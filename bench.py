@@ -61,6 +61,13 @@ def make_workload(n_axis: int):
     return mesh, field
 
 
+def workload_config(mesh, ws: int) -> dict:
+    """The `config` of both arms' JSON lines: the workload they measure."""
+    return {"workload": WORKLOAD, "elements": mesh.n_elem_total, "nodes": mesh.n_nodes, "counts": mesh.counts(),
+            "l2": "inputs larger than L2 (no flush needed)",
+            "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"}
+
+
 def tet_algorithmic_bytes(mesh) -> tuple:
     """Algorithmic bytes of one TET04 assembly launch: int32 connectivity
     (16 B/element) + each referenced node once: coordinates (12 B) +
@@ -463,7 +470,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_t / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "elements": mesh.n_elem_total, "nodes": mesh.n_nodes},
+            "config": workload_config(mesh, ws),
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
                              "serial_value": sampler.serial(), "cpu_model": cpu_model()},
@@ -623,9 +630,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "accumulation": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "elements": E, "nodes": dm.n_nodes,
-                       "counts": mesh.counts(), "l2": "inputs larger than L2 (no flush needed)",
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU", "plan": plan.as_dict()},
+            "config": workload_config(mesh, ws), "plan": plan.as_dict(),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak, "traffic": traffic, "kernel": "TET04 assembly (mixed, Vreman)",
                          "peak_kind": "measured FP32: the library's FMA-chain kernel (fea_fp32_peak), the larger "

@@ -120,7 +120,7 @@ def test_times_are_the_maximum_over_two_gloo_ranks(bench):
     assert bench.max_over_ranks([3.5, 1.0], 1, device="cpu") == [3.5, 1.0]
 
 
-def test_reference_arm_prints_its_json_line():
+def test_reference_arm_prints_its_json_line(bench):
     """`bench.py --impl reference` (the oracle on the host cores, no GPU) on
     a small airplane-like mesh: one JSON line with the contract's keys."""
     import json
@@ -135,6 +135,10 @@ def test_reference_arm_prints_its_json_line():
     assert d["impl"] == "reference" and d["metric"] == "RHS assembly Melem/s" and d["unit"] == "Melem/s"
     assert d["higher_is_better"] is True and d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 3
     assert d["value"] > 0 and d["e2e"]["value"] == d["value"]
+    # the same workload description as the GPU arm's line
+    assert set(d["config"]) == {"workload", "elements", "nodes", "counts", "l2", "parallelism"}
+    assert d["config"]["workload"] == bench.WORKLOAD and d["config"]["elements"] == sum(
+        d["config"]["counts"].values())
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
