@@ -261,7 +261,11 @@ fea_status fea_state_download(fea_ctx *ctx, int32_t mesh, double *out, void *str
  * layer with the output weights to about 2^-19; normalised features are
  * clamped to +-64.  With an envelope set (fea_mlp_set_envelope), a Gauss
  * point whose features or element size lie outside it takes Vreman's nu_t
- * instead (section 2.1), so the plain closure is the network's fallback. */
+ * instead (section 2.1), so the plain closure is the network's fallback.
+ * The kernels that evaluate the network run persistent CTAs of 128 threads,
+ * two per SM, each holding 256 tensor-memory columns for its lifetime; a
+ * kernel that allocates tensor memory on the same SMs at the same time
+ * waits for those columns. */
 
 /* Loads theta, the feature mean and std [6] (host or device) and out_scale;
  * resets the Adam state.  Errors: FEA_EINVAL (null, std <= 0, scale <= 0). */
