@@ -760,14 +760,16 @@ static int device_sms() {
     return sms > 0 ? sms : 148;
 }
 
+// The network's waits keep their default limit (the wait limit a context
+// sets applies to the TET04 kernel).
 __device__ __forceinline__ void mlp_cta_setup(unsigned char *base, int ng, const void *gw, unsigned *err,
-                                              uint32_t polls, MlpUse &mu, tc::Warpgroup &wg) {
+                                              MlpUse &mu, tc::Warpgroup &wg) {
     tc::MlpTc *w = reinterpret_cast<tc::MlpTc *>(base);
     unsigned char *feat = base + sizeof(tc::MlpTc);
     unsigned char *zero = feat + (size_t)ng * tc::kRows * 16;
     unsigned char *scr = zero + tc::kRows * 16;
     uint64_t *bars = reinterpret_cast<uint64_t *>(scr + 4 * mlp_warp_scratch_bytes(ng));
-    tc::setup(static_cast<const tc::MlpTc *>(gw), w, zero, bars, wg, err, polls);
+    tc::setup(static_cast<const tc::MlpTc *>(gw), w, zero, bars, wg, err, 0u);
     mu.w = w;
     mu.feat = feat;
     mu.zero = zero;
@@ -874,8 +876,7 @@ __global__ void __launch_bounds__(MLP ? 128 : 256, MLP ? 2 : 1) k_assemble_atomi
         extern __shared__ float4 smem4[];
         MlpUse mu{};
         tc::Warpgroup wg;
-        mlp_cta_setup(reinterpret_cast<unsigned char *>(smem4), mlp_rows_per_elem(ET), args.mlp, args.err,
-                      args.wait_polls, mu, wg);
+        mlp_cta_setup(reinterpret_cast<unsigned char *>(smem4), mlp_rows_per_elem(ET), args.mlp, args.err, mu, wg);
         for (int64_t blk = blockIdx.x; blk * 128 < b.count; blk += gridDim.x)
             atomic_element<ET, R, J64, true, false>(b, f, args, blk * 128 + threadIdx.x, 0u, mu);
         tc::teardown(wg);
@@ -1159,7 +1160,7 @@ __global__ void __launch_bounds__(MLP ? 128 : 256, (MLP || J64 || ET == FEA_HEX0
     if constexpr (MLP) {
         // the fused closure's block after the chunk's buffers (one warpgroup)
         unsigned char *tail = reinterpret_cast<unsigned char *>(smem4) + mlp_tail_offset(chunk_smem_bytes_dev(b));
-        mlp_cta_setup(tail, mlp_rows_per_elem(ET), args.mlp, args.err, args.wait_polls, mu, wg);
+        mlp_cta_setup(tail, mlp_rows_per_elem(ET), args.mlp, args.err, mu, wg);
     }
     if constexpr (MLP) {
         // persistent: two CTAs per SM take the chunks in turn
@@ -1201,7 +1202,7 @@ __global__ void __launch_bounds__(MLP ? 128 : 256, 2) k_assemble_batch(const Buc
     if constexpr (MLP) {
         // element types vary per item: tiles and scratch for the largest row count
         unsigned char *tail = reinterpret_cast<unsigned char *>(smem4) + mlp_tail_offset(chunk_bytes);
-        mlp_cta_setup(tail, kMaxNg, ag[0].mlp, ag[0].err, ag[0].wait_polls, mu, wg);
+        mlp_cta_setup(tail, kMaxNg, ag[0].mlp, ag[0].err, mu, wg);
     }
     for (;;) {
         if (threadIdx.x == 0) item_s = (long long)atomicAdd(counter, 1ull);

@@ -254,7 +254,7 @@ __device__ __forceinline__ void setup(const MlpTc *gw, MlpTc *sw, unsigned char 
         for (int k = threadIdx.x; k < kRows; k += blockDim.x) z[k] = make_int4(0, 0, 0, 0);
     }
     uint32_t *taddr_slot = reinterpret_cast<uint32_t *>(bars + 4);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     if (warp == 0) {
         tmem_alloc(taddr_slot, kColsPerWg);
         tmem_relinquish();
@@ -284,7 +284,6 @@ __device__ __forceinline__ void setup(const MlpTc *gw, MlpTc *sw, unsigned char 
     st8(wg.tmem + lane_base + kOnesCol, ones);
     st8(wg.tmem + lane_base + kSlotCols + kOnesCol, ones);
     wait_st();
-    (void)lane;
     fence_before();
     __syncthreads();
     fence_after();
