@@ -88,6 +88,18 @@ def test_tet_flop_count_matches_its_itemisation(bench):
     assert sum(items) == bench.TET_FLOPS == 411
 
 
+def test_mesh_flops_sum_the_per_type_counts(bench):
+    # per Gauss point 90 nen + 147 operations, plus 5 per element
+    assert bench.ELEM_FLOPS == {"TET04": 4 * 507 + 5, "PYR05": 8 * 597 + 5, "PEN06": 6 * 687 + 5,
+                                "HEX08": 8 * 867 + 5}
+    counts = {"TET04": 3, "PYR05": 0, "PEN06": 2, "HEX08": 1}
+    assert bench.mesh_flops(counts) == 3 * 2033 + 2 * 4127 + 6941
+    assert bench.mesh_flops({}) == 0
+    # the batch's meshes (channel-like) by their own counts
+    m = mg.channel_mesh(nx=6, ny=10, nz=4, seed=1, n_layers=2, split_frac=0.3)
+    assert bench.mesh_flops(m.counts()) == sum(bench.ELEM_FLOPS[t] * n for t, n in m.counts().items())
+
+
 def _max_rank_main(rank, world, port, q):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
