@@ -132,7 +132,9 @@ typedef struct {
                                    runs ATOMIC (COLOUR and WARP apply to both) */
     int32_t threads_per_block;  /* element kernels: multiple of 32 in [32, 1024] (capped at 256);
                                    the TET04 chunk kernel (FEA_MIXED) takes from it its
-                                   compute warps: 12 from 384 threads, 8 from 256, else 4 */
+                                   compute warps: 12 from 384 threads, 8 from 256, else 4;
+                                   with the MLP closure the element kernels run one
+                                   warpgroup (128 threads) per CTA whatever this says */
     int32_t chunk_elems;        /* elements per chunk for FEA_SCATTER_CHUNK: multiple of 32 in [32, 4096]
                                    (the TET04 chunk kernel uses 64 per compute warp) */
     int32_t chunk_acc;          /* FEA_SCATTER_CHUNK nodal sums inside a chunk: 0 = FP32,
