@@ -459,6 +459,17 @@ def sampled_error(ctx, dm, mesh, field, n_sample: int = 3000, seed: int = 0) -> 
                                                                                               "max_norm": 2e-4}}
 
 
+def run_leg(name: str, fn):
+    """One secondary measurement of the JSON line (a configuration, the
+    oracle's error or rate): its result, or its failure reported in its
+    place, so that the headline and the other legs still print."""
+    try:
+        return fn()
+    except Exception as e:  # noqa: BLE001 - any failure of a secondary leg is reported, not raised
+        log(f"[bench] {name} failed: {type(e).__name__}: {e}")
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
@@ -657,13 +668,14 @@ def run_ours(args):
             "gpu_launches": launches, "clocks": clk}
     if rank == 0 and not args.no_secondary:
         t = time.time()
-        line["secondary"] = {"channel": secondary_channel(ctx, alu_peak), "batch": secondary_batch(ctx, alu_peak),
-                             "closure": secondary_closure(ctx)}
+        line["secondary"] = {"channel": run_leg("channel", lambda: secondary_channel(ctx, alu_peak)),
+                             "batch": run_leg("batch", lambda: secondary_batch(ctx, alu_peak)),
+                             "closure": run_leg("closure", lambda: secondary_closure(ctx))}
         log(f"[bench] secondary configs {time.time() - t:.1f}s")
     if rank == 0 and ws == 1 and not args.no_cpu:
         # the CPU leg: the oracle's error of the headline RHS, then its rate
-        line["error"] = sampled_error(ctx, dm, mesh, field)
-        line["cpu_baseline"] = cpu_baseline(mesh, field, target_s=args.cpu_seconds)
+        line["error"] = run_leg("error", lambda: sampled_error(ctx, dm, mesh, field))
+        line["cpu_baseline"] = run_leg("cpu_baseline", lambda: cpu_baseline(mesh, field, target_s=args.cpu_seconds))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

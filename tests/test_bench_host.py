@@ -88,6 +88,14 @@ def test_tet_flop_count_matches_its_itemisation(bench):
     assert sum(items) == bench.TET_FLOPS == 411
 
 
+def test_a_failed_secondary_leg_is_reported_in_its_place(bench):
+    assert bench.run_leg("ok", lambda: {"v": 1}) == {"v": 1}
+
+    def boom():
+        raise RuntimeError("device lost")
+    assert bench.run_leg("bad", boom) == {"error": "RuntimeError: device lost"}
+
+
 def test_mesh_flops_sum_the_per_type_counts(bench):
     # per Gauss point 90 nen + 147 operations, plus 5 per element
     assert bench.ELEM_FLOPS == {"TET04": 4 * 507 + 5, "PYR05": 8 * 597 + 5, "PEN06": 6 * 687 + 5,
